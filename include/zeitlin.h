@@ -1,0 +1,139 @@
+/*
+ * zeitlin.h -- C ABI of the GB300 (sm_103a) library for the per-time-step hot
+ * path of the Zeitlin-Euler solver on the sphere with the isospectral midpoint
+ * (IsoMP) integrator of Cifani, Viviani & Modin, "An efficient geometric method
+ * for incompressible hydrodynamics on the sphere" (arXiv 2206.05466).
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ *  - Matrices are N x N complex128 in DEVICE memory, row-major, leading
+ *    dimension N, real and imaginary parts interleaved: element (i, j) is
+ *    ptr[2*(i*N + j)] + i*ptr[2*(i*N + j) + 1].  A pointer must be 16-byte
+ *    aligned.  The caller owns every matrix; the library never frees one.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; calls that must read a device result to decide what to
+ *    launch next (isomp_step, isomp_run) block the calling host thread.
+ *  - The return value is a status: 0 success, > 0 a warning with the result
+ *    written, < 0 an error.  zt_last_error() gives a message for the calling
+ *    thread's last non-zero status.
+ *  - A plan owns its workspace; calls on one plan must not run concurrently
+ *    (on different streams or threads).  Different plans are independent.
+ */
+#ifndef ZEITLIN_H
+#define ZEITLIN_H
+
+#if defined(__GNUC__)
+#define ZT_API __attribute__((visibility("default")))
+#else
+#define ZT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ZT_OK              0
+#define ZT_NOT_CONVERGED   1   /* maxit sweeps reached; W_{n+1} still written  */
+#define ZT_EINVAL         -1   /* bad argument (size, pointer, alignment, h)   */
+#define ZT_ENOMEM         -2   /* device or host allocation failed             */
+#define ZT_ECUDA          -3   /* a CUDA runtime/driver call failed            */
+#define ZT_ENONFINITE     -4   /* residual is NaN or Inf (input not finite)    */
+#define ZT_ETIMEOUT       -5   /* a bounded device wait ran out                */
+
+#define ZT_PRECISION_FP64   0  /* complex products in FP64 (DFMA)                 */
+#define ZT_PRECISION_SPLIT  1  /* complex products as BF16 digit slices on tcgen05 */
+
+#define ZT_FINAL_FRESH  0      /* W_{n+1} from products recomputed at the last iterate */
+#define ZT_FINAL_REUSE  1      /* W_{n+1} from the products of the last sweep           */
+
+typedef struct zt_plan zt_plan;
+
+/* Tuning knobs; zero fields take the library default. */
+typedef struct zt_tuning {
+    int slices;          /* SPLIT: digit slices per operand, 3..8 (default 7)        */
+    int digit_bits;      /* SPLIT: bits per balanced digit, 6..8 (default 7)         */
+    int exact_groups;    /* SPLIT: leading digit groups summed exactly (default 4)   */
+    int final_mode;      /* ZT_FINAL_FRESH (default) or ZT_FINAL_REUSE               */
+    int sweeps_per_sync; /* sweeps enqueued between host convergence checks (def. 4) */
+} zt_tuning;
+
+typedef struct zt_step_stats {
+    int    iters;        /* fixed-point sweeps taken                               */
+    int    converged;    /* 1 if the residual fell below tol                       */
+    double residual;     /* last ||Wt^{k+1} - Wt^k||_F                             */
+} zt_step_stats;
+
+typedef struct zt_run_stats {
+    long   steps;        /* steps completed                                        */
+    long   total_iters;  /* sweeps over all steps                                  */
+    int    max_iters;    /* largest sweep count of one step                        */
+    int    all_converged;/* 1 if every step converged                              */
+    double max_residual; /* largest final residual of a step                       */
+} zt_run_stats;
+
+/* Create a plan for size N (1 <= N <= 16384) and precision ZT_PRECISION_*.
+ * Precomputes, once, the tridiagonal blocks of Delta_N (Sec. 3.2, Eq.
+ * delta_tria) and their LDL^T factors (the factorisation behind the HPD
+ * tridiagonal solve of Sec. 3.3), and allocates the step workspace (about
+ * 6 N^2 complex values, plus the digit slices for ZT_PRECISION_SPLIT).
+ * `opt` may be NULL.  On success *out receives the plan.  Errors: ZT_EINVAL,
+ * ZT_ENOMEM, ZT_ECUDA.  Uses the current CUDA device. */
+ZT_API int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_plan** out);
+
+/* Free a plan and its device workspace (NULL is ignored).  Synchronises the
+ * device first. */
+ZT_API void zt_plan_destroy(zt_plan* plan);
+
+/* Message for the calling thread's last non-zero status ("" if none). */
+ZT_API const char* zt_last_error(void);
+
+/* W = Delta_N P (Sec. 3.2-3.3): the discrete Laplacian applied diagonal by
+ * diagonal, each diagonal m (sub- and super-) through the tridiagonal block
+ * -T_m of Eq. delta_tria.  P is any complex N x N matrix; W must not alias P.
+ * O(N^2).  Errors: ZT_EINVAL, ZT_ECUDA. */
+ZT_API int zeitlin_laplacian_apply(zt_plan* plan, const double* P, double* W, void* stream);
+
+/* P = Delta_N^{-1} W for W in su(N) (Sec. 3.3, Eq. sub_tria_W): one
+ * tridiagonal system per sub-diagonal m = 0..N-1, solved with the
+ * precomputed factors; the l = 0 mode of the singular m = 0 block is
+ * projected out (mean of the right-hand side and of the solution removed).
+ * Only the lower triangle of W is read; the upper triangle of P is written as
+ * -conj of the lower (skew-Hermitian), so P is in su(N).  W must not alias P.
+ * O(N^2).  Errors: ZT_EINVAL, ZT_ECUDA. */
+ZT_API int zeitlin_stream_solve(zt_plan* plan, const double* W, double* P, void* stream);
+
+/* One IsoMP step in place, W = W_n on entry, W_{n+1} on return (Sec. 2,
+ * Eqs. isomp and isomp_iter; products as in Sec. 3.1).  Fixed-point sweeps
+ *   Pt = Delta_N^{-1} Wt,  A = Pt Wt,  B = A Pt,
+ *   Wt <- W_n + h/2 (A - A^H) + h^2/4 B,   r = ||Wt_new - Wt_old||_F
+ * from Wt = W_n until r < tol or maxit sweeps, then
+ *   W_{n+1} = Wt + h/2 (A - A^H) - h^2/4 B.
+ * W must be in su(N).  `stats` (host pointer, may be NULL) receives the sweep
+ * count and last residual.  Blocks the host thread until the step is done.
+ * Returns ZT_OK, ZT_NOT_CONVERGED (W_{n+1} written from the last iterate),
+ * ZT_ENONFINITE, ZT_ETIMEOUT, ZT_EINVAL or ZT_ECUDA. */
+ZT_API int isomp_step(zt_plan* plan, double* W, double h, double tol, int maxit,
+               zt_step_stats* stats, void* stream);
+
+/* nsteps IsoMP steps in place (same semantics as isomp_step for each step).
+ * `stats` (host pointer, may be NULL) receives totals.  Stops at the first
+ * error; a step that does not converge is reported in stats and in the
+ * return value (ZT_NOT_CONVERGED) but the run continues. */
+ZT_API int isomp_run(zt_plan* plan, double* W, double h, long nsteps, double tol,
+              int maxit, zt_run_stats* stats, void* stream);
+
+/* C = X Y for complex N x N X and skew-Hermitian Y (Y^H = -Y), in the plan's
+ * precision: the product kernel of the step (Sec. 3.1, both factors of the
+ * commutator products are in su(N)).  Only Y's skew-Hermitian structure is
+ * used: C = -X conj(Y)^T.  Exposed for parity tests.  Errors: ZT_EINVAL,
+ * ZT_ECUDA, ZT_ETIMEOUT. */
+ZT_API int zt_zgemm_skew(zt_plan* plan, const double* X, const double* Y, double* C, void* stream);
+
+/* Number of kernel launches the library enqueued since the plan was created
+ * (every launch of every entry point on this plan). */
+ZT_API long zt_plan_launch_count(const zt_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZEITLIN_H */

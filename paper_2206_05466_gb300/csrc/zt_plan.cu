@@ -1,0 +1,668 @@
+// Plan, Laplacian apply, stream solve, fixed-point update/convergence and the
+// IsoMP step driver of libzeitlin (GB300, sm_103a).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "zt_internal.h"
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+int zt_fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int zt_cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation)
+        return zt_fail(ZT_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return zt_fail(ZT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" const char* zt_last_error(void) { return g_err; }
+
+static int launch_check(zt_plan* p, const char* what) {
+    p->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, what);
+    return ZT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Constant per-diagonal data (Sec. 3.2, Eq. delta_tria) and LDL^T factors.
+// One thread per diagonal m; entries go to packed lower-triangular arrays at
+// (r, c) = (i + m, i).  For m = 0 only the leading N-1 equations are factored
+// (the l = 0 mode is projected out); the dropped row gets l = 0, -1/d = 0.
+// ---------------------------------------------------------------------------
+__global__ void factor_kernel(int N, double* lap_a, double* lap_b, double* fac_l, double* fac_nd) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N) return;
+    const int n = N - m;
+    const int ns = (m == 0) ? N - 1 : n;   // size of the factored system
+    const double s = (N - 1) / 2.0;
+    double d = 0.0, bprev = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double di = (double)i;
+        const double a = 2.0 * (s * (2.0 * di + 1.0 + m) - di * (di + m));
+        double b = 0.0;
+        if (i < n - 1)
+            b = -sqrt((di + m + 1.0) * (N - 1.0 - di - m)) * sqrt((di + 1.0) * (N - 1.0 - di));
+        const size_t at = zt_tri(i + m, i);
+        lap_a[at] = a;
+        lap_b[at] = b;
+        double l = 0.0, nd = 0.0;
+        if (i < ns) {
+            if (i == 0) {
+                d = a;
+            } else {
+                l = bprev / d;
+                d = a - l * bprev;
+            }
+            nd = -1.0 / d;
+        }
+        fac_l[at] = l;
+        fac_nd[at] = nd;
+        bprev = b;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// W = Delta_N P, elementwise over the matrix: element (r, c) lies on diagonal
+// |r - c| at position min(r, c); the block -T_m couples it to its neighbours
+// (r-1, c-1) and (r+1, c+1) on the same diagonal.
+// ---------------------------------------------------------------------------
+__global__ void laplacian_kernel(const double2* __restrict__ P, double2* __restrict__ W,
+                                 const double* __restrict__ la, const double* __restrict__ lb, int N) {
+    const int r = blockIdx.y;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int hi = max(r, c), lo = min(r, c);
+    const double a = la[zt_tri(hi, lo)];
+    const double2 p = P[(size_t)r * N + c];
+    double vx = a * p.x, vy = a * p.y;
+    if (lo > 0) {
+        const double b = lb[zt_tri(hi - 1, lo - 1)];
+        const double2 q = P[(size_t)(r - 1) * N + (c - 1)];
+        vx = fma(b, q.x, vx);
+        vy = fma(b, q.y, vy);
+    }
+    if (hi < N - 1) {
+        const double b = lb[zt_tri(hi, lo)];
+        const double2 q = P[(size_t)(r + 1) * N + (c + 1)];
+        vx = fma(b, q.x, vx);
+        vy = fma(b, q.y, vy);
+    }
+    W[(size_t)r * N + c] = make_double2(-vx, -vy);
+}
+
+int zt_launch_laplacian(zt_plan* p, const double2* P, double2* W, cudaStream_t s) {
+    const int N = p->N;
+    dim3 grid((N + 127) / 128, N);
+    laplacian_kernel<<<grid, 128, 0, s>>>(P, W, p->lap_a, p->lap_b, N);
+    return launch_check(p, "laplacian_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Stream solve (Sec. 3.3, Eq. sub_tria_W).
+//
+// A CTA owns a band of SD consecutive sub-diagonals [m0, m0+SD).  The band's
+// elements in rows [r0, r0+SR) form, row by row, contiguous runs of SD
+// complex values (row r holds W[r, r-m] at columns r-m0-SD+1 .. r-m0), so
+// the band is staged through shared memory in coalesced row segments
+// (cp.async, double buffered).  One warp runs the Thomas recurrences, one
+// lane per diagonal:
+//   forward   z_i = w_i - l_i z_{i-1}
+//   backward  x_i = (-1/d_i) z_i - l_{i+1} x_{i+1}      (x = P on the diagonal)
+// z is parked in the lower triangle of P between the passes.  The upper
+// triangle is written as P[i, i+m] = -conj(P[i+m, i]).  Band 0 also removes
+// the mean of the m = 0 right-hand side and of its solution (l = 0 mode).
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int SD = 32;   // diagonals per band
+constexpr int SR = 32;   // rows per staged chunk
+constexpr int ST = 128;  // threads per CTA
+constexpr size_t SOLVE_SMEM = 2 * SR * SD * (sizeof(double2) + 2 * sizeof(double));
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    int sz = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    int sz = valid ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Deterministic block sum of a complex value over ST threads.
+__device__ double2 block_sum2(double2 v, double2* sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int w = ST / 2; w > 0; w >>= 1) {
+        if (t < w) {
+            sh[t].x += sh[t + w].x;
+            sh[t].y += sh[t + w].y;
+        }
+        __syncthreads();
+    }
+    double2 r = sh[0];
+    __syncthreads();
+    return r;
+}
+}  // namespace
+
+__global__ void __launch_bounds__(ST)
+stream_solve_kernel(const double2* __restrict__ W, double2* __restrict__ P,
+                    const double* __restrict__ fl, const double* __restrict__ fnd,
+                    int N, const zt_dev_state* st, int gate) {
+    if (zt_gate_skip(st, gate)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* tw = reinterpret_cast<double2*>(smem_raw);                       // [2][SR][SD]
+    double* tl = reinterpret_cast<double*>(tw + 2 * SR * SD);                 // [2][SR][SD]
+    double* tn = tl + 2 * SR * SD;                                            // [2][SR][SD]
+    __shared__ double2 red[ST];
+
+    const int m0 = blockIdx.x * SD;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nch = (N - m0 + SR - 1) / SR;
+    const int m = m0 + lane;   // diagonal of this lane in the compute warp
+
+    double2 mu = make_double2(0.0, 0.0);
+    if (m0 == 0) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int i = tid; i < N; i += ST) {
+            double2 w = W[(size_t)i * N + i];
+            acc.x += w.x;
+            acc.y += w.y;
+        }
+        acc = block_sum2(acc, red);
+        mu = make_double2(acc.x / N, acc.y / N);
+    }
+
+    // stage rows [r0, r0+SR) of the band: element (rr, tt) = (r0+rr, r0+rr-m0-tt)
+    auto stage = [&](int buf, int r0, const double2* src, bool want_nd) {
+        for (int rr = warp; rr < SR; rr += ST / 32) {
+            const int tt = SD - 1 - lane;
+            const int r = r0 + rr, mm = m0 + tt, c = r - mm;
+            const bool ok = (r >= 0) && (r < N) && (mm < N) && (c >= 0);
+            const size_t e = ok ? (size_t)r * N + c : 0;
+            const size_t q = ok ? zt_tri(r, c) : 0;
+            const int at = (buf * SR + rr) * SD + tt;
+            cp_async16(&tw[at], src + e, ok);
+            cp_async8(&tl[at], fl + q, ok);
+            if (want_nd) cp_async8(&tn[at], fnd + q, ok);
+        }
+    };
+    auto unstage = [&](int buf, int r0) {
+        for (int rr = warp; rr < SR; rr += ST / 32) {
+            const int tt = SD - 1 - lane;
+            const int r = r0 + rr, mm = m0 + tt, c = r - mm;
+            const bool ok = (r >= 0) && (r < N) && (mm < N) && (c >= 0);
+            if (ok) P[(size_t)r * N + c] = tw[(buf * SR + rr) * SD + tt];
+        }
+    };
+
+    // ---- forward pass: rows m0 .. N-1 in increasing order ----
+    double2 zprev = make_double2(0.0, 0.0);
+    stage(0, m0, W, false);
+    cp_async_commit();
+    for (int ch = 0; ch < nch; ++ch) {
+        const int b = ch & 1, r0 = m0 + ch * SR;
+        if (ch + 1 < nch) stage(b ^ 1, r0 + SR, W, false);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        if (warp == 0 && m < N) {
+#pragma unroll 4
+            for (int rr = 0; rr < SR; ++rr) {
+                const int r = r0 + rr;
+                if (r >= m && r < N) {
+                    const int at = (b * SR + rr) * SD + lane;
+                    double2 w = tw[at];
+                    if (m == 0) {
+                        w.x -= mu.x;
+                        w.y -= mu.y;
+                    }
+                    const double l = tl[at];
+                    double2 z;
+                    z.x = fma(-l, zprev.x, w.x);
+                    z.y = fma(-l, zprev.y, w.y);
+                    tw[at] = z;
+                    zprev = z;
+                }
+            }
+        }
+        __syncthreads();
+        unstage(b, r0);
+        __syncthreads();
+    }
+
+    // ---- backward pass: rows N-1 .. m0 in decreasing order ----
+    double2 xnext = make_double2(0.0, 0.0);
+    double lnext = 0.0;
+    stage(0, N - SR, P, true);
+    cp_async_commit();
+    for (int ch = 0; ch < nch; ++ch) {
+        const int b = ch & 1, r0 = N - (ch + 1) * SR;
+        if (ch + 1 < nch) stage(b ^ 1, r0 - SR, P, true);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        if (warp == 0 && m < N) {
+#pragma unroll 4
+            for (int rr = SR - 1; rr >= 0; --rr) {
+                const int r = r0 + rr;
+                if (r >= m && r < N && r >= 0) {
+                    const int at = (b * SR + rr) * SD + lane;
+                    const double2 z = tw[at];
+                    const double nd = tn[at];
+                    double2 x;
+                    x.x = fma(-lnext, xnext.x, z.x * nd);
+                    x.y = fma(-lnext, xnext.y, z.y * nd);
+                    tw[at] = x;
+                    xnext = x;
+                    lnext = tl[at];
+                    if (m > 0) P[(size_t)(r - m) * N + r] = make_double2(-x.x, x.y);
+                }
+            }
+        }
+        __syncthreads();
+        unstage(b, r0);
+        __syncthreads();
+    }
+
+    if (m0 == 0) {   // remove the mean of the m = 0 solution
+        double2 acc = make_double2(0.0, 0.0);
+        for (int i = tid; i < N; i += ST) {
+            double2 x = P[(size_t)i * N + i];
+            acc.x += x.x;
+            acc.y += x.y;
+        }
+        acc = block_sum2(acc, red);
+        const double2 mx = make_double2(acc.x / N, acc.y / N);
+        for (int i = tid; i < N; i += ST) {
+            double2 x = P[(size_t)i * N + i];
+            P[(size_t)i * N + i] = make_double2(x.x - mx.x, x.y - mx.y);
+        }
+    }
+}
+
+int zt_launch_stream_solve(zt_plan* p, const double2* W, double2* P, cudaStream_t s, int gate) {
+    const int N = p->N;
+    const int nb = (N + SD - 1) / SD;
+    stream_solve_kernel<<<nb, ST, SOLVE_SMEM, s>>>(W, P, p->fac_l, p->fac_nd, N, p->state, gate);
+    return launch_check(p, "stream_solve_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point update (Eq. isomp_iter with the products of Sec. 3.1) and the
+// assembly of W_{n+1} (second line of Eq. isomp):
+//   out = base + h/2 (A - A^H) + c2 B,     c2 = +h^2/4 (sweep), -h^2/4 (final)
+// computed on the lower triangle and mirrored (out stays skew-Hermitian; the
+// diagonal keeps its imaginary part only).  With `partials`, each CTA also
+// writes its share of ||out - old||_F^2.  32x32 tiles over the lower triangle.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int UT = 32;
+}
+
+__global__ void __launch_bounds__(256)
+update_kernel(const double2* __restrict__ base, const double2* __restrict__ A,
+              const double2* __restrict__ B, const double2* old, double2* out,
+              double h2, double c2, double* partials, int N,
+              const zt_dev_state* st, int gate) {
+    if (zt_gate_skip(st, gate)) return;
+    __shared__ double2 sAT[UT][UT + 1];
+    __shared__ double2 sOut[UT][UT + 1];
+    __shared__ double sred[256];
+    const int t = blockIdx.x;
+    int bi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while (bi * (bi + 1) / 2 > t) --bi;
+    while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+    const int bj = t - bi * (bi + 1) / 2;
+    const int i0 = bi * UT, j0 = bj * UT;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+
+    for (int q = 0; q < UT / 8; ++q) {   // sAT[jj][ii] = A[j0+jj, i0+ii]
+        const int jj = ty + 8 * q, j = j0 + jj, i = i0 + tx;
+        sAT[jj][tx] = (j < N && i < N) ? A[(size_t)j * N + i] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int q = 0; q < UT / 8; ++q) {
+        const int ii = ty + 8 * q, jj = tx, i = i0 + ii, j = j0 + jj;
+        if (i < N && j < N && i >= j) {
+            const size_t e = (size_t)i * N + j;
+            const double2 a = A[e], at = sAT[jj][ii], bb = B[e], w = base[e];
+            double2 v;
+            v.x = w.x + h2 * (a.x - at.x) + c2 * bb.x;
+            v.y = w.y + h2 * (a.y + at.y) + c2 * bb.y;
+            if (i == j) v.x = 0.0;
+            if (partials) {
+                const double2 o = old[e];
+                const double dx = v.x - o.x, dy = v.y - o.y;
+                acc += (i == j ? 1.0 : 2.0) * (dx * dx + dy * dy);
+            }
+            out[e] = v;
+            sOut[ii][jj] = v;
+        }
+    }
+    __syncthreads();
+    for (int q = 0; q < UT / 8; ++q) {   // mirror: out[j, i] = -conj(out[i, j])
+        const int jj = ty + 8 * q, ii = tx, i = i0 + ii, j = j0 + jj;
+        if (i < N && j < N && i > j) {
+            const double2 v = sOut[ii][jj];
+            out[(size_t)j * N + i] = make_double2(-v.x, v.y);
+        }
+    }
+    if (partials) {
+        sred[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sred[threadIdx.x] += sred[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partials[t] = sred[0];
+    }
+}
+
+// Fixed-order reduction of the residual partials and the stop decision.
+__global__ void converge_kernel(const double* __restrict__ partials, int n, zt_dev_state* st) {
+    if (st->done) return;
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += 256) s += partials[k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double r = sqrt(sh[0]);
+        st->iters += 1;
+        st->residual = r;
+        if (!isfinite(r)) {
+            st->nonfinite = 1;
+            st->done = 1;
+        } else if (r < st->tol) {
+            st->converged = 1;
+            st->done = 1;
+        } else if (st->iters >= st->maxit || st->timeout) {
+            st->done = 1;
+        }
+    }
+}
+
+__global__ void state_init_kernel(zt_dev_state* st, double tol, int maxit) {
+    st->done = 0;
+    st->iters = 0;
+    st->converged = 0;
+    st->nonfinite = 0;
+    st->timeout = 0;
+    st->maxit = maxit;
+    st->residual = 0.0;
+    st->tol = tol;
+}
+
+static int launch_update(zt_plan* p, const double2* base, const double2* old, double2* out,
+                         double h, double sign_b, bool resid, cudaStream_t s, int gate) {
+    const int N = p->N;
+    const int nt = (N + UT - 1) / UT;
+    const int ntiles = nt * (nt + 1) / 2;
+    update_kernel<<<ntiles, 256, 0, s>>>(base, p->A, p->B, old, out, h / 2.0, sign_b * h * h / 4.0,
+                                         resid ? p->partials : nullptr, N, p->state, gate);
+    return launch_check(p, "update_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+static int zgemm(zt_plan* p, const double2* X, const double2* Y, double2* C, double alpha,
+                 int lower_only, cudaStream_t s, int gate) {
+    if (p->precision == ZT_PRECISION_SPLIT)
+        return zt_launch_zgemm_split(p, X, Y, C, alpha, lower_only, s, gate);
+    return zt_launch_zgemm_fp64(p, X, Y, C, alpha, lower_only, s, gate);
+}
+
+extern "C" void zt_plan_destroy(zt_plan* p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    if (p->split) zt_split_destroy(p);
+    cudaFree(p->lap_a);
+    cudaFree(p->lap_b);
+    cudaFree(p->fac_l);
+    cudaFree(p->fac_nd);
+    cudaFree(p->Wn);
+    cudaFree(p->Wt);
+    cudaFree(p->P);
+    cudaFree(p->A);
+    cudaFree(p->B);
+    cudaFree(p->partials);
+    cudaFree(p->state);
+    if (p->h_state) cudaFreeHost(p->h_state);
+    delete p;
+}
+
+extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_plan** out) {
+    if (!out) return zt_fail(ZT_EINVAL, "zt_plan_create: out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > 16384) return zt_fail(ZT_EINVAL, "zt_plan_create: N=%d outside [1, 16384]", N);
+    if (precision != ZT_PRECISION_FP64 && precision != ZT_PRECISION_SPLIT)
+        return zt_fail(ZT_EINVAL, "zt_plan_create: unknown precision %d", precision);
+    zt_plan* p = new (std::nothrow) zt_plan();
+    if (!p) return zt_fail(ZT_ENOMEM, "zt_plan_create: host allocation failed");
+    p->N = N;
+    p->precision = precision;
+    if (opt) p->tun = *opt;
+    if (p->tun.slices == 0) p->tun.slices = 7;
+    if (p->tun.digit_bits == 0) p->tun.digit_bits = 7;
+    if (p->tun.exact_groups == 0) p->tun.exact_groups = 4;
+    if (p->tun.sweeps_per_sync == 0) p->tun.sweeps_per_sync = 4;
+    if (p->tun.final_mode != ZT_FINAL_FRESH && p->tun.final_mode != ZT_FINAL_REUSE) {
+        delete p;
+        return zt_fail(ZT_EINVAL, "zt_plan_create: bad final_mode %d", opt->final_mode);
+    }
+    if (p->tun.sweeps_per_sync < 1 || p->tun.sweeps_per_sync > 64) {
+        delete p;
+        return zt_fail(ZT_EINVAL, "zt_plan_create: sweeps_per_sync outside [1, 64]");
+    }
+    int rc = ZT_OK;
+    auto fail = [&](int code) {
+        zt_plan_destroy(p);
+        return code;
+    };
+#define ZT_TRY(call)                                         \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return fail(zt_cuda_check(_e, #call)); \
+    } while (0)
+    ZT_TRY(cudaGetDevice(&p->device));
+    const size_t ntri = (size_t)N * (N + 1) / 2;
+    const size_t mat = (size_t)N * N * sizeof(double2);
+    ZT_TRY(cudaMalloc(&p->lap_a, ntri * sizeof(double)));
+    ZT_TRY(cudaMalloc(&p->lap_b, ntri * sizeof(double)));
+    ZT_TRY(cudaMalloc(&p->fac_l, ntri * sizeof(double)));
+    ZT_TRY(cudaMalloc(&p->fac_nd, ntri * sizeof(double)));
+    ZT_TRY(cudaMalloc(&p->Wn, mat));
+    ZT_TRY(cudaMalloc(&p->Wt, mat));
+    ZT_TRY(cudaMalloc(&p->P, mat));
+    ZT_TRY(cudaMalloc(&p->A, mat));
+    ZT_TRY(cudaMalloc(&p->B, mat));
+    const int nt = (N + UT - 1) / UT;
+    p->npartials = nt * (nt + 1) / 2;
+    ZT_TRY(cudaMalloc(&p->partials, (size_t)p->npartials * sizeof(double)));
+    ZT_TRY(cudaMalloc(&p->state, sizeof(zt_dev_state)));
+    ZT_TRY(cudaMallocHost(&p->h_state, sizeof(zt_dev_state)));
+    ZT_TRY(cudaMemset(p->state, 0, sizeof(zt_dev_state)));
+    ZT_TRY(cudaFuncSetAttribute(stream_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)SOLVE_SMEM));
+    factor_kernel<<<(N + 127) / 128, 128>>>(N, p->lap_a, p->lap_b, p->fac_l, p->fac_nd);
+    ZT_TRY(cudaGetLastError());
+    p->launches++;
+    if (precision == ZT_PRECISION_SPLIT) {
+        rc = zt_split_create(p);
+        if (rc != ZT_OK) return fail(rc);
+    }
+    ZT_TRY(cudaDeviceSynchronize());
+#undef ZT_TRY
+    *out = p;
+    return ZT_OK;
+}
+
+extern "C" long zt_plan_launch_count(const zt_plan* p) { return p ? p->launches : 0; }
+
+static int check_ptr(const void* ptr, const char* name) {
+    if (!ptr) return zt_fail(ZT_EINVAL, "%s is NULL", name);
+    if (((uintptr_t)ptr & 15u) != 0) return zt_fail(ZT_EINVAL, "%s is not 16-byte aligned", name);
+    return ZT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// public entry points
+// ---------------------------------------------------------------------------
+extern "C" int zeitlin_laplacian_apply(zt_plan* p, const double* P, double* W, void* stream) {
+    if (!p) return zt_fail(ZT_EINVAL, "plan is NULL");
+    int rc;
+    if ((rc = check_ptr(P, "P")) || (rc = check_ptr(W, "W"))) return rc;
+    if (P == W) return zt_fail(ZT_EINVAL, "W must not alias P");
+    return zt_launch_laplacian(p, (const double2*)P, (double2*)W, (cudaStream_t)stream);
+}
+
+extern "C" int zeitlin_stream_solve(zt_plan* p, const double* W, double* P, void* stream) {
+    if (!p) return zt_fail(ZT_EINVAL, "plan is NULL");
+    int rc;
+    if ((rc = check_ptr(P, "P")) || (rc = check_ptr(W, "W"))) return rc;
+    if (P == W) return zt_fail(ZT_EINVAL, "P must not alias W");
+    return zt_launch_stream_solve(p, (const double2*)W, (double2*)P, (cudaStream_t)stream, ZT_GATE_NONE);
+}
+
+extern "C" int zt_zgemm_skew(zt_plan* p, const double* X, const double* Y, double* C, void* stream) {
+    if (!p) return zt_fail(ZT_EINVAL, "plan is NULL");
+    int rc;
+    if ((rc = check_ptr(X, "X")) || (rc = check_ptr(Y, "Y")) || (rc = check_ptr(C, "C"))) return rc;
+    if (C == X || C == Y) return zt_fail(ZT_EINVAL, "C must not alias X or Y");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->precision == ZT_PRECISION_SPLIT) {
+        ZT_CU(cudaMemsetAsync(p->state, 0, sizeof(zt_dev_state), s));
+        rc = zgemm(p, (const double2*)X, (const double2*)Y, (double2*)C, -1.0, 0, s, ZT_GATE_NONE);
+        if (rc) return rc;
+        ZT_CU(cudaMemcpyAsync(p->h_state, p->state, sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
+        ZT_CU(cudaStreamSynchronize(s));
+        if (p->h_state->timeout) return zt_fail(ZT_ETIMEOUT, "zt_zgemm_skew: bounded device wait ran out");
+        return ZT_OK;
+    }
+    return zgemm(p, (const double2*)X, (const double2*)Y, (double2*)C, -1.0, 0, s, ZT_GATE_NONE);
+}
+
+// One fixed-point sweep (Eq. isomp_iter): Pt = solve(Wt), A = Pt Wt,
+// B = A Pt, Wt <- W_n + h/2 (A - A^H) + h^2/4 B, residual, stop decision.
+static int enqueue_sweep(zt_plan* p, double h, cudaStream_t s) {
+    int rc;
+    if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, ZT_GATE_SWEEP))) return rc;
+    if ((rc = zgemm(p, p->P, p->Wt, p->A, -1.0, 0, s, ZT_GATE_SWEEP))) return rc;   // A = Pt Wt
+    if ((rc = zgemm(p, p->A, p->P, p->B, -1.0, 1, s, ZT_GATE_SWEEP))) return rc;    // B = A Pt (lower half)
+    if ((rc = launch_update(p, p->Wn, p->Wt, p->Wt, h, +1.0, true, s, ZT_GATE_SWEEP))) return rc;
+    converge_kernel<<<1, 256, 0, s>>>(p->partials, p->npartials, p->state);
+    return launch_check(p, "converge_kernel");
+}
+
+// Second line of Eq. isomp; runs only once the sweeps are done.
+static int enqueue_final(zt_plan* p, double2* W, double h, cudaStream_t s) {
+    int rc;
+    if (p->tun.final_mode == ZT_FINAL_FRESH) {
+        if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, ZT_GATE_FINAL))) return rc;
+        if ((rc = zgemm(p, p->P, p->Wt, p->A, -1.0, 0, s, ZT_GATE_FINAL))) return rc;
+        if ((rc = zgemm(p, p->A, p->P, p->B, -1.0, 1, s, ZT_GATE_FINAL))) return rc;
+    }
+    return launch_update(p, p->Wt, nullptr, W, h, -1.0, false, s, ZT_GATE_FINAL);
+}
+
+static int step_impl(zt_plan* p, double2* W, double h, double tol, int maxit, zt_step_stats* stats,
+                     cudaStream_t s) {
+    const size_t mat = (size_t)p->N * p->N * sizeof(double2);
+    ZT_CU(cudaMemcpyAsync(p->Wn, W, mat, cudaMemcpyDeviceToDevice, s));
+    ZT_CU(cudaMemcpyAsync(p->Wt, W, mat, cudaMemcpyDeviceToDevice, s));
+    state_init_kernel<<<1, 1, 0, s>>>(p->state, tol, maxit);
+    int rc = launch_check(p, "state_init_kernel");
+    if (rc) return rc;
+    int enq = 0;
+    for (;;) {
+        const int chunk = p->tun.sweeps_per_sync;
+        for (int c = 0; c < chunk && enq < maxit; ++c, ++enq)
+            if ((rc = enqueue_sweep(p, h, s))) return rc;
+        if ((rc = enqueue_final(p, W, h, s))) return rc;
+        ZT_CU(cudaMemcpyAsync(p->h_state, p->state, sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
+        ZT_CU(cudaStreamSynchronize(s));
+        if (p->h_state->done) break;
+        if (enq >= maxit) return zt_fail(ZT_ECUDA, "isomp_step: state not done after maxit sweeps");
+    }
+    const zt_dev_state& hs = *p->h_state;
+    if (stats) {
+        stats->iters = hs.iters;
+        stats->converged = hs.converged;
+        stats->residual = hs.residual;
+    }
+    if (hs.timeout) return zt_fail(ZT_ETIMEOUT, "isomp_step: a bounded device wait ran out");
+    if (hs.nonfinite) return zt_fail(ZT_ENONFINITE, "isomp_step: residual is not finite");
+    if (!hs.converged)
+        return zt_fail(ZT_NOT_CONVERGED, "isomp_step: no convergence in %d sweeps (residual %.3e)",
+                       hs.iters, hs.residual);
+    return ZT_OK;
+}
+
+static int check_step_args(zt_plan* p, const double* W, double h, double tol, int maxit) {
+    if (!p) return zt_fail(ZT_EINVAL, "plan is NULL");
+    int rc;
+    if ((rc = check_ptr(W, "W"))) return rc;
+    if (!std::isfinite(h)) return zt_fail(ZT_EINVAL, "h is not finite");
+    if (!(tol >= 0.0)) return zt_fail(ZT_EINVAL, "tol must be >= 0");
+    if (maxit < 1 || maxit > 100000) return zt_fail(ZT_EINVAL, "maxit outside [1, 100000]");
+    return ZT_OK;
+}
+
+extern "C" int isomp_step(zt_plan* p, double* W, double h, double tol, int maxit, zt_step_stats* stats,
+                          void* stream) {
+    int rc = check_step_args(p, W, h, tol, maxit);
+    if (rc) return rc;
+    return step_impl(p, (double2*)W, h, tol, maxit, stats, (cudaStream_t)stream);
+}
+
+extern "C" int isomp_run(zt_plan* p, double* W, double h, long nsteps, double tol, int maxit,
+                         zt_run_stats* stats, void* stream) {
+    int rc = check_step_args(p, W, h, tol, maxit);
+    if (rc) return rc;
+    if (nsteps < 0) return zt_fail(ZT_EINVAL, "nsteps < 0");
+    zt_run_stats tot{};
+    tot.all_converged = 1;
+    int worst = ZT_OK;
+    for (long n = 0; n < nsteps; ++n) {
+        zt_step_stats st{};
+        rc = step_impl(p, (double2*)W, h, tol, maxit, &st, (cudaStream_t)stream);
+        if (rc < 0) {
+            if (stats) *stats = tot;
+            return rc;
+        }
+        if (rc == ZT_NOT_CONVERGED) worst = ZT_NOT_CONVERGED;
+        tot.steps++;
+        tot.total_iters += st.iters;
+        if (st.iters > tot.max_iters) tot.max_iters = st.iters;
+        if (!st.converged) tot.all_converged = 0;
+        if (st.residual > tot.max_residual) tot.max_residual = st.residual;
+    }
+    if (stats) *stats = tot;
+    if (worst) return zt_fail(worst, "isomp_run: some steps did not converge");
+    return ZT_OK;
+}

@@ -1,0 +1,185 @@
+"""Thin ctypes binding of libzeitlin (argument marshalling only).
+
+Every operation runs in the library's CUDA kernels; this module only passes
+device pointers, sizes and the current CUDA stream.  Tensors are torch
+complex128, contiguous, on a CUDA device (PyTorch supplies device memory and
+streams).  There is no CPU fallback: if the shared library is missing or a
+call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+ZT_OK = 0
+ZT_NOT_CONVERGED = 1
+ZT_EINVAL = -1
+ZT_ENOMEM = -2
+ZT_ECUDA = -3
+ZT_ENONFINITE = -4
+ZT_ETIMEOUT = -5
+PRECISION_FP64 = 0
+PRECISION_SPLIT = 1
+FINAL_FRESH = 0
+FINAL_REUSE = 1
+
+HEADER = os.path.join(_build.ROOT, "include", "zeitlin.h")
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("slices", ctypes.c_int), ("digit_bits", ctypes.c_int), ("exact_groups", ctypes.c_int),
+                ("final_mode", ctypes.c_int), ("sweeps_per_sync", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("converged", ctypes.c_int), ("residual", ctypes.c_double)]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_long), ("total_iters", ctypes.c_long), ("max_iters", ctypes.c_int),
+                ("all_converged", ctypes.c_int), ("max_residual", ctypes.c_double)]
+
+
+class ZeitlinError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libzeitlin status {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/zeitlin.h declares."""
+    txt = open(HEADER).read()
+    return re.findall(r"^ZT_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt, flags=re.M)
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libzeitlin.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and _build.is_stale():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libzeitlin.so not found at {_build.LIB}; run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i, d, l = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_long
+    L.zt_plan_create.argtypes = [i, i, ctypes.POINTER(Tuning), ctypes.POINTER(vp)]
+    L.zt_plan_create.restype = i
+    L.zt_plan_destroy.argtypes = [vp]
+    L.zt_plan_destroy.restype = None
+    L.zt_last_error.argtypes = []
+    L.zt_last_error.restype = ctypes.c_char_p
+    L.zeitlin_laplacian_apply.argtypes = [vp, vp, vp, vp]
+    L.zeitlin_laplacian_apply.restype = i
+    L.zeitlin_stream_solve.argtypes = [vp, vp, vp, vp]
+    L.zeitlin_stream_solve.restype = i
+    L.isomp_step.argtypes = [vp, vp, d, d, i, ctypes.POINTER(StepStats), vp]
+    L.isomp_step.restype = i
+    L.isomp_run.argtypes = [vp, vp, d, l, d, i, ctypes.POINTER(RunStats), vp]
+    L.isomp_run.restype = i
+    L.zt_zgemm_skew.argtypes = [vp, vp, vp, vp, vp]
+    L.zt_zgemm_skew.restype = i
+    L.zt_plan_launch_count.argtypes = [vp]
+    L.zt_plan_launch_count.restype = l
+    _lib = L
+    return L
+
+
+def _check(rc, allow=(ZT_OK,)):
+    if rc not in allow:
+        raise ZeitlinError(rc, load().zt_last_error().decode())
+    return rc
+
+
+def _ptr(t, N):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda:
+        raise TypeError("expected a complex128 CUDA tensor")
+    if tuple(t.shape) != (N, N) or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous ({N}, {N}) tensor, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A zt_plan: constant Laplacian factors plus step workspace for one N."""
+
+    def __init__(self, N: int, precision: int = PRECISION_FP64, slices=0, digit_bits=0,
+                 exact_groups=0, final_mode=FINAL_FRESH, sweeps_per_sync=0):
+        L = load()
+        self.N = int(N)
+        self.precision = precision
+        tun = Tuning(slices, digit_bits, exact_groups, final_mode, sweeps_per_sync)
+        h = ctypes.c_void_p()
+        _check(L.zt_plan_create(self.N, precision, ctypes.byref(tun), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().zt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        return load().zt_plan_launch_count(self._h)
+
+
+def zeitlin_laplacian_apply(plan: Plan, P, W, stream=None):
+    _check(load().zeitlin_laplacian_apply(plan.handle, _ptr(P, plan.N), _ptr(W, plan.N), _stream(stream)))
+    return W
+
+
+def zeitlin_stream_solve(plan: Plan, W, P, stream=None):
+    _check(load().zeitlin_stream_solve(plan.handle, _ptr(W, plan.N), _ptr(P, plan.N), _stream(stream)))
+    return P
+
+
+def isomp_step(plan: Plan, W, h: float, tol: float = 1e-12, maxit: int = 50, stream=None,
+               allow_not_converged: bool = False):
+    st = StepStats()
+    allow = (ZT_OK, ZT_NOT_CONVERGED) if allow_not_converged else (ZT_OK,)
+    rc = _check(load().isomp_step(plan.handle, _ptr(W, plan.N), float(h), float(tol), int(maxit),
+                                  ctypes.byref(st), _stream(stream)), allow)
+    return {"status": rc, "iters": st.iters, "converged": bool(st.converged), "residual": st.residual}
+
+
+def isomp_run(plan: Plan, W, h: float, nsteps: int, tol: float = 1e-12, maxit: int = 50, stream=None,
+              allow_not_converged: bool = False):
+    st = RunStats()
+    allow = (ZT_OK, ZT_NOT_CONVERGED) if allow_not_converged else (ZT_OK,)
+    rc = _check(load().isomp_run(plan.handle, _ptr(W, plan.N), float(h), int(nsteps), float(tol), int(maxit),
+                                 ctypes.byref(st), _stream(stream)), allow)
+    return {"status": rc, "steps": st.steps, "total_iters": st.total_iters, "max_iters": st.max_iters,
+            "all_converged": bool(st.all_converged), "max_residual": st.max_residual}
+
+
+def zt_zgemm_skew(plan: Plan, X, Y, C, stream=None):
+    _check(load().zt_zgemm_skew(plan.handle, _ptr(X, plan.N), _ptr(Y, plan.N), _ptr(C, plan.N),
+                                _stream(stream)))
+    return C

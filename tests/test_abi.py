@@ -1,0 +1,47 @@
+"""The C-ABI library builds for sm_103a, loads, and exports what include/zeitlin.h declares (CPU only)."""
+import ctypes
+import subprocess
+
+import pytest
+
+from paper_2206_05466_gb300 import build as B
+from paper_2206_05466_gb300 import zeitlin as z
+
+
+def test_header_declares_the_boundary():
+    names = set(z.declared_functions())
+    for want in ("zeitlin_laplacian_apply", "zeitlin_stream_solve", "isomp_step", "isomp_run",
+                 "zt_plan_create", "zt_plan_destroy", "zt_last_error", "zt_zgemm_skew"):
+        assert want in names, want
+
+
+def test_library_builds_loads_and_exports_every_declared_symbol():
+    path = B.build()
+    L = ctypes.CDLL(path)
+    for name in z.declared_functions():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
+    assert exported == set(z.declared_functions()), exported ^ set(z.declared_functions())
+
+
+def test_no_compute_without_gpu_reports_an_error():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    L = z.load()
+    h = ctypes.c_void_p()
+    rc = L.zt_plan_create(8, 0, None, ctypes.byref(h))
+    assert rc < 0 and not h.value
+    assert len(L.zt_last_error()) > 0
+
+
+def test_argument_validation_on_host():
+    L = z.load()
+    h = ctypes.c_void_p()
+    assert L.zt_plan_create(0, 0, None, ctypes.byref(h)) == z.ZT_EINVAL
+    assert L.zt_plan_create(8, 7, None, ctypes.byref(h)) == z.ZT_EINVAL
+    assert L.zt_plan_create(8, 0, None, None) == z.ZT_EINVAL
+    assert L.zeitlin_stream_solve(None, None, None, None) == z.ZT_EINVAL
+    assert L.isomp_step(None, None, 0.01, 1e-12, 50, None, None) == z.ZT_EINVAL
