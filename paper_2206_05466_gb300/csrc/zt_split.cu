@@ -1,15 +1,621 @@
-// Split-precision complex product on tcgen05 (placeholder until the kernel lands).
+// Split-precision complex product on the 5th-generation tensor cores (tcgen05).
+//
+// C = alpha * X conj(Y)^T (= alpha' X Y for Y in su(N), Sec. 3.1), emulating
+// the FP64 product with BF16 digit slices (an error-free splitting in the
+// spirit of Ozaki, Ogita, Oishi & Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59 (2012)):
+//
+//  1. Real formulation.  With X' the N x 2N real matrix of X's interleaved
+//     (re, im) rows, and B'^T the 2N x 2N real matrix whose rows 2j, 2j+1
+//     are interleaved(Y[j,:]) and interleaved(i Y[j,:]), the real and
+//     imaginary parts of sum_k X[i,k] conj(Y[j,k]) are the dot products of
+//     row i of X' with rows 2j and 2j+1 of B'^T, so the interleaved complex
+//     result is C' = X' B' (one real product, K' = 2N).
+//  2. Splitting.  Each row r of X' (and of B'^T) gets an exponent e_r with
+//     max|row| < 2^e_r; every entry becomes the integer
+//     round(x 2^(s*beta - 1 - e_r)) written in s balanced base-2^beta digits
+//     d_0 .. d_{s-1} (|d| <= 2^(beta-1), exact in BF16).  All integer work.
+//  3. Products.  Digit planes are multiplied on tcgen05 (kind::f16, BF16 in,
+//     FP32 accumulate in TMEM).  Pairs (p, q) with the same g = p + q share a
+//     weight, so they accumulate into one TMEM buffer; pairs with g >= s are
+//     dropped (triangular truncation).  The leading `exact_groups` groups are
+//     accumulated over K chunks short enough that every FP32 partial sum is an
+//     exact integer (< 2^24); the rest run over the whole K.
+//  4. Recombination.  Each drained TMEM buffer is converted to int64 and
+//     added, shifted by its weight, into an int64 fixed-point accumulator
+//     held in the output buffer itself; the last step scales it back to FP64.
+//
+// Kernel structure (one 128 x 256 output tile per CTA, 192 threads):
+//   warp 0  TMA producer: digit tiles (128 x 64 of X', 256 x 64 of B'^T,
+//           128-byte swizzle) into a 4-stage shared-memory ring;
+//   warp 1  TMEM allocation and the single MMA-issuing thread;
+//   warps 2-5  drain TMEM (double-buffered accumulator) into the int64
+//           accumulator, then the FP64 epilogue.
+// Every mbarrier wait is bounded by a wall-clock limit; on expiry the kernel
+// records a timeout in the step state, lets in-flight work retire and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
 #include "zt_internal.h"
 
-int zt_split_create(zt_plan* p) {
-    (void)p;
-    return zt_fail(ZT_EINVAL, "ZT_PRECISION_SPLIT is not available in this build");
+namespace {
+constexpr int BM = 128;            // tile rows (X' rows)
+constexpr int BN = 256;            // tile cols (B'^T rows = real output columns)
+constexpr int BK = 64;             // K per stage: 64 BF16 = 128 bytes per row
+constexpr int STAGES = 4;
+constexpr int A_TILE = BM * BK * 2;
+constexpr int B_TILE = BN * BK * 2;
+constexpr int STAGE_BYTES = A_TILE + B_TILE;
+constexpr int NTHREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;  // two 128 x 256 FP32 accumulators
+constexpr size_t SMEM_BYTES = 1024 /*align slack*/ + (size_t)STAGES * STAGE_BYTES + 256 /*barriers*/;
+constexpr int EXP_NAN = 0x7fff;    // row exponent marking a non-finite entry
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
+
+// instruction descriptor, kind::f16: D F32, A/B BF16, K-major, M=128, N=256
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
+                           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}  // namespace
+
+struct zt_split_ws {
+    int s = 7, beta = 7, exact_groups = 4;
+    int ldk = 0, Mpad = 0, Npad = 0, u = 0;
+    __nv_bfloat16* dA = nullptr;   // [s][Mpad][ldk]
+    __nv_bfloat16* dB = nullptr;   // [s][Npad][ldk]
+    int* eA = nullptr;             // [Mpad]
+    int* eB = nullptr;             // [Npad]
+    CUtensorMap tmA, tmB;
+};
+
+struct SplitArgs {
+    int N, s, beta, ldk, Mpad, Npad, u, exact_groups, ntn, lower_only;
+    double alpha;
+    const int* eA;
+    const int* eB;
+    double* C;
+    zt_dev_state* st;
+    int gate;
+};
+
+// ---------------------------------------------------------------------------
+// device helpers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false on timeout/abort.
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > WAIT_NS) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms of 1 KiB.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: 8-row atom
+    d |= (uint64_t)1 << 46;                      // descriptor version (sm_100 family)
+    d |= (uint64_t)2 << 61;                      // SWIZZLE_128B
+    return d;
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-void zt_split_destroy(zt_plan* p) { (void)p; }
+// K blocks per accumulation segment of digit group g: short enough that the
+// FP32 sums of the leading groups stay exact integers.
+__device__ __host__ inline int seg_kblocks(int g, int beta, int exact_groups, int nkb) {
+    if (g >= exact_groups) return nkb;
+    // (g+1) * kc * BK * 2^(2 beta - 2) <= 2^24
+    long long lim = (1LL << (26 - 2 * beta)) / ((long long)BK * (g + 1));
+    if (lim < 1) lim = 1;
+    return (int)(lim < nkb ? lim : nkb);
+}
+
+// ---------------------------------------------------------------------------
+// Splitting: one CTA per row of X (complex, N entries).  Writes X' digits
+// (mode A) and/or the two B'^T rows 2j, 2j+1 built from row j (mode B).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long to_fixed(double x, int e, int sb) {
+    const long long bits = __double_as_longlong(x);
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    long long mant = bits & 0xFFFFFFFFFFFFFLL;
+    int ex;
+    if (ef == 0) {
+        ex = -1074;
+    } else {
+        mant |= (1LL << 52);
+        ex = ef - 1075;
+    }
+    const int sh = ex + sb - 1 - e;   // <= sb - 54 for |x| < 2^e
+    long long v;
+    if (sh >= 0)
+        v = mant << sh;
+    else if (sh < -62)
+        v = 0;
+    else
+        v = (mant + (1LL << (-sh - 1))) >> (-sh);
+    return bits < 0 ? -v : v;
+}
+
+__global__ void __launch_bounds__(256)
+split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk,
+                  __nv_bfloat16* __restrict__ dA, int Mpad, int* __restrict__ eA,
+                  __nv_bfloat16* __restrict__ dB, int Npad, int* __restrict__ eB,
+                  const zt_dev_state* st, int gate) {
+    if (zt_gate_skip(st, gate)) return;
+    const int j = blockIdx.x;
+    const double2* row = X + (size_t)j * N;
+    __shared__ int smax[256];
+    int mx = 0;
+    for (int k = threadIdx.x; k < N; k += 256) {
+        const double2 v = row[k];
+        const int e1 = (int)((__double_as_longlong(v.x) >> 52) & 0x7FF);
+        const int e2 = (int)((__double_as_longlong(v.y) >> 52) & 0x7FF);
+        mx = max(mx, max(e1, e2));
+    }
+    smax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) smax[threadIdx.x] = max(smax[threadIdx.x], smax[threadIdx.x + w]);
+        __syncthreads();
+    }
+    mx = smax[0];
+    const bool bad = (mx == 0x7FF);
+    const int e = max(mx, 1) - 1022;   // max |entry| < 2^e
+    const int sb = s * beta;
+    const long long R = 1LL << beta, H = R >> 1;
+    const size_t planeA = (size_t)Mpad * ldk, planeB = (size_t)Npad * ldk;
+    for (int k = threadIdx.x; k < ldk / 2; k += 256) {
+        long long vr = 0, vi = 0;
+        if (k < N && !bad) {
+            const double2 v = row[k];
+            vr = to_fixed(v.x, e, sb);
+            vi = to_fixed(v.y, e, sb);
+        }
+        for (int p = s - 1; p >= 0; --p) {
+            long long dr, di;
+            if (p > 0) {
+                dr = ((vr + H) & (R - 1)) - H;
+                di = ((vi + H) & (R - 1)) - H;
+                vr = (vr - dr) >> beta;
+                vi = (vi - di) >> beta;
+            } else {
+                dr = vr;
+                di = vi;
+            }
+            const float fr = (float)dr, fi = (float)di;
+            if (dA) {
+                __nv_bfloat162 w2 = __floats2bfloat162_rn(fr, fi);
+                *reinterpret_cast<__nv_bfloat162*>(dA + p * planeA + (size_t)j * ldk + 2 * k) = w2;
+            }
+            if (dB) {
+                // row 2j: interleaved(y) ; row 2j+1: interleaved(i y) = (-im, re)
+                __nv_bfloat162 r0 = __floats2bfloat162_rn(fr, fi);
+                __nv_bfloat162 r1 = __floats2bfloat162_rn(-fi, fr);
+                *reinterpret_cast<__nv_bfloat162*>(dB + p * planeB + (size_t)(2 * j) * ldk + 2 * k) = r0;
+                *reinterpret_cast<__nv_bfloat162*>(dB + p * planeB + (size_t)(2 * j + 1) * ldk + 2 * k) = r1;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        const int ee = bad ? EXP_NAN : e;
+        if (eA) eA[j] = ee;
+        if (eB) {
+            eB[2 * j] = ee;
+            eB[2 * j + 1] = ee;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The tcgen05 product kernel.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NTHREADS, 1)
+zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const SplitArgs a) {
+    if (zt_gate_skip(a.st, a.gate)) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = base;
+    uint8_t* sB = base + STAGES * A_TILE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_TILE);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;   // [2]
+    uint64_t* acce = accf + 2;         // [2]
+    uint64_t* drain = acce + 2;        // [1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    // tile coordinates
+    int ti, tj;
+    if (a.lower_only) {
+        const int t = blockIdx.x;
+        int r = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        while (r * (r + 1) / 2 > t) --r;
+        while ((r + 1) * (r + 2) / 2 <= t) ++r;
+        ti = r;
+        tj = t - r * (r + 1) / 2;
+    } else {
+        ti = blockIdx.x / a.ntn;
+        tj = blockIdx.x % a.ntn;
+    }
+    const int i0 = ti * BM, c0 = tj * BN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkb = a.ldk / BK;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&accf[i], 1);
+            mbar_init(&acce[i], 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {   // ---- TMA producer ----
+            int stage = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int g = 0; g < a.s && ok; ++g) {
+                const int kc = seg_kblocks(g, a.beta, a.exact_groups, nkb);
+                for (int kb0 = 0; kb0 < nkb && ok; kb0 += kc) {
+                    const int kend = min(kb0 + kc, nkb);
+                    for (int kb = kb0; kb < kend && ok; ++kb) {
+                        for (int p = 0; p <= g; ++p) {
+                            if (!mbar_wait(&empty[stage], ph ^ 1, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_expect_tx(&full[stage], STAGE_BYTES);
+                            tma_load_2d(sA + stage * A_TILE, &tmA, &full[stage], kb * BK, p * a.Mpad + i0);
+                            tma_load_2d(sB + stage * B_TILE, &tmB, &full[stage], kb * BK, (g - p) * a.Npad + c0);
+                            if (++stage == STAGES) {
+                                stage = 0;
+                                ph ^= 1;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ---- MMA issuer ----
+            int stage = 0, seg = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int g = 0; g < a.s && ok; ++g) {
+                const int kc = seg_kblocks(g, a.beta, a.exact_groups, nkb);
+                for (int kb0 = 0; kb0 < nkb && ok; kb0 += kc, ++seg) {
+                    const int kend = min(kb0 + kc, nkb);
+                    const int b = seg & 1;
+                    if (!mbar_wait(&acce[b], ((seg >> 1) & 1) ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(b * BN);
+                    bool first = true;
+                    for (int kb = kb0; kb < kend && ok; ++kb) {
+                        for (int p = 0; p <= g; ++p) {
+                            if (!mbar_wait(&full[stage], ph, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint64_t ad = sw128_desc(smem_u32(sA + stage * A_TILE));
+                            const uint64_t bd = sw128_desc(smem_u32(sB + stage * B_TILE));
+#pragma unroll
+                            for (int k = 0; k < BK / 16; ++k)
+                                umma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (first && k == 0) ? 0u : 1u);
+                            first = false;
+                            umma_commit(&empty[stage]);
+                            if (++stage == STAGES) {
+                                stage = 0;
+                                ph ^= 1;
+                            }
+                        }
+                    }
+                    if (ok) umma_commit(&accf[b]);
+                }
+            }
+            // all MMAs issued by this thread retire before TMEM is released
+            umma_commit(drain);
+            volatile int dummy = 0;
+            if (!mbar_wait(drain, 0, &dummy)) *abort_flag = 1;
+        }
+    } else {   // ---- drain / epilogue: warps 2..5 ----
+        const int wq = warp & 3;
+        const int row = wq * 32 + lane;
+        const int gi = i0 + row;
+        const int ncols = 2 * a.N;
+        const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
+        long long* Crow = reinterpret_cast<long long*>(a.C) + (size_t)gi * ncols;
+        int seg = 0;
+        bool ok = true;
+        for (int g = 0; g < a.s && ok; ++g) {
+            const int kc = seg_kblocks(g, a.beta, a.exact_groups, nkb);
+            const int sh = (a.s - 1 - g) * a.beta - a.u;
+            for (int kb0 = 0; kb0 < nkb; kb0 += kc, ++seg) {
+                const int b = seg & 1;
+                if (!mbar_wait(&accf[b], (seg >> 1) & 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll 1
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + ch * 32), r);
+                    const int cb = c0 + ch * 32;
+                    if (gi < a.N && cb < ncols) {
+                        long long* dst = Crow + cb;
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int c = cb + 2 * q;
+                            if (c >= ncols) break;
+                            long long v0 = __float2ll_rn(__uint_as_float(r[2 * q]));
+                            long long v1 = __float2ll_rn(__uint_as_float(r[2 * q + 1]));
+                            if (sh >= 0) {
+                                v0 <<= sh;
+                                v1 <<= sh;
+                            } else {
+                                v0 = (v0 + (1LL << (-sh - 1))) >> (-sh);
+                                v1 = (v1 + (1LL << (-sh - 1))) >> (-sh);
+                            }
+                            longlong2* p2 = reinterpret_cast<longlong2*>(dst + 2 * q);
+                            if (seg != 0) {
+                                const longlong2 o = *p2;
+                                v0 += o.x;
+                                v1 += o.y;
+                            }
+                            *p2 = make_longlong2(v0, v1);
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&acce[b]);
+            }
+        }
+        if (ok && gi < a.N) {   // int64 fixed point -> FP64
+            const int ea = a.eA[gi];
+            const int off = -(a.s + 1) * a.beta + 2 + a.u;
+            for (int c = c0; c < c0 + BN && c < ncols; ++c) {
+                const int eb = a.eB[c];
+                const long long v = Crow[c];
+                double out;
+                if (ea == EXP_NAN || eb == EXP_NAN) {
+                    out = __longlong_as_double(0x7ff8000000000000LL);
+                } else {
+                    const int E = ea + eb + off;
+                    double scale = (E >= -1022 && E <= 1023) ? __longlong_as_double((long long)(E + 1023) << 52)
+                                                             : ldexp(1.0, E);
+                    out = (double)v * (scale * a.alpha);
+                }
+                reinterpret_cast<double*>(Crow)[c] = out;
+            }
+        }
+    }
+
+    __syncthreads();
+    if (*abort_flag) {
+        if (threadIdx.x == 0) atomicExch(&a.st->timeout, 1);
+        // give copies still in flight time to land before the CTA exits
+        const unsigned long long t0 = gtimer();
+        while (gtimer() - t0 < 200000ull) {
+        }
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+static int make_map(CUtensorMap* map, void* base, int rows, int ldk, int box_rows) {
+    auto enc = encode_fn();
+    if (!enc) return zt_fail(ZT_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ldk * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return zt_fail(ZT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ZT_OK;
+}
+
+static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+int zt_split_create(zt_plan* p) {
+    const int N = p->N;
+    const int s = p->tun.slices, beta = p->tun.digit_bits, eg = p->tun.exact_groups;
+    if (s < 3 || s > 8) return zt_fail(ZT_EINVAL, "slices=%d outside [3, 8]", s);
+    if (beta < 6 || beta > 8) return zt_fail(ZT_EINVAL, "digit_bits=%d outside [6, 8]", beta);
+    if (eg < 1 || eg > s) return zt_fail(ZT_EINVAL, "exact_groups=%d outside [1, slices]", eg);
+    if (s * beta > 62) return zt_fail(ZT_EINVAL, "slices*digit_bits must be <= 62");
+    zt_split_ws* w = new (std::nothrow) zt_split_ws();
+    if (!w) return zt_fail(ZT_ENOMEM, "host allocation failed");
+    p->split = w;
+    w->s = s;
+    w->beta = beta;
+    w->exact_groups = eg;
+    w->ldk = round_up(2 * N, BK);
+    w->Mpad = round_up(N, BM);
+    w->Npad = round_up(2 * N, BN);
+    // smallest u >= 0 with the worst-case int64 accumulator below 2^62
+    {
+        const double R = std::ldexp(1.0, beta);
+        double bound = 0.0;
+        for (int g = 0; g < s; ++g) bound += (g + 1) * std::pow(R, s - 1 - g);
+        bound *= (double)w->ldk * std::ldexp(1.0, 2 * beta - 2);
+        int u = 0;
+        while (bound >= std::ldexp(1.0, 62 + u)) ++u;
+        w->u = u;
+    }
+    const size_t szA = (size_t)s * w->Mpad * w->ldk * sizeof(__nv_bfloat16);
+    const size_t szB = (size_t)s * w->Npad * w->ldk * sizeof(__nv_bfloat16);
+    ZT_CU(cudaMalloc(&w->dA, szA));
+    ZT_CU(cudaMalloc(&w->dB, szB));
+    ZT_CU(cudaMemset(w->dA, 0, szA));   // padding rows/columns stay zero
+    ZT_CU(cudaMemset(w->dB, 0, szB));
+    ZT_CU(cudaMalloc(&w->eA, (size_t)w->Mpad * sizeof(int)));
+    ZT_CU(cudaMalloc(&w->eB, (size_t)w->Npad * sizeof(int)));
+    ZT_CU(cudaMemset(w->eA, 0, (size_t)w->Mpad * sizeof(int)));
+    ZT_CU(cudaMemset(w->eB, 0, (size_t)w->Npad * sizeof(int)));
+    int rc;
+    if ((rc = make_map(&w->tmA, w->dA, s * w->Mpad, w->ldk, BM))) return rc;
+    if ((rc = make_map(&w->tmB, w->dB, s * w->Npad, w->ldk, BN))) return rc;
+    ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    return ZT_OK;
+}
+
+void zt_split_destroy(zt_plan* p) {
+    zt_split_ws* w = p->split;
+    if (!w) return;
+    cudaFree(w->dA);
+    cudaFree(w->dB);
+    cudaFree(w->eA);
+    cudaFree(w->eB);
+    delete w;
+    p->split = nullptr;
+}
 
 int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double2* C, double alpha,
                           int lower_only, cudaStream_t s, int gate) {
-    (void)p; (void)X; (void)Y; (void)C; (void)alpha; (void)lower_only; (void)s; (void)gate;
-    return zt_fail(ZT_EINVAL, "ZT_PRECISION_SPLIT is not available in this build");
+    zt_split_ws* w = p->split;
+    if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
+    const int N = p->N;
+    split_rows_kernel<<<N, 256, 0, s>>>(X, N, w->s, w->beta, w->ldk, w->dA, w->Mpad, w->eA, nullptr, w->Npad,
+                                        nullptr, p->state, gate);
+    p->launches++;
+    split_rows_kernel<<<N, 256, 0, s>>>(Y, N, w->s, w->beta, w->ldk, nullptr, w->Mpad, nullptr, w->dB, w->Npad,
+                                        w->eB, p->state, gate);
+    p->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "split_rows_kernel");
+    SplitArgs a;
+    a.N = N;
+    a.s = w->s;
+    a.beta = w->beta;
+    a.ldk = w->ldk;
+    a.Mpad = w->Mpad;
+    a.Npad = w->Npad;
+    a.u = w->u;
+    a.exact_groups = w->exact_groups;
+    a.ntn = w->Npad / BN;
+    a.lower_only = lower_only;
+    a.alpha = alpha;
+    a.eA = w->eA;
+    a.eB = w->eB;
+    a.C = reinterpret_cast<double*>(C);
+    a.st = p->state;
+    a.gate = gate;
+    const int ntm = w->Mpad / BM;
+    const int ntiles = lower_only ? ntm * (ntm + 1) / 2 : ntm * a.ntn;
+    zgemm_split_kernel<<<ntiles, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB, a);
+    p->launches++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "zgemm_split_kernel");
+    return ZT_OK;
 }

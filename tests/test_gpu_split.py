@@ -1,0 +1,122 @@
+"""GPU parity of the split-precision (BF16 digit slices on tcgen05) path.
+
+Tolerances: the split product's error is set by the truncation of each
+operand row to s*beta - 1 bits and by the dropped digit pairs, about
+s * 2^-(s*beta - 1) relative to sum_k |x_ik||y_kj|.  With the default
+s = 7, beta = 7 that is ~2e-14; the tests allow 1e-12 relative Frobenius.
+Integer-valued inputs are reproduced bit-exactly (all digit products and
+their FP32 sums are exact).  The IsoMP step in split form is held to 1e-10
+relative Frobenius per step against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_05466_gb300.inputs import vorticity_w0
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2206_05466_gb300 import zeitlin as z  # noqa: E402
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128)).cuda()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _split_plan(N, **kw):
+    return z.Plan(N, z.PRECISION_SPLIT, **kw)
+
+
+def _gemm(plan, X, Y):
+    N = X.shape[0]
+    Cd = torch.full((N, N), float("nan"), dtype=torch.complex128, device="cuda")
+    z.zt_zgemm_skew(plan, _cuda(X), _cuda(Y), Cd)
+    return Cd.cpu().numpy()
+
+
+def _int_su(N, seed, lim=50):
+    rng = np.random.default_rng(seed)
+    a = rng.integers(-lim, lim + 1, (N, N)).astype(np.float64)
+    b = rng.integers(-lim, lim + 1, (N, N)).astype(np.float64)
+    Y = a - a.T + 1j * (b + b.T)          # skew-Hermitian, integer valued
+    return Y
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 64, 128, 129, 200, 256])
+def test_integer_inputs_bit_exact(N):
+    rng = np.random.default_rng(N)
+    X = rng.integers(-60, 61, (N, N)) + 1j * rng.integers(-60, 61, (N, N))
+    Y = _int_su(N, N + 1)
+    got = _gemm(_split_plan(N), X, Y)
+    want = X @ Y
+    assert np.array_equal(got, want), np.abs(got - want).max()
+
+
+@pytest.mark.parametrize("N", [1, 3, 33, 64, 128, 130, 257, 512])
+def test_split_product_accuracy(N):
+    rng = np.random.default_rng(7 + N)
+    X = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    Y = vorticity_w0(N, seed=2)
+    got = _gemm(_split_plan(N), X, Y)
+    want = X @ Y
+    assert _rel(got, want) < 1e-12
+
+
+@pytest.mark.parametrize("s,beta,eg", [(3, 8, 2), (6, 8, 4), (7, 7, 4), (8, 7, 8), (5, 6, 5)])
+def test_split_tunings(s, beta, eg):
+    # short exact chunks (beta = 8) force many accumulator drains per tile
+    N = 1024
+    rng = np.random.default_rng(s * 100 + beta)
+    X = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    Y = vorticity_w0(N, seed=3)
+    got = _gemm(_split_plan(N, slices=s, digit_bits=beta, exact_groups=eg), X, Y)
+    want = X @ Y
+    bound = 4.0 * s * 2.0 ** (-(s * beta - 1)) * np.sqrt(N)   # loose a-priori bound, relative
+    assert _rel(got, want) < max(bound, 1e-13)
+    Xi = rng.integers(-60, 61, (N, N)) + 0j
+    Yi = _int_su(N, 5)
+    assert np.array_equal(_gemm(_split_plan(N, slices=s, digit_bits=beta, exact_groups=eg), Xi, Yi), Xi @ Yi)
+
+
+def test_split_nonfinite_propagates():
+    N = 64
+    X = np.ones((N, N), complex)
+    X[3, 5] = np.inf
+    Y = vorticity_w0(N, seed=1)
+    got = _gemm(_split_plan(N), X, Y)
+    assert np.all(np.isnan(got[3]))
+    assert np.all(np.isfinite(np.delete(got, 3, axis=0)))
+
+
+def test_isomp_trajectory_split_n64():
+    N, h, steps = 64, 0.01, 100
+    W0 = vorticity_w0(N, seed=0)
+    plan = _split_plan(N)
+    Wd = _cuda(W0)
+    Wo = W0.copy()
+    worst = 0.0
+    for n in range(steps):
+        z.isomp_step(plan, Wd, h)
+        Wo, _ = oracle.isomp_step(Wo, h)
+        err = _rel(Wd.cpu().numpy(), Wo)
+        worst = max(worst, err)
+        assert err <= 1e-10, (n, err)
+    print(f"split N=64 worst per-step relative error {worst:.3e}")
+
+
+def test_isomp_split_n1024_first_steps():
+    N, h = 1024, 0.01
+    W0 = vorticity_w0(N, seed=0)
+    plan = _split_plan(N)
+    Wd = _cuda(W0)
+    Wo = W0
+    for n in range(2):
+        info = z.isomp_step(plan, Wd, h)
+        Wo, oi = oracle.isomp_step(Wo, h)
+        assert info["converged"]
+        assert _rel(Wd.cpu().numpy(), Wo) <= 1e-10
