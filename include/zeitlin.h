@@ -133,6 +133,29 @@ ZT_API int zt_zgemm_skew(zt_plan* plan, const double* X, const double* Y, double
  * (every launch of every entry point on this plan). */
 ZT_API long zt_plan_launch_count(const zt_plan* plan);
 
+/* Measurement hook (no counterpart in the paper).  When enabled, the library
+ * records a CUDA event pair on the launching stream around every launch of
+ * the kernel classes below, and sums, per class, the elapsed time and the
+ * algorithmic work of the launches that did work (sweeps skipped after
+ * convergence are not counted).  Work units: ZT_KERNEL_PRODUCT -- tensor
+ * FLOPs issued (SPLIT: BF16 digit-pair products over the computed tiles;
+ * FP64: 8 flops per complex multiply-add over the computed tiles) and, in
+ * work_alg, FP64-equivalent FLOPs of the complex product (8 N^3 for a full
+ * product, 4 N^2 (N+1) for the lower triangle); ZT_KERNEL_SOLVE -- bytes
+ * (lower triangle of W read, all of P written: 8 N (N+1) + 16 N^2);
+ * ZT_KERNEL_SPLIT -- bytes read and written; ZT_KERNEL_UPDATE -- bytes.
+ * zt_plan_set_timing(plan, 1) also clears the sums. */
+#define ZT_KERNEL_PRODUCT 0
+#define ZT_KERNEL_SOLVE   1
+#define ZT_KERNEL_SPLIT   2
+#define ZT_KERNEL_UPDATE  3
+#define ZT_KERNEL_KINDS   4
+ZT_API int zt_plan_set_timing(zt_plan* plan, int enable);
+/* Totals for one kernel class since timing was enabled; synchronises on the
+ * recorded events.  Any output pointer may be NULL. */
+ZT_API int zt_plan_kernel_time(zt_plan* plan, int kind, long* launches, double* total_ms,
+                               double* work, double* work_alg);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,14 @@ int zt_launch_zgemm_fp64(zt_plan* p, const double2* X, const double2* Y, double2
                          int lower_only, cudaStream_t s, int gate) {
     const int N = p->N;
     dim3 grid((N + BN - 1) / BN, (N + BM - 1) / BM);
+    // work: FP64 flops over the computed tiles; FP64-equivalent algorithmic flops
+    double tiles = (double)grid.x * grid.y;
+    if (lower_only) tiles = 0.5 * grid.y * (grid.y + 1.0);
+    const double work = tiles * BM * BN * 8.0 * (double)N;
+    const double alg = lower_only ? 4.0 * N * (double)N * (N + 1.0) : 8.0 * (double)N * N * N;
+    const int t = zt_timer_begin(p, ZT_KERNEL_PRODUCT, work, alg, s);
     zgemm_fp64_kernel<<<grid, NT, 0, s>>>(X, Y, C, alpha, N, lower_only, p->state, gate);
+    zt_timer_end(p, t, s);
     p->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "zgemm_fp64_kernel");

@@ -44,6 +44,16 @@ __host__ __device__ inline size_t zt_tri(int r, int c) {
 
 struct zt_split_ws;   // split-precision workspace (zt_split.cu)
 
+// One timed launch (measurement hook).
+struct zt_timer_rec {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int kind = 0;
+    int sweep = -1;       // sweep index inside a step, ZT_SWEEP_FINAL, or -1 outside a step
+    double work = 0.0;
+    double work_alg = 0.0;
+};
+constexpr int ZT_SWEEP_FINAL = 1 << 30;
+
 struct zt_plan {
     int N = 0;
     int precision = 0;
@@ -67,7 +77,22 @@ struct zt_plan {
     zt_dev_state* h_state = nullptr;   // pinned host mirror
     zt_split_ws* split = nullptr;
     long launches = 0;
+    // measurement hook
+    int timing = 0;
+    int cur_sweep = -1;
+    zt_timer_rec* recs = nullptr;
+    int nrecs = 0, caprecs = 0;
+    long t_n[ZT_KERNEL_KINDS] = {0, 0, 0, 0};
+    double t_ms[ZT_KERNEL_KINDS] = {0, 0, 0, 0};
+    double t_work[ZT_KERNEL_KINDS] = {0, 0, 0, 0};
+    double t_work_alg[ZT_KERNEL_KINDS] = {0, 0, 0, 0};
 };
+
+// Measurement hook: bracket a launch with events when timing is enabled.
+int zt_timer_begin(zt_plan* p, int kind, double work, double work_alg, cudaStream_t s);
+void zt_timer_end(zt_plan* p, int idx, cudaStream_t s);
+// Fold finished records into the totals; iters >= 0 drops sweeps >= iters.
+int zt_timer_collect(zt_plan* p, int iters);
 
 // ---- error handling ---------------------------------------------------------
 int zt_fail(int code, const char* fmt, ...);

@@ -38,6 +38,79 @@ static int launch_check(zt_plan* p, const char* what) {
 }
 
 // ---------------------------------------------------------------------------
+// measurement hook
+// ---------------------------------------------------------------------------
+int zt_timer_begin(zt_plan* p, int kind, double work, double work_alg, cudaStream_t s) {
+    if (!p->timing) return -1;
+    if (p->nrecs == p->caprecs) {
+        const int cap = p->caprecs ? 2 * p->caprecs : 64;
+        zt_timer_rec* n = new (std::nothrow) zt_timer_rec[cap];
+        if (!n) return -1;
+        for (int i = 0; i < p->caprecs; ++i) n[i] = p->recs[i];
+        delete[] p->recs;
+        p->recs = n;
+        p->caprecs = cap;
+    }
+    zt_timer_rec& r = p->recs[p->nrecs];
+    if (!r.a && cudaEventCreate(&r.a) != cudaSuccess) return -1;
+    if (!r.b && cudaEventCreate(&r.b) != cudaSuccess) return -1;
+    r.kind = kind;
+    r.sweep = p->cur_sweep;
+    r.work = work;
+    r.work_alg = work_alg;
+    cudaEventRecord(r.a, s);
+    return p->nrecs++;
+}
+
+void zt_timer_end(zt_plan* p, int idx, cudaStream_t s) {
+    if (idx >= 0) cudaEventRecord(p->recs[idx].b, s);
+}
+
+static int timer_collect(zt_plan* p, int iters, int final_tag) {
+    for (int i = 0; i < p->nrecs; ++i) {
+        zt_timer_rec& r = p->recs[i];
+        const bool count = (r.sweep < 0) || (r.sweep < iters) || (r.sweep == final_tag) || iters < 0;
+        ZT_CU(cudaEventSynchronize(r.b));
+        if (!count) continue;
+        float ms = 0.f;
+        ZT_CU(cudaEventElapsedTime(&ms, r.a, r.b));
+        p->t_n[r.kind]++;
+        p->t_ms[r.kind] += ms;
+        p->t_work[r.kind] += r.work;
+        p->t_work_alg[r.kind] += r.work_alg;
+    }
+    p->nrecs = 0;
+    return ZT_OK;
+}
+
+int zt_timer_collect(zt_plan* p, int iters) { return timer_collect(p, iters, -2); }
+
+extern "C" int zt_plan_set_timing(zt_plan* p, int enable) {
+    if (!p) return zt_fail(ZT_EINVAL, "plan is NULL");
+    int rc = timer_collect(p, -1, -2);
+    if (rc) return rc;
+    p->timing = enable ? 1 : 0;
+    for (int k = 0; k < ZT_KERNEL_KINDS; ++k) {
+        p->t_n[k] = 0;
+        p->t_ms[k] = p->t_work[k] = p->t_work_alg[k] = 0.0;
+    }
+    return ZT_OK;
+}
+
+extern "C" int zt_plan_kernel_time(zt_plan* p, int kind, long* launches, double* total_ms, double* work,
+                                   double* work_alg) {
+    if (!p) return zt_fail(ZT_EINVAL, "plan is NULL");
+    if (kind < 0 || kind >= ZT_KERNEL_KINDS) return zt_fail(ZT_EINVAL, "bad kernel kind %d", kind);
+    int rc = timer_collect(p, -1, -2);
+    if (rc) return rc;
+    if (launches) *launches = p->t_n[kind];
+    if (total_ms) *total_ms = p->t_ms[kind];
+    if (work) *work = p->t_work[kind];
+    if (work_alg) *work_alg = p->t_work_alg[kind];
+    return ZT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Constant per-diagonal data (Sec. 3.2, Eq. delta_tria) and LDL^T factors.
 // One thread per diagonal m; entries go to packed lower-triangular arrays at
 // (r, c) = (i + m, i).  For m = 0 only the leading N-1 equations are factored
@@ -302,7 +375,10 @@ stream_solve_kernel(const double2* __restrict__ W, double2* __restrict__ P,
 int zt_launch_stream_solve(zt_plan* p, const double2* W, double2* P, cudaStream_t s, int gate) {
     const int N = p->N;
     const int nb = (N + SD - 1) / SD;
+    const double bytes = 8.0 * N * (N + 1.0) + 16.0 * N * N;
+    const int t = zt_timer_begin(p, ZT_KERNEL_SOLVE, bytes, bytes, s);
     stream_solve_kernel<<<nb, ST, SOLVE_SMEM, s>>>(W, P, p->fac_l, p->fac_nd, N, p->state, gate);
+    zt_timer_end(p, t, s);
     return launch_check(p, "stream_solve_kernel");
 }
 
@@ -422,8 +498,13 @@ static int launch_update(zt_plan* p, const double2* base, const double2* old, do
     const int N = p->N;
     const int nt = (N + UT - 1) / UT;
     const int ntiles = nt * (nt + 1) / 2;
+    // lower triangle: base, A, A^T, B (+ old) read, out written twice
+    const double tri = 16.0 * N * (N + 1.0) / 2.0;
+    const double bytes = tri * ((resid ? 5.0 : 4.0) + 2.0);
+    const int t = zt_timer_begin(p, ZT_KERNEL_UPDATE, bytes, bytes, s);
     update_kernel<<<ntiles, 256, 0, s>>>(base, p->A, p->B, old, out, h / 2.0, sign_b * h * h / 4.0,
                                          resid ? p->partials : nullptr, N, p->state, gate);
+    zt_timer_end(p, t, s);
     return launch_check(p, "update_kernel");
 }
 
@@ -453,6 +534,11 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     cudaFree(p->partials);
     cudaFree(p->state);
     if (p->h_state) cudaFreeHost(p->h_state);
+    for (int i = 0; i < p->caprecs; ++i) {
+        if (p->recs[i].a) cudaEventDestroy(p->recs[i].a);
+        if (p->recs[i].b) cudaEventDestroy(p->recs[i].b);
+    }
+    delete[] p->recs;
     delete p;
 }
 
@@ -569,25 +655,30 @@ extern "C" int zt_zgemm_skew(zt_plan* p, const double* X, const double* Y, doubl
 
 // One fixed-point sweep (Eq. isomp_iter): Pt = solve(Wt), A = Pt Wt,
 // B = A Pt, Wt <- W_n + h/2 (A - A^H) + h^2/4 B, residual, stop decision.
-static int enqueue_sweep(zt_plan* p, double h, cudaStream_t s) {
+static int enqueue_sweep(zt_plan* p, int k, double h, cudaStream_t s) {
     int rc;
+    p->cur_sweep = k;
     if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, ZT_GATE_SWEEP))) return rc;
     if ((rc = zgemm(p, p->P, p->Wt, p->A, -1.0, 0, s, ZT_GATE_SWEEP))) return rc;   // A = Pt Wt
     if ((rc = zgemm(p, p->A, p->P, p->B, -1.0, 1, s, ZT_GATE_SWEEP))) return rc;    // B = A Pt (lower half)
     if ((rc = launch_update(p, p->Wn, p->Wt, p->Wt, h, +1.0, true, s, ZT_GATE_SWEEP))) return rc;
     converge_kernel<<<1, 256, 0, s>>>(p->partials, p->npartials, p->state);
+    p->cur_sweep = -1;
     return launch_check(p, "converge_kernel");
 }
 
 // Second line of Eq. isomp; runs only once the sweeps are done.
-static int enqueue_final(zt_plan* p, double2* W, double h, cudaStream_t s) {
+static int enqueue_final(zt_plan* p, int tag, double2* W, double h, cudaStream_t s) {
     int rc;
+    p->cur_sweep = tag;
     if (p->tun.final_mode == ZT_FINAL_FRESH) {
         if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, ZT_GATE_FINAL))) return rc;
         if ((rc = zgemm(p, p->P, p->Wt, p->A, -1.0, 0, s, ZT_GATE_FINAL))) return rc;
         if ((rc = zgemm(p, p->A, p->P, p->B, -1.0, 1, s, ZT_GATE_FINAL))) return rc;
     }
-    return launch_update(p, p->Wt, nullptr, W, h, -1.0, false, s, ZT_GATE_FINAL);
+    rc = launch_update(p, p->Wt, nullptr, W, h, -1.0, false, s, ZT_GATE_FINAL);
+    p->cur_sweep = -1;
+    return rc;
 }
 
 static int step_impl(zt_plan* p, double2* W, double h, double tol, int maxit, zt_step_stats* stats,
@@ -598,18 +689,19 @@ static int step_impl(zt_plan* p, double2* W, double h, double tol, int maxit, zt
     state_init_kernel<<<1, 1, 0, s>>>(p->state, tol, maxit);
     int rc = launch_check(p, "state_init_kernel");
     if (rc) return rc;
-    int enq = 0;
-    for (;;) {
+    int enq = 0, round = 0;
+    for (;; ++round) {
         const int chunk = p->tun.sweeps_per_sync;
         for (int c = 0; c < chunk && enq < maxit; ++c, ++enq)
-            if ((rc = enqueue_sweep(p, h, s))) return rc;
-        if ((rc = enqueue_final(p, W, h, s))) return rc;
+            if ((rc = enqueue_sweep(p, enq, h, s))) return rc;
+        if ((rc = enqueue_final(p, ZT_SWEEP_FINAL + round, W, h, s))) return rc;
         ZT_CU(cudaMemcpyAsync(p->h_state, p->state, sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
         ZT_CU(cudaStreamSynchronize(s));
         if (p->h_state->done) break;
         if (enq >= maxit) return zt_fail(ZT_ECUDA, "isomp_step: state not done after maxit sweeps");
     }
     const zt_dev_state& hs = *p->h_state;
+    if (p->timing && (rc = timer_collect(p, hs.iters, ZT_SWEEP_FINAL + round))) return rc;
     if (stats) {
         stats->iters = hs.iters;
         stats->converged = hs.converged;

@@ -586,11 +586,17 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
     zt_split_ws* w = p->split;
     if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
     const int N = p->N;
+    const double rd = 16.0 * N * N;
+    const double wa = 2.0 * w->s * (double)N * w->ldk, wb = 2.0 * wa;
+    int t = zt_timer_begin(p, ZT_KERNEL_SPLIT, rd + wa, rd + wa, s);
     split_rows_kernel<<<N, 256, 0, s>>>(X, N, w->s, w->beta, w->ldk, w->dA, w->Mpad, w->eA, nullptr, w->Npad,
                                         nullptr, p->state, gate);
+    zt_timer_end(p, t, s);
     p->launches++;
+    t = zt_timer_begin(p, ZT_KERNEL_SPLIT, rd + wb, rd + wb, s);
     split_rows_kernel<<<N, 256, 0, s>>>(Y, N, w->s, w->beta, w->ldk, nullptr, w->Mpad, nullptr, w->dB, w->Npad,
                                         w->eB, p->state, gate);
+    zt_timer_end(p, t, s);
     p->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "split_rows_kernel");
@@ -613,7 +619,12 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
     a.gate = gate;
     const int ntm = w->Mpad / BM;
     const int ntiles = lower_only ? ntm * (ntm + 1) / 2 : ntm * a.ntn;
+    const double pairs = 0.5 * w->s * (w->s + 1.0);
+    const double work = pairs * 2.0 * BM * (double)BN * w->ldk * ntiles;
+    const double alg = lower_only ? 4.0 * N * (double)N * (N + 1.0) : 8.0 * (double)N * N * N;
+    t = zt_timer_begin(p, ZT_KERNEL_PRODUCT, work, alg, s);
     zgemm_split_kernel<<<ntiles, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB, a);
+    zt_timer_end(p, t, s);
     p->launches++;
     e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "zgemm_split_kernel");

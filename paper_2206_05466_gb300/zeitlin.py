@@ -25,6 +25,10 @@ PRECISION_FP64 = 0
 PRECISION_SPLIT = 1
 FINAL_FRESH = 0
 FINAL_REUSE = 1
+KERNEL_PRODUCT = 0
+KERNEL_SOLVE = 1
+KERNEL_SPLIT = 2
+KERNEL_UPDATE = 3
 
 HEADER = os.path.join(_build.ROOT, "include", "zeitlin.h")
 
@@ -91,6 +95,11 @@ def load(build_if_missing: bool = True):
     L.zt_zgemm_skew.restype = i
     L.zt_plan_launch_count.argtypes = [vp]
     L.zt_plan_launch_count.restype = l
+    L.zt_plan_set_timing.argtypes = [vp, i]
+    L.zt_plan_set_timing.restype = i
+    dp, lp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)
+    L.zt_plan_kernel_time.argtypes = [vp, i, lp, dp, dp, dp]
+    L.zt_plan_kernel_time.restype = i
     _lib = L
     return L
 
@@ -148,6 +157,16 @@ class Plan:
 
     def launch_count(self) -> int:
         return load().zt_plan_launch_count(self._h)
+
+    def set_timing(self, enable: bool = True):
+        _check(load().zt_plan_set_timing(self._h, 1 if enable else 0))
+
+    def kernel_time(self, kind: int) -> dict:
+        n = ctypes.c_long()
+        ms, work, alg = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load().zt_plan_kernel_time(self._h, kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(work),
+                                          ctypes.byref(alg)))
+        return {"launches": n.value, "total_ms": ms.value, "work": work.value, "work_alg": alg.value}
 
 
 def zeitlin_laplacian_apply(plan: Plan, P, W, stream=None):
