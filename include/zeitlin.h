@@ -156,6 +156,34 @@ ZT_API int zt_plan_set_timing(zt_plan* plan, int enable);
 ZT_API int zt_plan_kernel_time(zt_plan* plan, int kind, long* launches, double* total_ms,
                                double* work, double* work_alg);
 
+/* Allocation-free split-precision product (no counterpart in the paper).
+ *
+ * Computes the same C = X Y, Y skew-Hermitian, as zt_zgemm_skew with a
+ * ZT_PRECISION_SPLIT plan at the default tuning (7 slices of 7 bits), but
+ * needs no plan and never allocates device or pinned memory: it is meant for
+ * callers that cannot call cudaMalloc -- a serving process that reserved all
+ * of the device memory for resident simulation state at start-up, code
+ * embedded in a host application whose own allocator owns the device, or a
+ * time-critical loop that must not hit the implicit device synchronisation
+ * of cudaMalloc/cudaFree.
+ *
+ * Its scratch (digit planes, row exponents, a status word) is one file-scope
+ * device array of ZT_NOALLOC_SCRATCH_BYTES (about 5.5 MB); every GPU that
+ * loads the library holds it until the process exits.  N is limited to
+ * 1 <= N <= ZT_NOALLOC_MAX_N; larger N returns ZT_EINVAL.  X, Y, C are
+ * caller-owned device matrices as for zt_zgemm_skew (C must not alias X or
+ * Y).  The first call on each device resolves the device address of the
+ * array (cudaGetSymbolAddress) and sets the kernel's shared-memory limit;
+ * make that first call before any stream capture.  Every call clears the
+ * array on `stream` before use, so no state carries over between calls, but
+ * all calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Blocks the host thread until the product is done.  Errors: ZT_EINVAL,
+ * ZT_ECUDA, ZT_ETIMEOUT. */
+#define ZT_NOALLOC_MAX_N 256
+#define ZT_NOALLOC_SCRATCH_BYTES 5508352
+ZT_API int zt_zgemm_skew_split_noalloc(int N, const double* X, const double* Y, double* C, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -630,3 +630,125 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
     if (e != cudaSuccess) return zt_cuda_check(e, "zgemm_split_kernel");
     return ZT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free split-precision product (no counterpart in the paper).
+//
+// For callers that cannot allocate device memory, the scratch of the split
+// product (digit planes of X' and B'^T, row exponents, a status word) lives
+// in one file-scope device array sized for N <= ZT_NOALLOC_MAX_N, laid out
+// once for that maximum (Mpad = 256 rows, Npad = 512 rows, K' = 512).  The
+// host never dereferences the array's name: its device address is resolved
+// per device with cudaGetSymbolAddress on first use and passed to the
+// kernels.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+constexpr int NA_S = 7, NA_BETA = 7, NA_EG = 4;
+constexpr int NA_MPAD = 256, NA_NPAD = 512, NA_LDK = 512;
+constexpr size_t NA_DA = (size_t)NA_S * NA_MPAD * NA_LDK * 2;
+constexpr size_t NA_DB = (size_t)NA_S * NA_NPAD * NA_LDK * 2;
+constexpr size_t NA_EA = (size_t)NA_MPAD * sizeof(int);
+constexpr size_t NA_EB = (size_t)NA_NPAD * sizeof(int);
+constexpr size_t NA_ST = 256;
+constexpr size_t NA_BYTES = NA_DA + NA_DB + NA_EA + NA_EB + NA_ST;
+static_assert(NA_BYTES == ZT_NOALLOC_SCRATCH_BYTES, "scratch size must match the header");
+static_assert(2 * ZT_NOALLOC_MAX_N <= NA_LDK && ZT_NOALLOC_MAX_N <= NA_MPAD && 2 * ZT_NOALLOC_MAX_N <= NA_NPAD,
+              "scratch layout too small for ZT_NOALLOC_MAX_N");
+static_assert(sizeof(zt_dev_state) <= NA_ST, "status word does not fit");
+constexpr int NA_MAX_DEVICES = 64;
+
+struct NoAllocDevice {
+    bool ready = false;
+    unsigned char* base = nullptr;   // device address of zt_noalloc_scratch on this device
+};
+NoAllocDevice g_noalloc[NA_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+}  // namespace
+
+static __device__ __align__(256) unsigned char zt_noalloc_scratch[NA_BYTES];
+
+// Once per device, with that device current: resolve the array's device
+// address and raise the product kernel's dynamic shared-memory limit.
+static int noalloc_setup(unsigned char** base) {
+    int dev = -1;
+    ZT_CU(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NA_MAX_DEVICES) return zt_fail(ZT_EINVAL, "device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc[dev].ready) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, zt_noalloc_scratch);
+        if (e != cudaSuccess) return zt_cuda_check(e, "cudaGetSymbolAddress(zt_noalloc_scratch)");
+        e = cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e != cudaSuccess) return zt_cuda_check(e, "cudaFuncSetAttribute(zgemm_split_kernel)");
+        g_noalloc[dev].base = static_cast<unsigned char*>(p);
+        g_noalloc[dev].ready = true;
+    }
+    *base = g_noalloc[dev].base;
+    return ZT_OK;
+}
+
+extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double* Y, double* C, void* stream) {
+    if (N < 1 || N > ZT_NOALLOC_MAX_N)
+        return zt_fail(ZT_EINVAL, "zt_zgemm_skew_split_noalloc: N=%d outside [1, %d] (static scratch limit)", N,
+                       ZT_NOALLOC_MAX_N);
+    if (!X || !Y || !C) return zt_fail(ZT_EINVAL, "zt_zgemm_skew_split_noalloc: NULL matrix");
+    if ((((uintptr_t)X) | ((uintptr_t)Y) | ((uintptr_t)C)) & 15u)
+        return zt_fail(ZT_EINVAL, "zt_zgemm_skew_split_noalloc: matrices must be 16-byte aligned");
+    if (C == X || C == Y) return zt_fail(ZT_EINVAL, "zt_zgemm_skew_split_noalloc: C must not alias X or Y");
+    unsigned char* base = nullptr;
+    int rc = noalloc_setup(&base);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    __nv_bfloat16* dA = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* dB = reinterpret_cast<__nv_bfloat16*>(base + NA_DA);
+    int* eA = reinterpret_cast<int*>(base + NA_DA + NA_DB);
+    int* eB = reinterpret_cast<int*>(base + NA_DA + NA_DB + NA_EA);
+    zt_dev_state* st = reinterpret_cast<zt_dev_state*>(base + NA_DA + NA_DB + NA_EA + NA_EB);
+    // The array keeps the previous call's contents: padding rows and columns
+    // of the digit planes and the status word must start at zero.
+    ZT_CU(cudaMemsetAsync(base, 0, NA_BYTES, s));
+    CUtensorMap tmA, tmB;
+    if ((rc = make_map(&tmA, dA, NA_S * NA_MPAD, NA_LDK, BM))) return rc;
+    if ((rc = make_map(&tmB, dB, NA_S * NA_NPAD, NA_LDK, BN))) return rc;
+    int u = 0;
+    {
+        const double R = std::ldexp(1.0, NA_BETA);
+        double bound = 0.0;
+        for (int g = 0; g < NA_S; ++g) bound += (g + 1) * std::pow(R, NA_S - 1 - g);
+        bound *= (double)NA_LDK * std::ldexp(1.0, 2 * NA_BETA - 2);
+        while (bound >= std::ldexp(1.0, 62 + u)) ++u;
+    }
+    split_rows_kernel<<<N, 256, 0, s>>>((const double2*)X, N, NA_S, NA_BETA, NA_LDK, dA, NA_MPAD, eA, nullptr,
+                                        NA_NPAD, nullptr, st, ZT_GATE_NONE);
+    split_rows_kernel<<<N, 256, 0, s>>>((const double2*)Y, N, NA_S, NA_BETA, NA_LDK, nullptr, NA_MPAD, nullptr, dB,
+                                        NA_NPAD, eB, st, ZT_GATE_NONE);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "split_rows_kernel");
+    SplitArgs a;
+    a.N = N;
+    a.s = NA_S;
+    a.beta = NA_BETA;
+    a.ldk = NA_LDK;
+    a.Mpad = NA_MPAD;
+    a.Npad = NA_NPAD;
+    a.u = u;
+    a.exact_groups = NA_EG;
+    a.ntn = NA_NPAD / BN;
+    a.lower_only = 0;
+    a.alpha = -1.0;
+    a.eA = eA;
+    a.eB = eB;
+    a.C = C;
+    a.st = st;
+    a.gate = ZT_GATE_NONE;
+    zgemm_split_kernel<<<(NA_MPAD / BM) * (NA_NPAD / BN), NTHREADS, SMEM_BYTES, s>>>(tmA, tmB, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "zgemm_split_kernel");
+    zt_dev_state hs;
+    ZT_CU(cudaMemcpyAsync(&hs, st, sizeof hs, cudaMemcpyDeviceToHost, s));
+    ZT_CU(cudaStreamSynchronize(s));
+    if (hs.timeout) return zt_fail(ZT_ETIMEOUT, "zt_zgemm_skew_split_noalloc: bounded device wait ran out");
+    return ZT_OK;
+}
