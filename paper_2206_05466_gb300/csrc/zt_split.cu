@@ -65,6 +65,7 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
 
 struct zt_split_ws {
     int s = 7, beta = 7, exact_groups = 4;
+    int cm = 1, cn = 1;            // cluster shape of the product kernel
     int ldk = 0, Mpad = 0, Npad = 0, u = 0;
     __nv_bfloat16* dA = nullptr;   // [s][Mpad][ldk]
     __nv_bfloat16* dB = nullptr;   // [s][Npad][ldk]
@@ -75,6 +76,8 @@ struct zt_split_ws {
 
 struct SplitArgs {
     int N, s, beta, ldk, Mpad, Npad, u, exact_groups, ntn, lower_only;
+    int cm, cn;        // cluster shape: cm row tiles share B'^T slices, cn column tiles share X' slices
+    int ntmg, ntng;    // tile groups (one cluster each) along rows and columns
     double alpha;
     const int* eA;
     const int* eB;
@@ -132,6 +135,24 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
 }
+// Multicast variant: the box lands at the same shared-memory offset in every
+// CTA of the cluster named in `mask`, and completes on each one's mbarrier.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -155,6 +176,15 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
+}
+// Arrive on the mbarrier at this offset in every CTA of `mask` once the
+// tcgen05 operations issued so far by this thread have completed.
+__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
@@ -295,27 +325,42 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-    // tile coordinates
-    int ti, tj;
-    if (a.lower_only) {
-        const int t = blockIdx.x;
-        int r = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-        while (r * (r + 1) / 2 > t) --r;
-        while ((r + 1) * (r + 2) / 2 <= t) ++r;
-        ti = r;
-        tj = t - r * (r + 1) / 2;
+    // Tile coordinates.  A cluster of cm x cn CTAs owns a group of cm row
+    // tiles and cn column tiles; CTA rank r sits at (r % cm, r / cm).
+    const int cs = a.cm * a.cn;
+    const int rank = cs > 1 ? (int)cluster_ctarank() : 0;
+    const int grp = blockIdx.x / cs;
+    int tig, tjg;
+    if (a.lower_only && a.cm == a.cn) {   // groups on or below the diagonal, triangular order
+        int r = (int)((sqrtf(8.0f * grp + 1.0f) - 1.0f) * 0.5f);
+        while (r * (r + 1) / 2 > grp) --r;
+        while ((r + 1) * (r + 2) / 2 <= grp) ++r;
+        tig = r;
+        tjg = grp - r * (r + 1) / 2;
     } else {
-        ti = blockIdx.x / a.ntn;
-        tj = blockIdx.x % a.ntn;
+        tig = grp / a.ntng;
+        tjg = grp % a.ntng;
+        // a group strictly above the diagonal has no lower-triangle element (whole cluster leaves)
+        if (a.lower_only && tjg * a.cn >= (tig + 1) * a.cm) return;
     }
+    const int rm = rank % a.cm, rn = rank / a.cm;
+    const int ti = tig * a.cm + rm, tj = tjg * a.cn + rn;
     const int i0 = ti * BM, c0 = tj * BN;
+    // each CTA fetches one slice of its X' tile (shared along the cluster row)
+    // and one slice of its B'^T tile (shared along the cluster column)
+    const int a_rows = BM / a.cn, b_rows = BN / a.cm;
+    const int a_off = rn * a_rows, b_off = rm * b_rows;
+    uint16_t mask_a = 0, mask_b = 0;
+    for (int n2 = 0; n2 < a.cn; ++n2) mask_a |= (uint16_t)(1u << (rm + a.cm * n2));
+    for (int m2 = 0; m2 < a.cm; ++m2) mask_b |= (uint16_t)(1u << (m2 + a.cm * rn));
+    const uint16_t mask_all = (uint16_t)((1u << cs) - 1u);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = a.ldk / BK;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], 1);
+            mbar_init(&empty[i], cs);   // released by the MMA of every CTA that reads this stage's slices
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&accf[i], 1);
@@ -332,7 +377,10 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    if (cs > 1)
+        cluster_sync();   // peers' barriers exist before any multicast lands
+    else
+        __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -352,8 +400,17 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                                 break;
                             }
                             mbar_expect_tx(&full[stage], STAGE_BYTES);
-                            tma_load_2d(sA + stage * A_TILE, &tmA, &full[stage], kb * BK, p * a.Mpad + i0);
-                            tma_load_2d(sB + stage * B_TILE, &tmB, &full[stage], kb * BK, (g - p) * a.Npad + c0);
+                            uint8_t* dA = sA + stage * A_TILE + a_off * 128;
+                            uint8_t* dB = sB + stage * B_TILE + b_off * 128;
+                            const int ya = p * a.Mpad + i0 + a_off, yb = (g - p) * a.Npad + c0 + b_off;
+                            if (a.cn > 1)
+                                tma_load_2d_mc(dA, &tmA, &full[stage], kb * BK, ya, mask_a);
+                            else
+                                tma_load_2d(dA, &tmA, &full[stage], kb * BK, ya);
+                            if (a.cm > 1)
+                                tma_load_2d_mc(dB, &tmB, &full[stage], kb * BK, yb, mask_b);
+                            else
+                                tma_load_2d(dB, &tmB, &full[stage], kb * BK, yb);
                             if (++stage == STAGES) {
                                 stage = 0;
                                 ph ^= 1;
@@ -393,7 +450,10 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                             for (int k = 0; k < BK / 16; ++k)
                                 umma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (first && k == 0) ? 0u : 1u);
                             first = false;
-                            umma_commit(&empty[stage]);
+                            if (cs > 1)
+                                umma_commit_mc(&empty[stage], mask_all);
+                            else
+                                umma_commit(&empty[stage]);
                             if (++stage == STAGES) {
                                 stage = 0;
                                 ph ^= 1;
@@ -493,6 +553,8 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
+    // no CTA leaves while a peer may still write into its shared memory or barriers
+    if (cs > 1) cluster_sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -534,15 +596,21 @@ int zt_split_create(zt_plan* p) {
     if (beta < 6 || beta > 8) return zt_fail(ZT_EINVAL, "digit_bits=%d outside [6, 8]", beta);
     if (eg < 1 || eg > s) return zt_fail(ZT_EINVAL, "exact_groups=%d outside [1, slices]", eg);
     if (s * beta > 62) return zt_fail(ZT_EINVAL, "slices*digit_bits must be <= 62");
+    const int cm = p->tun.cluster_m, cn = p->tun.cluster_n;
+    auto pow2 = [](int v) { return v == 1 || v == 2 || v == 4; };
+    if (!pow2(cm) || !pow2(cn) || cm * cn > 8)
+        return zt_fail(ZT_EINVAL, "cluster %dx%d: each side 1, 2 or 4 and at most 8 CTAs", cm, cn);
     zt_split_ws* w = new (std::nothrow) zt_split_ws();
     if (!w) return zt_fail(ZT_ENOMEM, "host allocation failed");
     p->split = w;
     w->s = s;
     w->beta = beta;
     w->exact_groups = eg;
+    w->cm = cm;
+    w->cn = cn;
     w->ldk = round_up(2 * N, BK);
-    w->Mpad = round_up(N, BM);
-    w->Npad = round_up(2 * N, BN);
+    w->Mpad = round_up(N, BM * cm);
+    w->Npad = round_up(2 * N, BN * cn);
     // smallest u >= 0 with the worst-case int64 accumulator below 2^62
     {
         const double R = std::ldexp(1.0, beta);
@@ -564,8 +632,8 @@ int zt_split_create(zt_plan* p) {
     ZT_CU(cudaMemset(w->eA, 0, (size_t)w->Mpad * sizeof(int)));
     ZT_CU(cudaMemset(w->eB, 0, (size_t)w->Npad * sizeof(int)));
     int rc;
-    if ((rc = make_map(&w->tmA, w->dA, s * w->Mpad, w->ldk, BM))) return rc;
-    if ((rc = make_map(&w->tmB, w->dB, s * w->Npad, w->ldk, BN))) return rc;
+    if ((rc = make_map(&w->tmA, w->dA, s * w->Mpad, w->ldk, BM / cn))) return rc;
+    if ((rc = make_map(&w->tmB, w->dB, s * w->Npad, w->ldk, BN / cm))) return rc;
     ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     return ZT_OK;
 }
@@ -611,19 +679,53 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
     a.exact_groups = w->exact_groups;
     a.ntn = w->Npad / BN;
     a.lower_only = lower_only;
+    a.cm = w->cm;
+    a.cn = w->cn;
+    a.ntmg = w->Mpad / (BM * w->cm);
+    a.ntng = w->Npad / (BN * w->cn);
     a.alpha = alpha;
     a.eA = w->eA;
     a.eB = w->eB;
     a.C = reinterpret_cast<double*>(C);
     a.st = p->state;
     a.gate = gate;
-    const int ntm = w->Mpad / BM;
-    const int ntiles = lower_only ? ntm * (ntm + 1) / 2 : ntm * a.ntn;
+    const int cs = w->cm * w->cn;
+    int ngroups, ntiles;
+    if (lower_only && w->cm == w->cn) {
+        ngroups = a.ntmg * (a.ntmg + 1) / 2;
+        ntiles = ngroups * cs;
+    } else {
+        ngroups = a.ntmg * a.ntng;
+        ntiles = 0;   // tiles of groups that touch the lower triangle (or all)
+        for (int tg = 0; tg < a.ntmg; ++tg)
+            for (int ug = 0; ug < a.ntng; ++ug)
+                if (!lower_only || ug * w->cn < (tg + 1) * w->cm) ntiles += cs;
+    }
     const double pairs = 0.5 * w->s * (w->s + 1.0);
     const double work = pairs * 2.0 * BM * (double)BN * w->ldk * ntiles;
     const double alg = lower_only ? 4.0 * N * (double)N * (N + 1.0) : 8.0 * (double)N * N * N;
     t = zt_timer_begin(p, ZT_KERNEL_PRODUCT, work, alg, s);
-    zgemm_split_kernel<<<ntiles, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB, a);
+    if (cs > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(ngroups * cs);
+        cfg.blockDim = dim3(NTHREADS);
+        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, zgemm_split_kernel, w->tmA, w->tmB, a);
+        if (e != cudaSuccess) {
+            zt_timer_end(p, t, s);
+            return zt_cuda_check(e, "cudaLaunchKernelEx(zgemm_split_kernel)");
+        }
+    } else {
+        zgemm_split_kernel<<<ngroups, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB, a);
+    }
     zt_timer_end(p, t, s);
     p->launches++;
     e = cudaGetLastError();
@@ -737,6 +839,10 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
     a.exact_groups = NA_EG;
     a.ntn = NA_NPAD / BN;
     a.lower_only = 0;
+    a.cm = 1;
+    a.cn = 1;
+    a.ntmg = NA_MPAD / BM;
+    a.ntng = NA_NPAD / BN;
     a.alpha = -1.0;
     a.eA = eA;
     a.eB = eB;
