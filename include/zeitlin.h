@@ -56,7 +56,7 @@ typedef struct zt_tuning {
     int final_mode;      /* ZT_FINAL_FRESH (default) or ZT_FINAL_REUSE               */
     int sweeps_per_sync; /* sweeps enqueued between host convergence checks (def. 4) */
     int cluster_m;       /* SPLIT: CTAs sharing each B'^T tile by TMA multicast (1, 2, 4; def. 2) */
-    int cluster_n;       /* SPLIT: CTAs sharing each X' tile by TMA multicast (1, 2, 4; def. 2) */
+    int cluster_n;       /* SPLIT: CTAs sharing each X' tile by TMA multicast (1, 2, 4; def. 1) */
 } zt_tuning;
 
 typedef struct zt_step_stats {

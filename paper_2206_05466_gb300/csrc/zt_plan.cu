@@ -558,7 +558,7 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     if (p->tun.exact_groups == 0) p->tun.exact_groups = 4;
     if (p->tun.sweeps_per_sync == 0) p->tun.sweeps_per_sync = 4;
     if (p->tun.cluster_m == 0) p->tun.cluster_m = 2;
-    if (p->tun.cluster_n == 0) p->tun.cluster_n = 2;
+    if (p->tun.cluster_n == 0) p->tun.cluster_n = 1;
     if (p->tun.final_mode != ZT_FINAL_FRESH && p->tun.final_mode != ZT_FINAL_REUSE) {
         delete p;
         return zt_fail(ZT_EINVAL, "zt_plan_create: bad final_mode %d", opt->final_mode);
