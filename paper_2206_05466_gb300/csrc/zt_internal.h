@@ -73,6 +73,14 @@ struct zt_plan {
     double2* B = nullptr;
     double* partials = nullptr;
     int npartials = 0;
+    // segmented stream solve: per-(diagonal, segment) end/start values
+    int nseg = 0;
+    double2* seg_z = nullptr;
+    double* seg_g = nullptr;
+    double2* seg_x = nullptr;
+    double* seg_h = nullptr;
+    double2* sum_x = nullptr;
+    double* sum_h = nullptr;
     zt_dev_state* state = nullptr;
     zt_dev_state* h_state = nullptr;   // pinned host mirror
     zt_split_ws* split = nullptr;
@@ -106,6 +114,8 @@ int zt_cuda_check(cudaError_t e, const char* what);
 // ---- kernels (launchers) ----------------------------------------------------
 int zt_launch_laplacian(zt_plan* p, const double2* P, double2* W, cudaStream_t s);
 int zt_launch_stream_solve(zt_plan* p, const double2* W, double2* P, cudaStream_t s, int gate);
+int zt_solve_create(zt_plan* p);
+void zt_solve_destroy(zt_plan* p);
 // C = alpha * X conj(Y)^T, FP64 DFMA.  With lower_only, only tiles that
 // touch the lower triangle (i >= j) are computed.
 int zt_launch_zgemm_fp64(zt_plan* p, const double2* X, const double2* Y, double2* C,

@@ -184,203 +184,6 @@ int zt_launch_laplacian(zt_plan* p, const double2* P, double2* W, cudaStream_t s
     return launch_check(p, "laplacian_kernel");
 }
 
-// ---------------------------------------------------------------------------
-// Stream solve (Sec. 3.3, Eq. sub_tria_W).
-//
-// A CTA owns a band of SD consecutive sub-diagonals [m0, m0+SD).  The band's
-// elements in rows [r0, r0+SR) form, row by row, contiguous runs of SD
-// complex values (row r holds W[r, r-m] at columns r-m0-SD+1 .. r-m0), so
-// the band is staged through shared memory in coalesced row segments
-// (cp.async, double buffered).  One warp runs the Thomas recurrences, one
-// lane per diagonal:
-//   forward   z_i = w_i - l_i z_{i-1}
-//   backward  x_i = (-1/d_i) z_i - l_{i+1} x_{i+1}      (x = P on the diagonal)
-// z is parked in the lower triangle of P between the passes.  The upper
-// triangle is written as P[i, i+m] = -conj(P[i+m, i]).  Band 0 also removes
-// the mean of the m = 0 right-hand side and of its solution (l = 0 mode).
-// ---------------------------------------------------------------------------
-namespace {
-constexpr int SD = 32;   // diagonals per band
-constexpr int SR = 32;   // rows per staged chunk
-constexpr int ST = 128;  // threads per CTA
-constexpr size_t SOLVE_SMEM = 2 * SR * SD * (sizeof(double2) + 2 * sizeof(double));
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    int sz = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    int sz = valid ? 8 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-// Deterministic block sum of a complex value over ST threads.
-__device__ double2 block_sum2(double2 v, double2* sh) {
-    const int t = threadIdx.x;
-    sh[t] = v;
-    __syncthreads();
-    for (int w = ST / 2; w > 0; w >>= 1) {
-        if (t < w) {
-            sh[t].x += sh[t + w].x;
-            sh[t].y += sh[t + w].y;
-        }
-        __syncthreads();
-    }
-    double2 r = sh[0];
-    __syncthreads();
-    return r;
-}
-}  // namespace
-
-__global__ void __launch_bounds__(ST)
-stream_solve_kernel(const double2* __restrict__ W, double2* __restrict__ P,
-                    const double* __restrict__ fl, const double* __restrict__ fnd,
-                    int N, const zt_dev_state* st, int gate) {
-    if (zt_gate_skip(st, gate)) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double2* tw = reinterpret_cast<double2*>(smem_raw);                       // [2][SR][SD]
-    double* tl = reinterpret_cast<double*>(tw + 2 * SR * SD);                 // [2][SR][SD]
-    double* tn = tl + 2 * SR * SD;                                            // [2][SR][SD]
-    __shared__ double2 red[ST];
-
-    const int m0 = blockIdx.x * SD;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nch = (N - m0 + SR - 1) / SR;
-    const int m = m0 + lane;   // diagonal of this lane in the compute warp
-
-    double2 mu = make_double2(0.0, 0.0);
-    if (m0 == 0) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int i = tid; i < N; i += ST) {
-            double2 w = W[(size_t)i * N + i];
-            acc.x += w.x;
-            acc.y += w.y;
-        }
-        acc = block_sum2(acc, red);
-        mu = make_double2(acc.x / N, acc.y / N);
-    }
-
-    // stage rows [r0, r0+SR) of the band: element (rr, tt) = (r0+rr, r0+rr-m0-tt)
-    auto stage = [&](int buf, int r0, const double2* src, bool want_nd) {
-        for (int rr = warp; rr < SR; rr += ST / 32) {
-            const int tt = SD - 1 - lane;
-            const int r = r0 + rr, mm = m0 + tt, c = r - mm;
-            const bool ok = (r >= 0) && (r < N) && (mm < N) && (c >= 0);
-            const size_t e = ok ? (size_t)r * N + c : 0;
-            const size_t q = ok ? zt_tri(r, c) : 0;
-            const int at = (buf * SR + rr) * SD + tt;
-            cp_async16(&tw[at], src + e, ok);
-            cp_async8(&tl[at], fl + q, ok);
-            if (want_nd) cp_async8(&tn[at], fnd + q, ok);
-        }
-    };
-    auto unstage = [&](int buf, int r0) {
-        for (int rr = warp; rr < SR; rr += ST / 32) {
-            const int tt = SD - 1 - lane;
-            const int r = r0 + rr, mm = m0 + tt, c = r - mm;
-            const bool ok = (r >= 0) && (r < N) && (mm < N) && (c >= 0);
-            if (ok) P[(size_t)r * N + c] = tw[(buf * SR + rr) * SD + tt];
-        }
-    };
-
-    // ---- forward pass: rows m0 .. N-1 in increasing order ----
-    double2 zprev = make_double2(0.0, 0.0);
-    stage(0, m0, W, false);
-    cp_async_commit();
-    for (int ch = 0; ch < nch; ++ch) {
-        const int b = ch & 1, r0 = m0 + ch * SR;
-        if (ch + 1 < nch) stage(b ^ 1, r0 + SR, W, false);
-        cp_async_commit();
-        cp_async_wait1();
-        __syncthreads();
-        if (warp == 0 && m < N) {
-#pragma unroll 4
-            for (int rr = 0; rr < SR; ++rr) {
-                const int r = r0 + rr;
-                if (r >= m && r < N) {
-                    const int at = (b * SR + rr) * SD + lane;
-                    double2 w = tw[at];
-                    if (m == 0) {
-                        w.x -= mu.x;
-                        w.y -= mu.y;
-                    }
-                    const double l = tl[at];
-                    double2 z;
-                    z.x = fma(-l, zprev.x, w.x);
-                    z.y = fma(-l, zprev.y, w.y);
-                    tw[at] = z;
-                    zprev = z;
-                }
-            }
-        }
-        __syncthreads();
-        unstage(b, r0);
-        __syncthreads();
-    }
-
-    // ---- backward pass: rows N-1 .. m0 in decreasing order ----
-    double2 xnext = make_double2(0.0, 0.0);
-    double lnext = 0.0;
-    stage(0, N - SR, P, true);
-    cp_async_commit();
-    for (int ch = 0; ch < nch; ++ch) {
-        const int b = ch & 1, r0 = N - (ch + 1) * SR;
-        if (ch + 1 < nch) stage(b ^ 1, r0 - SR, P, true);
-        cp_async_commit();
-        cp_async_wait1();
-        __syncthreads();
-        if (warp == 0 && m < N) {
-#pragma unroll 4
-            for (int rr = SR - 1; rr >= 0; --rr) {
-                const int r = r0 + rr;
-                if (r >= m && r < N && r >= 0) {
-                    const int at = (b * SR + rr) * SD + lane;
-                    const double2 z = tw[at];
-                    const double nd = tn[at];
-                    double2 x;
-                    x.x = fma(-lnext, xnext.x, z.x * nd);
-                    x.y = fma(-lnext, xnext.y, z.y * nd);
-                    tw[at] = x;
-                    xnext = x;
-                    lnext = tl[at];
-                    if (m > 0) P[(size_t)(r - m) * N + r] = make_double2(-x.x, x.y);
-                }
-            }
-        }
-        __syncthreads();
-        unstage(b, r0);
-        __syncthreads();
-    }
-
-    if (m0 == 0) {   // remove the mean of the m = 0 solution
-        double2 acc = make_double2(0.0, 0.0);
-        for (int i = tid; i < N; i += ST) {
-            double2 x = P[(size_t)i * N + i];
-            acc.x += x.x;
-            acc.y += x.y;
-        }
-        acc = block_sum2(acc, red);
-        const double2 mx = make_double2(acc.x / N, acc.y / N);
-        for (int i = tid; i < N; i += ST) {
-            double2 x = P[(size_t)i * N + i];
-            P[(size_t)i * N + i] = make_double2(x.x - mx.x, x.y - mx.y);
-        }
-    }
-}
-
-int zt_launch_stream_solve(zt_plan* p, const double2* W, double2* P, cudaStream_t s, int gate) {
-    const int N = p->N;
-    const int nb = (N + SD - 1) / SD;
-    const double bytes = 8.0 * N * (N + 1.0) + 16.0 * N * N;
-    const int t = zt_timer_begin(p, ZT_KERNEL_SOLVE, bytes, bytes, s);
-    stream_solve_kernel<<<nb, ST, SOLVE_SMEM, s>>>(W, P, p->fac_l, p->fac_nd, N, p->state, gate);
-    zt_timer_end(p, t, s);
-    return launch_check(p, "stream_solve_kernel");
-}
 
 // ---------------------------------------------------------------------------
 // Fixed-point update (Eq. isomp_iter with the products of Sec. 3.1) and the
@@ -522,6 +325,7 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     if (!p) return;
     cudaDeviceSynchronize();
     if (p->split) zt_split_destroy(p);
+    zt_solve_destroy(p);
     cudaFree(p->lap_a);
     cudaFree(p->lap_b);
     cudaFree(p->fac_l);
@@ -595,8 +399,8 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     ZT_TRY(cudaMalloc(&p->state, sizeof(zt_dev_state)));
     ZT_TRY(cudaMallocHost(&p->h_state, sizeof(zt_dev_state)));
     ZT_TRY(cudaMemset(p->state, 0, sizeof(zt_dev_state)));
-    ZT_TRY(cudaFuncSetAttribute(stream_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)SOLVE_SMEM));
+    rc = zt_solve_create(p);
+    if (rc != ZT_OK) return fail(rc);
     factor_kernel<<<(N + 127) / 128, 128>>>(N, p->lap_a, p->lap_b, p->fac_l, p->fac_nd);
     ZT_TRY(cudaGetLastError());
     p->launches++;
