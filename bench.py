@@ -181,6 +181,64 @@ def run_reference(args):
     return 0
 
 
+def _tuning(args, N):
+    """Split-product tuning: autotuned (cached per N and GPU) or fixed from the flags."""
+    if args.tuning == "auto":
+        from paper_2206_05466_gb300 import autotune
+
+        res = autotune.autotune(N, target=args.tune_target)
+        return dict(res["tuning"]), {"mode": "auto", "target_rel_err": args.tune_target,
+                                     "probe_rel_err": res["rel_err"], "probe_ms": res["ms"]}
+    tun = dict(slices=args.slices, digit_bits=args.digit_bits, exact_groups=args.exact_groups,
+               cluster_m=args.cluster_m, cluster_n=args.cluster_n)
+    return tun, {"mode": "fixed"}
+
+
+def _casimir_drift(W0, W1, ks=(2, 3, 4)):
+    """Relative drift of C_k = tr(W^k) and of the spectrum (eigenvalues i mu of W)."""
+    import numpy as np
+
+    mu0 = np.linalg.eigvalsh(-1j * W0)
+    mu1 = np.linalg.eigvalsh(-1j * W1)
+    out = {}
+    for k in ks:
+        out[f"C{k}"] = float(abs(np.sum(mu1 ** k) - np.sum(mu0 ** k)) / np.sum(np.abs(mu0) ** k))
+    out["spectrum_max_abs"] = float(np.max(np.abs(mu1 - mu0)))
+    return out
+
+
+def run_casimir(args):
+    """Long run: Casimir and spectrum drift after --steps steps, split and (optionally) FP64 form."""
+    import torch
+
+    from paper_2206_05466_gb300 import zeitlin as z
+    from paper_2206_05466_gb300.inputs import vorticity_w0
+
+    N, steps = args.n, args.steps
+    W0 = vorticity_w0(N, seed=0)
+    res = {"mode": "casimir", "N": N, "h": H, "steps": steps, "tol": TOL, "data": "synthetic"}
+    forms = [("split", z.PRECISION_SPLIT)] + ([("fp64", z.PRECISION_FP64)] if args.fp64_steps > 0 else [])
+    for name, prec in forms:
+        if prec == z.PRECISION_SPLIT:
+            tun, info = _tuning(args, N)
+            plan = z.Plan(N, prec, **tun)
+            res["split_tuning"] = tun
+        else:
+            plan = z.Plan(N, prec)
+        W = torch.from_numpy(W0).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = z.isomp_run(plan, W, H, steps, TOL, MAXIT)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        W1 = W.cpu().numpy()
+        res[name] = {"steps_per_s": steps / dt, "run_stats": r, "drift": _casimir_drift(W0, W1),
+                     "trace_abs": float(abs(W1.trace())), "skew_err": float(abs(W1 + W1.conj().T).max())}
+        plan.close()
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -197,7 +255,7 @@ def run_gpu(args):
     N = args.n
     peaks = _peaks()
     W0 = vorticity_w0(N, seed=rank)   # replicas: each rank its own seeded instance
-    tun = dict(slices=args.slices, digit_bits=args.digit_bits, exact_groups=args.exact_groups)
+    tun, tune_info = _tuning(args, N)
     plan = z.Plan(N, z.PRECISION_SPLIT, **tun)
     Wd = torch.from_numpy(W0).cuda()
     stream = torch.cuda.current_stream()
@@ -296,7 +354,7 @@ def run_gpu(args):
 
     if rank != 0:
         return 0
-    pairs = args.slices * (args.slices + 1) / 2
+    pairs = tun["slices"] * (tun["slices"] + 1) / 2
     achieved = prod["work"] / (prod["total_ms"] / 1e3) / 1e12 if prod["total_ms"] else None
     peak = peaks["bf16_tflops_sustained"]
     src = open(os.path.join(ROOT, "paper_2206_05466_gb300", "csrc", "zt_split.cu"), "rb").read()
@@ -307,9 +365,9 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (products: bf16 digit slices, fp32/int64 accumulate)",
         "data": "synthetic",
         "config": {"workload": f"IsoMP N={N} h={H} seeded W0 (decay 2, spectral norm 1), tol {TOL} Frobenius, "
-                               f"maxit {MAXIT}, split-precision products s={args.slices} beta={args.digit_bits}",
-                   "N": N, "h": H, "precision": "split", "slices": args.slices, "digit_bits": args.digit_bits,
-                   "exact_groups": args.exact_groups, "parallelism": f"replicas x{ws}",
+                               f"maxit {MAXIT}, split-precision products s={tun['slices']} beta={tun['digit_bits']}",
+                   "N": N, "h": H, "precision": "split", "tuning": tun, "tuning_source": tune_info,
+                   "parallelism": f"replicas x{ws}",
                    "l2": "working set > L2 (digit planes ~1.4 GB + 6 matrices of 268 MB)"},
         "sweeps_per_step": statistics.mean(step_iters) if step_iters else None,
         "gpu_launches": gpu_launches,
@@ -342,9 +400,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--mode", default="bench", choices=["bench", "casimir"])
+    ap.add_argument("--tuning", default="auto", choices=["auto", "fixed"])
+    ap.add_argument("--tune-target", type=float, default=1e-11)
     ap.add_argument("--slices", type=int, default=7)
     ap.add_argument("--digit-bits", type=int, default=7)
     ap.add_argument("--exact-groups", type=int, default=4)
+    ap.add_argument("--cluster-m", type=int, default=2)
+    ap.add_argument("--cluster-n", type=int, default=1)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--oracle-steps", type=int, default=2)
     args = ap.parse_args()
@@ -352,6 +415,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "casimir":
+        return run_casimir(args)
     return run_gpu(args)
 
 

@@ -1,0 +1,102 @@
+"""Autotuner for the split-precision product: digit count, digit width, cluster shape.
+
+For a matrix size N it times each candidate tuning on seeded probe operands
+(X complex Gaussian, Y from the seeded su(N) recipe) through the C ABI, measures
+the candidate's error against a reference product with more digits (8 slices
+of 7 bits, ~2^-55 relative), and keeps the fastest candidate whose relative
+Frobenius error is within `target`.  Choices are cached as JSON keyed by
+(N, GPU name) in $ZEITLIN_TUNE_CACHE (default ~/.cache/zeitlin_gb300/tune.json).
+All arithmetic runs in the library's kernels; this module only orchestrates.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+DEFAULT_CANDIDATES = [
+    dict(slices=7, digit_bits=7, exact_groups=4, cluster_m=2, cluster_n=1),
+    dict(slices=7, digit_bits=7, exact_groups=4, cluster_m=4, cluster_n=1),
+    dict(slices=6, digit_bits=7, exact_groups=4, cluster_m=2, cluster_n=1),
+    dict(slices=6, digit_bits=7, exact_groups=4, cluster_m=4, cluster_n=1),
+    dict(slices=6, digit_bits=7, exact_groups=3, cluster_m=2, cluster_n=1),
+]
+REFERENCE = dict(slices=8, digit_bits=7, exact_groups=8, cluster_m=2, cluster_n=1)
+
+
+def _cache_path():
+    return os.environ.get("ZEITLIN_TUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "zeitlin_gb300", "tune.json"))
+
+
+def _key(N):
+    import torch
+
+    return f"{torch.cuda.get_device_name()}|N={N}"
+
+
+def load_cached(N):
+    try:
+        return json.load(open(_cache_path())).get(_key(N))
+    except Exception:
+        return None
+
+
+def autotune(N: int, target: float = 1e-11, candidates=None, reps: int = 2, use_cache: bool = True) -> dict:
+    """Return {"tuning": {...}, "rel_err": e, "ms": t, "trials": [...]} for size N."""
+    import numpy as np
+    import torch
+
+    from . import zeitlin as z
+    from .inputs import vorticity_w0
+
+    if use_cache:
+        hit = load_cached(N)
+        if hit is not None:
+            return hit
+    cands = candidates or DEFAULT_CANDIDATES
+    rng = np.random.default_rng(1234)
+    X = torch.from_numpy(rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))).cuda()
+    Y = torch.from_numpy(vorticity_w0(N, seed=1234)).cuda()
+    ref = torch.empty_like(X)
+    plan = z.Plan(N, z.PRECISION_SPLIT, **REFERENCE)
+    z.zt_zgemm_skew(plan, X, Y, ref)
+    torch.cuda.synchronize()
+    plan.close()
+    ref_h = ref.cpu().numpy()
+    nref = float(np.linalg.norm(ref_h))
+    trials = []
+    C = torch.empty_like(X)
+    for tun in cands:
+        try:
+            plan = z.Plan(N, z.PRECISION_SPLIT, **tun)
+        except z.ZeitlinError as e:
+            trials.append({"tuning": tun, "error": str(e)})
+            continue
+        z.zt_zgemm_skew(plan, X, Y, C)
+        torch.cuda.synchronize()
+        err = float(np.linalg.norm(C.cpu().numpy() - ref_h)) / nref
+        plan.set_timing(True)
+        for _ in range(reps):
+            z.zt_zgemm_skew(plan, X, Y, C)
+        torch.cuda.synchronize()
+        kp = plan.kernel_time(z.KERNEL_PRODUCT)
+        ks = plan.kernel_time(z.KERNEL_SPLIT)
+        ms = (kp["total_ms"] + ks["total_ms"]) / reps
+        trials.append({"tuning": tun, "rel_err": err, "ms": ms})
+        plan.close()
+    ok = [t for t in trials if "rel_err" in t and t["rel_err"] <= target]
+    if not ok:
+        raise RuntimeError(f"no candidate meets relative error {target}: {trials}")
+    best = min(ok, key=lambda t: t["ms"])
+    out = {"tuning": best["tuning"], "rel_err": best["rel_err"], "ms": best["ms"], "target": target,
+           "trials": trials}
+    if use_cache:
+        path = _cache_path()
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        try:
+            data = json.load(open(path))
+        except Exception:
+            data = {}
+        data[_key(N)] = out
+        json.dump(data, open(path, "w"), indent=1)
+    return out

@@ -125,3 +125,8 @@ int zt_split_create(zt_plan* p);
 void zt_split_destroy(zt_plan* p);
 int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double2* C,
                           double alpha, int lower_only, cudaStream_t s, int gate);
+// The two halves of the split product: digit splitting of one operand (into
+// the X' planes and/or one of two B'^T slots) and the tcgen05 product of the
+// X' planes with a B'^T slot.
+int zt_split_operand(zt_plan* p, const double2* X, int to_a, int b_slot, cudaStream_t s, int gate);
+int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, cudaStream_t s, int gate);

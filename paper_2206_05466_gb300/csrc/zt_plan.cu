@@ -461,12 +461,26 @@ extern "C" int zt_zgemm_skew(zt_plan* p, const double* X, const double* Y, doubl
 
 // One fixed-point sweep (Eq. isomp_iter): Pt = solve(Wt), A = Pt Wt,
 // B = A Pt, Wt <- W_n + h/2 (A - A^H) + h^2/4 B, residual, stop decision.
+// Pt = solve(Wt), A = Pt Wt, B = A Pt (lower half).  In split form Pt is
+// split once into both operand forms.
+static int enqueue_products(zt_plan* p, cudaStream_t s, int gate) {
+    int rc;
+    if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, gate))) return rc;
+    if (p->precision == ZT_PRECISION_SPLIT) {
+        if ((rc = zt_split_operand(p, p->P, 1, 1, s, gate))) return rc;    // Pt: X' planes and B'^T slot 1
+        if ((rc = zt_split_operand(p, p->Wt, 0, 0, s, gate))) return rc;   // Wt: B'^T slot 0
+        if ((rc = zt_split_product(p, 0, p->A, -1.0, 0, s, gate))) return rc;   // A = Pt Wt
+        if ((rc = zt_split_operand(p, p->A, 1, -1, s, gate))) return rc;   // A: X' planes
+        return zt_split_product(p, 1, p->B, -1.0, 1, s, gate);                // B = A Pt
+    }
+    if ((rc = zgemm(p, p->P, p->Wt, p->A, -1.0, 0, s, gate))) return rc;
+    return zgemm(p, p->A, p->P, p->B, -1.0, 1, s, gate);
+}
+
 static int enqueue_sweep(zt_plan* p, int k, double h, cudaStream_t s) {
     int rc;
     p->cur_sweep = k;
-    if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, ZT_GATE_SWEEP))) return rc;
-    if ((rc = zgemm(p, p->P, p->Wt, p->A, -1.0, 0, s, ZT_GATE_SWEEP))) return rc;   // A = Pt Wt
-    if ((rc = zgemm(p, p->A, p->P, p->B, -1.0, 1, s, ZT_GATE_SWEEP))) return rc;    // B = A Pt (lower half)
+    if ((rc = enqueue_products(p, s, ZT_GATE_SWEEP))) return rc;
     if ((rc = launch_update(p, p->Wn, p->Wt, p->Wt, h, +1.0, true, s, ZT_GATE_SWEEP))) return rc;
     converge_kernel<<<1, 256, 0, s>>>(p->partials, p->npartials, p->state);
     p->cur_sweep = -1;
@@ -477,11 +491,7 @@ static int enqueue_sweep(zt_plan* p, int k, double h, cudaStream_t s) {
 static int enqueue_final(zt_plan* p, int tag, double2* W, double h, cudaStream_t s) {
     int rc;
     p->cur_sweep = tag;
-    if (p->tun.final_mode == ZT_FINAL_FRESH) {
-        if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, ZT_GATE_FINAL))) return rc;
-        if ((rc = zgemm(p, p->P, p->Wt, p->A, -1.0, 0, s, ZT_GATE_FINAL))) return rc;
-        if ((rc = zgemm(p, p->A, p->P, p->B, -1.0, 1, s, ZT_GATE_FINAL))) return rc;
-    }
+    if (p->tun.final_mode == ZT_FINAL_FRESH && (rc = enqueue_products(p, s, ZT_GATE_FINAL))) return rc;
     rc = launch_update(p, p->Wt, nullptr, W, h, -1.0, false, s, ZT_GATE_FINAL);
     p->cur_sweep = -1;
     return rc;

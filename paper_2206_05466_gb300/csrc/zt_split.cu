@@ -68,10 +68,10 @@ struct zt_split_ws {
     int cm = 1, cn = 1;            // cluster shape of the product kernel
     int ldk = 0, Mpad = 0, Npad = 0, u = 0;
     __nv_bfloat16* dA = nullptr;   // [s][Mpad][ldk]
-    __nv_bfloat16* dB = nullptr;   // [s][Npad][ldk]
-    int* eA = nullptr;             // [Mpad]
-    int* eB = nullptr;             // [Npad]
-    CUtensorMap tmA, tmB;
+    __nv_bfloat16* dB[2] = {nullptr, nullptr};   // two B'^T slots, each [s][Npad][ldk]
+    int* eA = nullptr;                           // [Mpad]
+    int* eB[2] = {nullptr, nullptr};             // [Npad]
+    CUtensorMap tmA, tmB[2];
 };
 
 struct SplitArgs {
@@ -264,35 +264,45 @@ split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk
     const int sb = s * beta;
     const long long R = 1LL << beta, H = R >> 1;
     const size_t planeA = (size_t)Mpad * ldk, planeB = (size_t)Npad * ldk;
-    for (int k = threadIdx.x; k < ldk / 2; k += 256) {
-        long long vr = 0, vi = 0;
-        if (k < N && !bad) {
-            const double2 v = row[k];
-            vr = to_fixed(v.x, e, sb);
-            vi = to_fixed(v.y, e, sb);
+    // each thread: 4 consecutive complex entries -> one 16-byte store per plane and row
+    for (int kq = threadIdx.x; kq < ldk / 8; kq += 256) {
+        long long vr[4], vi[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = 4 * kq + u;
+            vr[u] = vi[u] = 0;
+            if (k < N && !bad) {
+                const double2 v = row[k];
+                vr[u] = to_fixed(v.x, e, sb);
+                vi[u] = to_fixed(v.y, e, sb);
+            }
         }
         for (int p = s - 1; p >= 0; --p) {
-            long long dr, di;
-            if (p > 0) {
-                dr = ((vr + H) & (R - 1)) - H;
-                di = ((vi + H) & (R - 1)) - H;
-                vr = (vr - dr) >> beta;
-                vi = (vi - di) >> beta;
-            } else {
-                dr = vr;
-                di = vi;
+            __align__(16) __nv_bfloat162 wa[4], wb0[4], wb1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                long long dr, di;
+                if (p > 0) {
+                    dr = ((vr[u] + H) & (R - 1)) - H;
+                    di = ((vi[u] + H) & (R - 1)) - H;
+                    vr[u] = (vr[u] - dr) >> beta;
+                    vi[u] = (vi[u] - di) >> beta;
+                } else {
+                    dr = vr[u];
+                    di = vi[u];
+                }
+                const float fr = (float)dr, fi = (float)di;
+                wa[u] = __floats2bfloat162_rn(fr, fi);
+                // B'^T row 2j: interleaved(y); row 2j+1: interleaved(i y) = (-im, re)
+                wb0[u] = __floats2bfloat162_rn(fr, fi);
+                wb1[u] = __floats2bfloat162_rn(-fi, fr);
             }
-            const float fr = (float)dr, fi = (float)di;
-            if (dA) {
-                __nv_bfloat162 w2 = __floats2bfloat162_rn(fr, fi);
-                *reinterpret_cast<__nv_bfloat162*>(dA + p * planeA + (size_t)j * ldk + 2 * k) = w2;
-            }
+            const size_t col = (size_t)8 * kq;
+            if (dA) *reinterpret_cast<uint4*>(dA + p * planeA + (size_t)j * ldk + col) = *reinterpret_cast<uint4*>(wa);
             if (dB) {
-                // row 2j: interleaved(y) ; row 2j+1: interleaved(i y) = (-im, re)
-                __nv_bfloat162 r0 = __floats2bfloat162_rn(fr, fi);
-                __nv_bfloat162 r1 = __floats2bfloat162_rn(-fi, fr);
-                *reinterpret_cast<__nv_bfloat162*>(dB + p * planeB + (size_t)(2 * j) * ldk + 2 * k) = r0;
-                *reinterpret_cast<__nv_bfloat162*>(dB + p * planeB + (size_t)(2 * j + 1) * ldk + 2 * k) = r1;
+                *reinterpret_cast<uint4*>(dB + p * planeB + (size_t)(2 * j) * ldk + col) = *reinterpret_cast<uint4*>(wb0);
+                *reinterpret_cast<uint4*>(dB + p * planeB + (size_t)(2 * j + 1) * ldk + col) =
+                    *reinterpret_cast<uint4*>(wb1);
             }
         }
     }
@@ -624,16 +634,18 @@ int zt_split_create(zt_plan* p) {
     const size_t szA = (size_t)s * w->Mpad * w->ldk * sizeof(__nv_bfloat16);
     const size_t szB = (size_t)s * w->Npad * w->ldk * sizeof(__nv_bfloat16);
     ZT_CU(cudaMalloc(&w->dA, szA));
-    ZT_CU(cudaMalloc(&w->dB, szB));
     ZT_CU(cudaMemset(w->dA, 0, szA));   // padding rows/columns stay zero
-    ZT_CU(cudaMemset(w->dB, 0, szB));
     ZT_CU(cudaMalloc(&w->eA, (size_t)w->Mpad * sizeof(int)));
-    ZT_CU(cudaMalloc(&w->eB, (size_t)w->Npad * sizeof(int)));
     ZT_CU(cudaMemset(w->eA, 0, (size_t)w->Mpad * sizeof(int)));
-    ZT_CU(cudaMemset(w->eB, 0, (size_t)w->Npad * sizeof(int)));
     int rc;
     if ((rc = make_map(&w->tmA, w->dA, s * w->Mpad, w->ldk, BM / cn))) return rc;
-    if ((rc = make_map(&w->tmB, w->dB, s * w->Npad, w->ldk, BN / cm))) return rc;
+    for (int b = 0; b < 2; ++b) {
+        ZT_CU(cudaMalloc(&w->dB[b], szB));
+        ZT_CU(cudaMemset(w->dB[b], 0, szB));
+        ZT_CU(cudaMalloc(&w->eB[b], (size_t)w->Npad * sizeof(int)));
+        ZT_CU(cudaMemset(w->eB[b], 0, (size_t)w->Npad * sizeof(int)));
+        if ((rc = make_map(&w->tmB[b], w->dB[b], s * w->Npad, w->ldk, BN / cm))) return rc;
+    }
     ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     return ZT_OK;
 }
@@ -642,32 +654,36 @@ void zt_split_destroy(zt_plan* p) {
     zt_split_ws* w = p->split;
     if (!w) return;
     cudaFree(w->dA);
-    cudaFree(w->dB);
     cudaFree(w->eA);
-    cudaFree(w->eB);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(w->dB[b]);
+        cudaFree(w->eB[b]);
+    }
     delete w;
     p->split = nullptr;
 }
 
-int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double2* C, double alpha,
-                          int lower_only, cudaStream_t s, int gate) {
+int zt_split_operand(zt_plan* p, const double2* X, int to_a, int b_slot, cudaStream_t s, int gate) {
     zt_split_ws* w = p->split;
     if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
     const int N = p->N;
-    const double rd = 16.0 * N * N;
-    const double wa = 2.0 * w->s * (double)N * w->ldk, wb = 2.0 * wa;
-    int t = zt_timer_begin(p, ZT_KERNEL_SPLIT, rd + wa, rd + wa, s);
-    split_rows_kernel<<<N, 256, 0, s>>>(X, N, w->s, w->beta, w->ldk, w->dA, w->Mpad, w->eA, nullptr, w->Npad,
-                                        nullptr, p->state, gate);
-    zt_timer_end(p, t, s);
-    p->launches++;
-    t = zt_timer_begin(p, ZT_KERNEL_SPLIT, rd + wb, rd + wb, s);
-    split_rows_kernel<<<N, 256, 0, s>>>(Y, N, w->s, w->beta, w->ldk, nullptr, w->Mpad, nullptr, w->dB, w->Npad,
-                                        w->eB, p->state, gate);
+    const double bytes = 16.0 * N * N + (to_a ? 2.0 * w->s * (double)N * w->ldk : 0.0) +
+                         (b_slot >= 0 ? 4.0 * w->s * (double)N * w->ldk : 0.0);
+    const int t = zt_timer_begin(p, ZT_KERNEL_SPLIT, bytes, bytes, s);
+    split_rows_kernel<<<N, 256, 0, s>>>(X, N, w->s, w->beta, w->ldk, to_a ? w->dA : nullptr, w->Mpad,
+                                        to_a ? w->eA : nullptr, b_slot >= 0 ? w->dB[b_slot] : nullptr, w->Npad,
+                                        b_slot >= 0 ? w->eB[b_slot] : nullptr, p->state, gate);
     zt_timer_end(p, t, s);
     p->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "split_rows_kernel");
+    return ZT_OK;
+}
+
+int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, cudaStream_t s, int gate) {
+    zt_split_ws* w = p->split;
+    if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
+    const int N = p->N;
     SplitArgs a;
     a.N = N;
     a.s = w->s;
@@ -685,7 +701,7 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
     a.ntng = w->Npad / (BN * w->cn);
     a.alpha = alpha;
     a.eA = w->eA;
-    a.eB = w->eB;
+    a.eB = w->eB[b_slot];
     a.C = reinterpret_cast<double*>(C);
     a.st = p->state;
     a.gate = gate;
@@ -704,7 +720,8 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
     const double pairs = 0.5 * w->s * (w->s + 1.0);
     const double work = pairs * 2.0 * BM * (double)BN * w->ldk * ntiles;
     const double alg = lower_only ? 4.0 * N * (double)N * (N + 1.0) : 8.0 * (double)N * N * N;
-    t = zt_timer_begin(p, ZT_KERNEL_PRODUCT, work, alg, s);
+    const int t = zt_timer_begin(p, ZT_KERNEL_PRODUCT, work, alg, s);
+    cudaError_t e;
     if (cs > 1) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(ngroups * cs);
@@ -718,19 +735,27 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, zgemm_split_kernel, w->tmA, w->tmB, a);
+        e = cudaLaunchKernelEx(&cfg, zgemm_split_kernel, w->tmA, w->tmB[b_slot], a);
         if (e != cudaSuccess) {
             zt_timer_end(p, t, s);
             return zt_cuda_check(e, "cudaLaunchKernelEx(zgemm_split_kernel)");
         }
     } else {
-        zgemm_split_kernel<<<ngroups, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB, a);
+        zgemm_split_kernel<<<ngroups, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB[b_slot], a);
     }
     zt_timer_end(p, t, s);
     p->launches++;
     e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "zgemm_split_kernel");
     return ZT_OK;
+}
+
+int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double2* C, double alpha,
+                          int lower_only, cudaStream_t s, int gate) {
+    int rc;
+    if ((rc = zt_split_operand(p, X, 1, -1, s, gate))) return rc;
+    if ((rc = zt_split_operand(p, Y, 0, 0, s, gate))) return rc;
+    return zt_split_product(p, 0, C, alpha, lower_only, s, gate);
 }
 
 // ---------------------------------------------------------------------------

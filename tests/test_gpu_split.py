@@ -67,7 +67,7 @@ def test_split_product_accuracy(N):
     assert _rel(got, want) < 1e-12
 
 
-@pytest.mark.parametrize("s,beta,eg", [(3, 8, 2), (6, 8, 4), (7, 7, 4), (8, 7, 8), (5, 6, 5)])
+@pytest.mark.parametrize("s,beta,eg", [(3, 8, 2), (6, 8, 4), (6, 7, 4), (6, 7, 3), (7, 7, 4), (8, 7, 8), (5, 6, 5)])
 def test_split_tunings(s, beta, eg):
     # short exact chunks (beta = 8) force many accumulator drains per tile
     N = 1024
@@ -140,3 +140,14 @@ def test_cluster_shapes(cm, cn):
         z.isomp_step(plan, Wd, h)
     want, _ = oracle.isomp_run(W0, h, 2)
     assert _rel(Wd.cpu().numpy(), want) <= 1e-10
+
+
+def test_autotuner_picks_an_accurate_tuning(tmp_path, monkeypatch):
+    from paper_2206_05466_gb300 import autotune
+
+    monkeypatch.setenv("ZEITLIN_TUNE_CACHE", str(tmp_path / "tune.json"))
+    res = autotune.autotune(256, target=1e-11)
+    assert res["rel_err"] <= 1e-11
+    assert all("rel_err" in t for t in res["trials"])
+    again = autotune.autotune(256, target=1e-11)   # served from the cache
+    assert again["tuning"] == res["tuning"]
