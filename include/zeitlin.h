@@ -57,6 +57,8 @@ typedef struct zt_tuning {
     int sweeps_per_sync; /* sweeps enqueued between host convergence checks (def. 4) */
     int cluster_m;       /* SPLIT: CTAs sharing each B'^T tile by TMA multicast (1, 2, 4; def. 2) */
     int cluster_n;       /* SPLIT: CTAs sharing each X' tile by TMA multicast (1, 2, 4; def. 1) */
+    int dense;           /* SPLIT: 1 = multiply every digit pair; 0 (default) = skip digit-pair
+                            tiles that are exactly zero (identical results)                  */
 } zt_tuning;
 
 typedef struct zt_step_stats {

@@ -54,7 +54,9 @@ constexpr int B_TILE = BN * BK * 2;
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
 constexpr int NTHREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;  // two 128 x 256 FP32 accumulators
-constexpr size_t SMEM_BYTES = 1024 /*align slack*/ + (size_t)STAGES * STAGE_BYTES + 256 /*barriers*/;
+constexpr int MAX_KB = 512;        // K blocks of 64 for N <= 16384
+constexpr size_t SMEM_BYTES =
+    1024 /*align slack*/ + (size_t)STAGES * STAGE_BYTES + 256 /*barriers*/ + 2 * MAX_KB /*digit occupancy*/;
 constexpr int EXP_NAN = 0x7fff;    // row exponent marking a non-finite entry
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
 
@@ -71,11 +73,19 @@ struct zt_split_ws {
     __nv_bfloat16* dB[2] = {nullptr, nullptr};   // two B'^T slots, each [s][Npad][ldk]
     int* eA = nullptr;                           // [Mpad]
     int* eB[2] = {nullptr, nullptr};             // [Npad]
+    int nkb = 0, ngA = 0, ngB = 0;               // K blocks; row groups of X'; column groups of B'^T
+    int skip_zero = 1;                           // skip digit-pair units whose tiles are all zero
+    int* occA = nullptr;                         // [ngA][nkb]
+    int* occB[2] = {nullptr, nullptr};           // [ngB][nkb]
     CUtensorMap tmA, tmB[2];
 };
 
 struct SplitArgs {
     int N, s, beta, ldk, Mpad, Npad, u, exact_groups, ntn, lower_only;
+    // digit occupancy per (row group, K block): s - (first nonzero digit), 0 = all zero;
+    // NULL disables zero-unit skipping
+    const int* occA;
+    const int* occB;
     int cm, cn;        // cluster shape: cm row tiles share B'^T slices, cn column tiles share X' slices
     int ntmg, ntng;    // tile groups (one cluster each) along rows and columns
     double alpha;
@@ -240,6 +250,7 @@ __global__ void __launch_bounds__(256)
 split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk,
                   __nv_bfloat16* __restrict__ dA, int Mpad, int* __restrict__ eA,
                   __nv_bfloat16* __restrict__ dB, int Npad, int* __restrict__ eB,
+                  int* __restrict__ occA, int occA_rows, int* __restrict__ occB, int occB_rows,
                   const zt_dev_state* st, int gate) {
     if (zt_gate_skip(st, gate)) return;
     const int j = blockIdx.x;
@@ -264,14 +275,20 @@ split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk
     const int sb = s * beta;
     const long long R = 1LL << beta, H = R >> 1;
     const size_t planeA = (size_t)Mpad * ldk, planeB = (size_t)Npad * ldk;
-    // each thread: 4 consecutive complex entries -> one 16-byte store per plane and row
-    for (int kq = threadIdx.x; kq < ldk / 8; kq += 256) {
+    // each thread: 4 consecutive complex entries -> one 16-byte store per plane and row;
+    // 8 consecutive threads cover one K block of 64 reals (occupancy reduced by shuffles)
+    const int nkb = ldk / 64;
+    const int iters = (ldk / 8 + 255) / 256;
+    for (int it = 0; it < iters; ++it) {
+        const int kq = threadIdx.x + 256 * it;
+        const bool live = kq < ldk / 8;
+        int fz = s;   // first nonzero digit of this thread's entries (s: none)
         long long vr[4], vi[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int k = 4 * kq + u;
             vr[u] = vi[u] = 0;
-            if (k < N && !bad) {
+            if (live && k < N && !bad) {
                 const double2 v = row[k];
                 vr[u] = to_fixed(v.x, e, sb);
                 vi[u] = to_fixed(v.y, e, sb);
@@ -279,6 +296,7 @@ split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk
         }
         for (int p = s - 1; p >= 0; --p) {
             __align__(16) __nv_bfloat162 wa[4], wb0[4], wb1[4];
+            bool nz = false;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 long long dr, di;
@@ -291,12 +309,15 @@ split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk
                     dr = vr[u];
                     di = vi[u];
                 }
+                nz |= (dr != 0) | (di != 0);
                 const float fr = (float)dr, fi = (float)di;
                 wa[u] = __floats2bfloat162_rn(fr, fi);
                 // B'^T row 2j: interleaved(y); row 2j+1: interleaved(i y) = (-im, re)
                 wb0[u] = __floats2bfloat162_rn(fr, fi);
                 wb1[u] = __floats2bfloat162_rn(-fi, fr);
             }
+            if (nz) fz = p;
+            if (!live) continue;
             const size_t col = (size_t)8 * kq;
             if (dA) *reinterpret_cast<uint4*>(dA + p * planeA + (size_t)j * ldk + col) = *reinterpret_cast<uint4*>(wa);
             if (dB) {
@@ -304,6 +325,15 @@ split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk
                 *reinterpret_cast<uint4*>(dB + p * planeB + (size_t)(2 * j + 1) * ldk + col) =
                     *reinterpret_cast<uint4*>(wb1);
             }
+        }
+        int occ = s - fz;   // 0: all digits zero, s: leading digit present
+        occ = max(occ, __shfl_xor_sync(0xffffffffu, occ, 1));
+        occ = max(occ, __shfl_xor_sync(0xffffffffu, occ, 2));
+        occ = max(occ, __shfl_xor_sync(0xffffffffu, occ, 4));
+        if (live && (kq & 7) == 0) {
+            const int kb = kq >> 3;
+            if (occA) atomicMax(&occA[(size_t)(j / occA_rows) * nkb + kb], occ);
+            if (occB) atomicMax(&occB[(size_t)(j / occB_rows) * nkb + kb], occ);
         }
     }
     if (threadIdx.x == 0) {
@@ -314,6 +344,14 @@ split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk
             eB[2 * j + 1] = ee;
         }
     }
+}
+
+// A segment (digit group g, K blocks [kb0, kend)) has a nonzero unit iff some
+// K block has fa + fb <= g.
+__device__ __forceinline__ bool seg_has_units(const uint8_t* fa, const uint8_t* fb, int g, int kb0, int kend) {
+    for (int kb = kb0; kb < kend; ++kb)
+        if (fa[kb] + fb[kb] <= g) return true;
+    return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -334,6 +372,8 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint64_t* drain = acce + 2;        // [1]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    uint8_t* fa = reinterpret_cast<uint8_t*>(full) + 256;   // [MAX_KB] first nonzero X' digit per K block
+    uint8_t* fb = fa + MAX_KB;                               // [MAX_KB] first nonzero B'^T digit
 
     // Tile coordinates.  A cluster of cm x cn CTAs owns a group of cm row
     // tiles and cn column tiles; CTA rank r sits at (r % cm, r / cm).
@@ -386,6 +426,12 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // Digit occupancy of this cluster's row group (X') and column group (B'^T):
+    // the unit (p, q, kb) is all zero unless p >= fa[kb] and q >= fb[kb].
+    for (int kb = threadIdx.x; kb < nkb; kb += NTHREADS) {
+        fa[kb] = a.occA ? (uint8_t)(a.s - a.occA[(size_t)tig * nkb + kb]) : 0;
+        fb[kb] = a.occB ? (uint8_t)(a.s - a.occB[(size_t)tjg * nkb + kb]) : 0;
+    }
     tc_fence_before();
     if (cs > 1)
         cluster_sync();   // peers' barriers exist before any multicast lands
@@ -404,7 +450,7 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                 for (int kb0 = 0; kb0 < nkb && ok; kb0 += kc) {
                     const int kend = min(kb0 + kc, nkb);
                     for (int kb = kb0; kb < kend && ok; ++kb) {
-                        for (int p = 0; p <= g; ++p) {
+                        for (int p = fa[kb]; p <= g - fb[kb]; ++p) {
                             if (!mbar_wait(&empty[stage], ph ^ 1, abort_flag)) {
                                 ok = false;
                                 break;
@@ -437,10 +483,12 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             bool ok = true;
             for (int g = 0; g < a.s && ok; ++g) {
                 const int kc = seg_kblocks(g, a.beta, a.exact_groups, nkb);
-                for (int kb0 = 0; kb0 < nkb && ok; kb0 += kc, ++seg) {
+                for (int kb0 = 0; kb0 < nkb && ok; kb0 += kc) {
                     const int kend = min(kb0 + kc, nkb);
+                    if (!seg_has_units(fa, fb, g, kb0, kend)) continue;
                     const int b = seg & 1;
-                    if (!mbar_wait(&acce[b], ((seg >> 1) & 1) ^ 1, abort_flag)) {
+                    ++seg;
+                    if (!mbar_wait(&acce[b], (((seg - 1) >> 1) & 1) ^ 1, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -448,7 +496,7 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                     const uint32_t d = tmem + (uint32_t)(b * BN);
                     bool first = true;
                     for (int kb = kb0; kb < kend && ok; ++kb) {
-                        for (int p = 0; p <= g; ++p) {
+                        for (int p = fa[kb]; p <= g - fb[kb]; ++p) {
                             if (!mbar_wait(&full[stage], ph, abort_flag)) {
                                 ok = false;
                                 break;
@@ -490,9 +538,11 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         for (int g = 0; g < a.s && ok; ++g) {
             const int kc = seg_kblocks(g, a.beta, a.exact_groups, nkb);
             const int sh = (a.s - 1 - g) * a.beta - a.u;
-            for (int kb0 = 0; kb0 < nkb; kb0 += kc, ++seg) {
+            for (int kb0 = 0; kb0 < nkb; kb0 += kc) {
+                if (!seg_has_units(fa, fb, g, kb0, min(kb0 + kc, nkb))) continue;
                 const int b = seg & 1;
-                if (!mbar_wait(&accf[b], (seg >> 1) & 1, abort_flag)) {
+                ++seg;
+                if (!mbar_wait(&accf[b], (((seg - 1) >> 1) & 1), abort_flag)) {
                     ok = false;
                     break;
                 }
@@ -518,7 +568,7 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                                 v1 = (v1 + (1LL << (-sh - 1))) >> (-sh);
                             }
                             longlong2* p2 = reinterpret_cast<longlong2*>(dst + 2 * q);
-                            if (seg != 0) {
+                            if (seg != 1) {   // the first drained segment initialises the accumulator
                                 const longlong2 o = *p2;
                                 v0 += o.x;
                                 v1 += o.y;
@@ -536,7 +586,7 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             const int off = -(a.s + 1) * a.beta + 2 + a.u;
             for (int c = c0; c < c0 + BN && c < ncols; ++c) {
                 const int eb = a.eB[c];
-                const long long v = Crow[c];
+                const long long v = seg ? Crow[c] : 0;   // no drained segment: all digit products were zero
                 double out;
                 if (ea == EXP_NAN || eb == EXP_NAN) {
                     out = __longlong_as_double(0x7ff8000000000000LL);
@@ -618,6 +668,7 @@ int zt_split_create(zt_plan* p) {
     w->exact_groups = eg;
     w->cm = cm;
     w->cn = cn;
+    w->skip_zero = p->tun.dense ? 0 : 1;
     w->ldk = round_up(2 * N, BK);
     w->Mpad = round_up(N, BM * cm);
     w->Npad = round_up(2 * N, BN * cn);
@@ -639,7 +690,15 @@ int zt_split_create(zt_plan* p) {
     ZT_CU(cudaMemset(w->eA, 0, (size_t)w->Mpad * sizeof(int)));
     int rc;
     if ((rc = make_map(&w->tmA, w->dA, s * w->Mpad, w->ldk, BM / cn))) return rc;
+    w->nkb = w->ldk / BK;
+    if (w->nkb > MAX_KB) return zt_fail(ZT_EINVAL, "N too large for the split product (K blocks > %d)", MAX_KB);
+    w->ngA = w->Mpad / (BM * cm);
+    w->ngB = w->Npad / (BN * cn);
+    ZT_CU(cudaMalloc(&w->occA, (size_t)w->ngA * w->nkb * sizeof(int)));
+    ZT_CU(cudaMemset(w->occA, 0, (size_t)w->ngA * w->nkb * sizeof(int)));
     for (int b = 0; b < 2; ++b) {
+        ZT_CU(cudaMalloc(&w->occB[b], (size_t)w->ngB * w->nkb * sizeof(int)));
+        ZT_CU(cudaMemset(w->occB[b], 0, (size_t)w->ngB * w->nkb * sizeof(int)));
         ZT_CU(cudaMalloc(&w->dB[b], szB));
         ZT_CU(cudaMemset(w->dB[b], 0, szB));
         ZT_CU(cudaMalloc(&w->eB[b], (size_t)w->Npad * sizeof(int)));
@@ -655,9 +714,11 @@ void zt_split_destroy(zt_plan* p) {
     if (!w) return;
     cudaFree(w->dA);
     cudaFree(w->eA);
+    cudaFree(w->occA);
     for (int b = 0; b < 2; ++b) {
         cudaFree(w->dB[b]);
         cudaFree(w->eB[b]);
+        cudaFree(w->occB[b]);
     }
     delete w;
     p->split = nullptr;
@@ -669,10 +730,15 @@ int zt_split_operand(zt_plan* p, const double2* X, int to_a, int b_slot, cudaStr
     const int N = p->N;
     const double bytes = 16.0 * N * N + (to_a ? 2.0 * w->s * (double)N * w->ldk : 0.0) +
                          (b_slot >= 0 ? 4.0 * w->s * (double)N * w->ldk : 0.0);
+    // occupancy is reduced with atomicMax over the rows of each group: start from 0
+    if (to_a) ZT_CU(cudaMemsetAsync(w->occA, 0, (size_t)w->ngA * w->nkb * sizeof(int), s));
+    if (b_slot >= 0) ZT_CU(cudaMemsetAsync(w->occB[b_slot], 0, (size_t)w->ngB * w->nkb * sizeof(int), s));
     const int t = zt_timer_begin(p, ZT_KERNEL_SPLIT, bytes, bytes, s);
     split_rows_kernel<<<N, 256, 0, s>>>(X, N, w->s, w->beta, w->ldk, to_a ? w->dA : nullptr, w->Mpad,
                                         to_a ? w->eA : nullptr, b_slot >= 0 ? w->dB[b_slot] : nullptr, w->Npad,
-                                        b_slot >= 0 ? w->eB[b_slot] : nullptr, p->state, gate);
+                                        b_slot >= 0 ? w->eB[b_slot] : nullptr, to_a ? w->occA : nullptr,
+                                        BM * w->cm, b_slot >= 0 ? w->occB[b_slot] : nullptr, (BN / 2) * w->cn,
+                                        p->state, gate);
     zt_timer_end(p, t, s);
     p->launches++;
     cudaError_t e = cudaGetLastError();
@@ -699,6 +765,8 @@ int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower
     a.cn = w->cn;
     a.ntmg = w->Mpad / (BM * w->cm);
     a.ntng = w->Npad / (BN * w->cn);
+    a.occA = w->skip_zero ? w->occA : nullptr;
+    a.occB = w->skip_zero ? w->occB[b_slot] : nullptr;
     a.alpha = alpha;
     a.eA = w->eA;
     a.eB = w->eB[b_slot];
@@ -848,9 +916,9 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
         while (bound >= std::ldexp(1.0, 62 + u)) ++u;
     }
     split_rows_kernel<<<N, 256, 0, s>>>((const double2*)X, N, NA_S, NA_BETA, NA_LDK, dA, NA_MPAD, eA, nullptr,
-                                        NA_NPAD, nullptr, st, ZT_GATE_NONE);
+                                        NA_NPAD, nullptr, nullptr, 1, nullptr, 1, st, ZT_GATE_NONE);
     split_rows_kernel<<<N, 256, 0, s>>>((const double2*)Y, N, NA_S, NA_BETA, NA_LDK, nullptr, NA_MPAD, nullptr, dB,
-                                        NA_NPAD, eB, st, ZT_GATE_NONE);
+                                        NA_NPAD, eB, nullptr, 1, nullptr, 1, st, ZT_GATE_NONE);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "split_rows_kernel");
     SplitArgs a;
@@ -868,6 +936,8 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
     a.cn = 1;
     a.ntmg = NA_MPAD / BM;
     a.ntng = NA_NPAD / BN;
+    a.occA = nullptr;   // no zero-unit skipping: every digit pair is multiplied
+    a.occB = nullptr;
     a.alpha = -1.0;
     a.eA = eA;
     a.eB = eB;

@@ -36,7 +36,7 @@ HEADER = os.path.join(_build.ROOT, "include", "zeitlin.h")
 class Tuning(ctypes.Structure):
     _fields_ = [("slices", ctypes.c_int), ("digit_bits", ctypes.c_int), ("exact_groups", ctypes.c_int),
                 ("final_mode", ctypes.c_int), ("sweeps_per_sync", ctypes.c_int), ("cluster_m", ctypes.c_int),
-                ("cluster_n", ctypes.c_int)]
+                ("cluster_n", ctypes.c_int), ("dense", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -132,11 +132,12 @@ class Plan:
     """A zt_plan: constant Laplacian factors plus step workspace for one N."""
 
     def __init__(self, N: int, precision: int = PRECISION_FP64, slices=0, digit_bits=0,
-                 exact_groups=0, final_mode=FINAL_FRESH, sweeps_per_sync=0, cluster_m=0, cluster_n=0):
+                 exact_groups=0, final_mode=FINAL_FRESH, sweeps_per_sync=0, cluster_m=0, cluster_n=0, dense=0):
         L = load()
         self.N = int(N)
         self.precision = precision
-        tun = Tuning(slices, digit_bits, exact_groups, final_mode, sweeps_per_sync, cluster_m, cluster_n)
+        tun = Tuning(slices, digit_bits, exact_groups, final_mode, sweeps_per_sync, cluster_m, cluster_n,
+                     1 if dense else 0)
         h = ctypes.c_void_p()
         _check(L.zt_plan_create(self.N, precision, ctypes.byref(tun), ctypes.byref(h)))
         self._h = h

@@ -151,3 +151,38 @@ def test_autotuner_picks_an_accurate_tuning(tmp_path, monkeypatch):
     assert all("rel_err" in t for t in res["trials"])
     again = autotune.autotune(256, target=1e-11)   # served from the cache
     assert again["tuning"] == res["tuning"]
+
+
+def _band(N, width, seed, skew):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    i = np.arange(N)
+    X[np.abs(i[:, None] - i[None, :]) > width] = 0
+    if skew:
+        X = (X - X.conj().T) / 2
+    return X
+
+
+@pytest.mark.parametrize("N", [300, 1024])
+def test_zero_unit_skipping_is_exact(N):
+    # Skipping digit-pair tiles that are exactly zero must not change a single bit:
+    # decaying matrices (leading digits vanish off the diagonal) and banded ones
+    # (whole output tiles without any nonzero unit).
+    W = vorticity_w0(N, seed=6)
+    P = oracle.stream_solve(W)
+    cases = [(P, W), (_band(N, 20, 1, False), _band(N, 20, 2, True)), (W, P)]
+    for X, Y in cases:
+        dense = _gemm(_split_plan(N, dense=1), X, Y)
+        skip = _gemm(_split_plan(N), X, Y)
+        assert np.array_equal(dense, skip)
+        assert _rel(skip, X @ Y) < 1e-12
+
+
+def test_banded_product_has_zero_far_tiles():
+    N = 1024
+    X, Y = _band(N, 10, 3, False), _band(N, 10, 4, True)
+    got = _gemm(_split_plan(N), X, Y)
+    i = np.arange(N)
+    far = np.abs(i[:, None] - i[None, :]) > 20
+    assert np.all(got[far] == 0)
+    assert _rel(got, X @ Y) < 1e-12
