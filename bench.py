@@ -355,6 +355,8 @@ def run_gpu(args):
     if rank != 0:
         return 0
     pairs = tun["slices"] * (tun["slices"] + 1) / 2
+    # dense equivalent: every digit pair on every computed tile of the timed launches
+    dense_work = pairs * prod["work_alg"] if prod["work_alg"] else None
     achieved = prod["work"] / (prod["total_ms"] / 1e3) / 1e12 if prod["total_ms"] else None
     peak = peaks["bf16_tflops_sustained"]
     src = open(os.path.join(ROOT, "paper_2206_05466_gb300", "csrc", "zt_split.cu"), "rb").read()
@@ -376,7 +378,9 @@ def run_gpu(args):
         "roofline": {"bound": "tensor", "kernel": "zgemm_split_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": f"{peaks['source']} bf16 sustained",
-                     "work": "BF16 digit-pair products issued (s(s+1)/2 pairs x 2 x 128 x 256 x K' per tile)",
+                     "work": "BF16 digit-pair MMA units issued (2 x 128 x 256 x 64 flops each, counted on the "
+                             "device; exactly-zero digit tiles are skipped)",
+                     "dense_units_fraction_issued": prod["work"] / dense_work if dense_work else None,
                      "launches": prod["launches"], "avg_launch_ms": prod["total_ms"] / max(1, prod["launches"]),
                      "fp64_equivalent_tflops": prod["work_alg"] / (prod["total_ms"] / 1e3) / 1e12
                      if prod["total_ms"] else None,

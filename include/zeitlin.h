@@ -142,7 +142,8 @@ ZT_API long zt_plan_launch_count(const zt_plan* plan);
  * the kernel classes below, and sums, per class, the elapsed time and the
  * algorithmic work of the launches that did work (sweeps skipped after
  * convergence are not counted).  Work units: ZT_KERNEL_PRODUCT -- tensor
- * FLOPs issued (SPLIT: BF16 digit-pair products over the computed tiles;
+ * FLOPs issued (SPLIT: 2 x 128 x 256 x 64 per digit-pair MMA unit actually
+ * issued, counted on the device, so all-zero units skipped are not counted;
  * FP64: 8 flops per complex multiply-add over the computed tiles) and, in
  * work_alg, FP64-equivalent FLOPs of the complex product (8 N^3 for a full
  * product, 4 N^2 (N+1) for the lower triangle); ZT_KERNEL_SOLVE -- bytes

@@ -87,6 +87,7 @@ struct zt_plan {
     long launches = 0;
     // measurement hook
     int timing = 0;
+    unsigned long long* d_units = nullptr;   // MMA units (128 x 256 x 64) issued by split products
     int cur_sweep = -1;
     zt_timer_rec* recs = nullptr;
     int nrecs = 0, caprecs = 0;

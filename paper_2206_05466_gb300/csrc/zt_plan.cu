@@ -90,6 +90,7 @@ extern "C" int zt_plan_set_timing(zt_plan* p, int enable) {
     int rc = timer_collect(p, -1, -2);
     if (rc) return rc;
     p->timing = enable ? 1 : 0;
+    if (p->d_units) ZT_CU(cudaMemset(p->d_units, 0, sizeof(unsigned long long)));
     for (int k = 0; k < ZT_KERNEL_KINDS; ++k) {
         p->t_n[k] = 0;
         p->t_ms[k] = p->t_work[k] = p->t_work_alg[k] = 0.0;
@@ -105,7 +106,14 @@ extern "C" int zt_plan_kernel_time(zt_plan* p, int kind, long* launches, double*
     if (rc) return rc;
     if (launches) *launches = p->t_n[kind];
     if (total_ms) *total_ms = p->t_ms[kind];
-    if (work) *work = p->t_work[kind];
+    double extra = 0.0;
+    if (kind == ZT_KERNEL_PRODUCT && p->d_units) {   // split products: units issued on the device
+        unsigned long long units = 0;
+        ZT_CU(cudaDeviceSynchronize());
+        ZT_CU(cudaMemcpy(&units, p->d_units, sizeof units, cudaMemcpyDeviceToHost));
+        extra = (double)units * 2.0 * 128.0 * 256.0 * 64.0;
+    }
+    if (work) *work = p->t_work[kind] + extra;
     if (work_alg) *work_alg = p->t_work_alg[kind];
     return ZT_OK;
 }
@@ -337,6 +345,7 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     cudaFree(p->B);
     cudaFree(p->partials);
     cudaFree(p->state);
+    cudaFree(p->d_units);
     if (p->h_state) cudaFreeHost(p->h_state);
     for (int i = 0; i < p->caprecs; ++i) {
         if (p->recs[i].a) cudaEventDestroy(p->recs[i].a);
@@ -397,6 +406,8 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     p->npartials = nt * (nt + 1) / 2;
     ZT_TRY(cudaMalloc(&p->partials, (size_t)p->npartials * sizeof(double)));
     ZT_TRY(cudaMalloc(&p->state, sizeof(zt_dev_state)));
+    ZT_TRY(cudaMalloc(&p->d_units, sizeof(unsigned long long)));
+    ZT_TRY(cudaMemset(p->d_units, 0, sizeof(unsigned long long)));
     ZT_TRY(cudaMallocHost(&p->h_state, sizeof(zt_dev_state)));
     ZT_TRY(cudaMemset(p->state, 0, sizeof(zt_dev_state)));
     rc = zt_solve_create(p);
