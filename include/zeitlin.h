@@ -161,6 +161,35 @@ ZT_API int zt_plan_set_timing(zt_plan* plan, int enable);
 ZT_API int zt_plan_kernel_time(zt_plan* plan, int kind, long* launches, double* total_ms,
                                double* work, double* work_alg);
 
+/* ---- Ensembles: grouped steps over many independent instances ----------
+ *
+ * A batch binds `count` existing plans (any mix of N and precision; split
+ * instances must share the cluster shape, all must share the final mode),
+ * their device state matrices W[i] (caller-owned, bound for the batch's
+ * lifetime) and their time steps h[i].  One batched step advances every
+ * instance by one IsoMP step exactly as isomp_step would, bit for bit, but
+ * each kernel of the step is one grouped launch over all instances; each
+ * instance keeps its own device convergence state, so instances that
+ * converge early are masked off while the others keep sweeping (Sec. 2,
+ * Eqs. 8-9, applied to an ensemble).  A plan may belong to one batch at a
+ * time and must not be stepped on its own while the batch is in use. */
+typedef struct zt_batch zt_batch;
+ZT_API int zt_batch_create(int count, zt_plan* const* plans, double* const* W, const double* h, zt_batch** out);
+ZT_API void zt_batch_destroy(zt_batch* batch);
+/* Capture the step's launch sequence into CUDA graphs on the next step and
+ * replay them afterwards (1 = on, 0 = off; default off). */
+ZT_API int zt_batch_set_graph(zt_batch* batch, int enable);
+/* One step of every instance.  `stats` (host array of `count`, may be NULL)
+ * receives each instance's sweeps and residual.  Blocks the host thread until
+ * the step is done (one synchronisation per step while all instances converge
+ * within sweeps_per_sync sweeps).  Returns the worst status over instances. */
+ZT_API int isomp_step_batched(zt_batch* batch, double tol, int maxit, zt_step_stats* stats, void* stream);
+/* nsteps batched steps; `stats` receives totals over all instances and steps. */
+ZT_API int isomp_run_batched(zt_batch* batch, long nsteps, double tol, int maxit, zt_run_stats* stats,
+                             void* stream);
+/* Kernel launches enqueued by the batch so far. */
+ZT_API long zt_batch_launch_count(const zt_batch* batch);
+
 /* Allocation-free split-precision product (no counterpart in the paper).
  *
  * Computes the same C = X Y, Y skew-Hermitian, as zt_zgemm_skew with a

@@ -1,0 +1,506 @@
+// Grouped IsoMP steps over many independent instances (ensembles, serving).
+//
+// A batch binds existing plans (each with its own N, precision and
+// workspace), their state matrices W and their time steps h.  One batched
+// step runs the same sequence as isomp_step, but every kernel is one grouped
+// launch over all instances (per-instance arguments in device tables, CTAs
+// mapped to instances through prefix sums).  Each instance keeps its own
+// device convergence state, so members that converge early are masked off by
+// the kernels' gates while the others keep sweeping; one host
+// synchronisation per step reads all states.  Optionally the launch sequence
+// of a step is captured once into CUDA graphs and replayed.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "zt_internal.h"
+
+namespace {
+
+struct CopyArgs {   // W -> W_n and W -> Wt
+    const double2* src;
+    double2* d1;
+    double2* d2;
+    long long count;
+};
+constexpr int COPY_PER_CTA = 256 * 4;
+
+struct Op {          // one grouped launch: table and CTA prefix sums in device memory
+    void* tab = nullptr;
+    int* offs = nullptr;
+    int n = 0;
+    int total = 0;
+    int cluster = 1;
+};
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) copy_grouped(const CopyArgs* tab, const int* offs, int n) {
+    const int inst = zt_group_find(offs, n, blockIdx.x);
+    const CopyArgs a = tab[inst];
+    const long long base = (long long)(blockIdx.x - offs[inst]) * COPY_PER_CTA;
+    for (int q = 0; q < 4; ++q) {
+        const long long i = base + threadIdx.x + 256 * q;
+        if (i < a.count) {
+            const double2 v = a.src[i];
+            a.d1[i] = v;
+            a.d2[i] = v;
+        }
+    }
+}
+
+__global__ void state_init_grouped(zt_dev_state* const* sts, int n, double tol, int maxit) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    zt_dev_state* st = sts[i];
+    st->done = 0;
+    st->iters = 0;
+    st->converged = 0;
+    st->nonfinite = 0;
+    st->timeout = 0;
+    st->maxit = maxit;
+    st->residual = 0.0;
+    st->tol = tol;
+    st->finalized = 0;
+}
+
+__global__ void state_gather(zt_dev_state* const* sts, int n, zt_dev_state* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = *sts[i];
+}
+
+struct zt_batch {
+    int n = 0;
+    int device = 0;
+    int final_mode = ZT_FINAL_FRESH;
+    std::vector<zt_plan*> plans;
+    std::vector<double2*> W;
+    std::vector<double> h;
+    unsigned char* dbuf = nullptr;   // all tables
+    zt_dev_state** dstates = nullptr;
+    zt_dev_state* gathered = nullptr;
+    zt_dev_state* hstates = nullptr;   // pinned
+    Op copy, solve, split_P, split_W, split_A, gemm1, gemm2, f64a, f64b, upd_sweep, upd_final, conv;
+    int sweeps_per_sync = 4;
+    long launches = 0;
+    int use_graph = 0;
+    cudaGraphExec_t g_first = nullptr, g_more = nullptr;
+    long g_first_k = 0, g_more_k = 0;   // kernels in each graph
+    cudaStream_t g_stream = nullptr;
+    int g_tol_maxit_set = 0;
+    double g_tol = 0.0;
+    int g_maxit = 0;
+};
+
+namespace {
+
+// Host-side builder: collects tables, then uploads them in one allocation.
+struct Builder {
+    std::vector<unsigned char> bytes;
+    struct Pending {
+        Op* op;
+        size_t tab_off, offs_off;
+    };
+    std::vector<Pending> pend;
+
+    size_t put(const void* src, size_t n, size_t align) {
+        size_t off = (bytes.size() + align - 1) / align * align;
+        bytes.resize(off + n);
+        if (n) std::memcpy(bytes.data() + off, src, n);
+        return off;
+    }
+    template <class T>
+    void add(Op* op, const std::vector<T>& tab, const std::vector<int>& ctas, int cluster = 1) {
+        std::vector<int> offs(ctas.size() + 1, 0);
+        for (size_t i = 0; i < ctas.size(); ++i) offs[i + 1] = offs[i] + ctas[i];
+        op->n = (int)tab.size();
+        op->total = offs.back();
+        op->cluster = cluster;
+        const size_t t = put(tab.data(), tab.size() * sizeof(T), 128);
+        const size_t o = put(offs.data(), offs.size() * sizeof(int), 16);
+        pend.push_back({op, t, o});
+    }
+    int upload(zt_batch* b) {
+        if (bytes.empty()) return ZT_OK;
+        ZT_CU(cudaMalloc(&b->dbuf, bytes.size()));
+        ZT_CU(cudaMemcpy(b->dbuf, bytes.data(), bytes.size(), cudaMemcpyHostToDevice));
+        for (auto& q : pend) {
+            q.op->tab = b->dbuf + q.tab_off;
+            q.op->offs = reinterpret_cast<int*>(b->dbuf + q.offs_off);
+        }
+        return ZT_OK;
+    }
+};
+
+int count_launch(zt_batch* b, const char* what) {
+    b->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, what);
+    return ZT_OK;
+}
+
+// Pt = solve(Wt), A = Pt Wt, B = A Pt for every instance (grouped launches).
+int enqueue_products(zt_batch* b, cudaStream_t s, int gate) {
+    int rc;
+    if ((rc = zt_solve_grouped((const SolveArgs*)b->solve.tab, b->solve.offs, b->solve.n, b->solve.total, s,
+                               gate)))
+        return rc;
+    b->launches += 3;
+    if (b->gemm1.n) {
+        if ((rc = zt_split_rows_grouped((const SplitRowsArgs*)b->split_P.tab, b->split_P.offs, b->split_P.n,
+                                        b->split_P.total, s, gate)))
+            return rc;
+        if ((rc = zt_split_rows_grouped((const SplitRowsArgs*)b->split_W.tab, b->split_W.offs, b->split_W.n,
+                                        b->split_W.total, s, gate)))
+            return rc;
+        if ((rc = zt_split_gemm_grouped((const GemmEntry*)b->gemm1.tab, b->gemm1.offs, b->gemm1.n, b->gemm1.total,
+                                        b->gemm1.cluster, s, gate)))
+            return rc;
+        if ((rc = zt_split_rows_grouped((const SplitRowsArgs*)b->split_A.tab, b->split_A.offs, b->split_A.n,
+                                        b->split_A.total, s, gate)))
+            return rc;
+        if ((rc = zt_split_gemm_grouped((const GemmEntry*)b->gemm2.tab, b->gemm2.offs, b->gemm2.n, b->gemm2.total,
+                                        b->gemm2.cluster, s, gate)))
+            return rc;
+        b->launches += 8;
+    }
+    if (b->f64a.n) {
+        if ((rc = zt_fp64_gemm_grouped((const Fp64GemmArgs*)b->f64a.tab, b->f64a.offs, b->f64a.n, b->f64a.total, s,
+                                       gate)))
+            return rc;
+        if ((rc = zt_fp64_gemm_grouped((const Fp64GemmArgs*)b->f64b.tab, b->f64b.offs, b->f64b.n, b->f64b.total, s,
+                                       gate)))
+            return rc;
+        b->launches += 2;
+    }
+    return ZT_OK;
+}
+
+int enqueue_sweep(zt_batch* b, cudaStream_t s) {
+    int rc;
+    if ((rc = enqueue_products(b, s, ZT_GATE_SWEEP))) return rc;
+    if ((rc = zt_update_grouped((const UpdateArgs*)b->upd_sweep.tab, b->upd_sweep.offs, b->upd_sweep.n,
+                                b->upd_sweep.total, s, ZT_GATE_SWEEP)))
+        return rc;
+    b->launches++;
+    if ((rc = zt_converge_grouped((const ConvArgs*)b->conv.tab, b->conv.n, s))) return rc;
+    b->launches++;
+    return ZT_OK;
+}
+
+int enqueue_final(zt_batch* b, cudaStream_t s) {
+    int rc;
+    if (b->final_mode == ZT_FINAL_FRESH && (rc = enqueue_products(b, s, ZT_GATE_FINAL))) return rc;
+    if ((rc = zt_update_grouped((const UpdateArgs*)b->upd_final.tab, b->upd_final.offs, b->upd_final.n,
+                                b->upd_final.total, s, ZT_GATE_FINAL)))
+        return rc;
+    b->launches++;
+    return ZT_OK;
+}
+
+int enqueue_read_states(zt_batch* b, cudaStream_t s) {
+    state_gather<<<(b->n + 127) / 128, 128, 0, s>>>(b->dstates, b->n, b->gathered);
+    int rc = count_launch(b, "state_gather");
+    if (rc) return rc;
+    ZT_CU(cudaMemcpyAsync(b->hstates, b->gathered, (size_t)b->n * sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
+    return ZT_OK;
+}
+
+int enqueue_first_round(zt_batch* b, double tol, int maxit, int nsweeps, cudaStream_t s) {
+    int rc;
+    copy_grouped<<<b->copy.total, 256, 0, s>>>((const CopyArgs*)b->copy.tab, b->copy.offs, b->copy.n);
+    if ((rc = count_launch(b, "copy_grouped"))) return rc;
+    state_init_grouped<<<(b->n + 127) / 128, 128, 0, s>>>(b->dstates, b->n, tol, maxit);
+    if ((rc = count_launch(b, "state_init_grouped"))) return rc;
+    for (int c = 0; c < nsweeps; ++c)
+        if ((rc = enqueue_sweep(b, s))) return rc;
+    if ((rc = enqueue_final(b, s))) return rc;
+    return enqueue_read_states(b, s);
+}
+
+int enqueue_more_round(zt_batch* b, int nsweeps, cudaStream_t s) {
+    int rc;
+    for (int c = 0; c < nsweeps; ++c)
+        if ((rc = enqueue_sweep(b, s))) return rc;
+    if ((rc = enqueue_final(b, s))) return rc;
+    return enqueue_read_states(b, s);
+}
+
+int capture(zt_batch* b, cudaStream_t s, cudaGraphExec_t* out, bool first, double tol, int maxit, int nsweeps) {
+    cudaGraph_t g = nullptr;
+    ZT_CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const long k0 = b->launches;
+    int rc = first ? enqueue_first_round(b, tol, maxit, nsweeps, s) : enqueue_more_round(b, nsweeps, s);
+    (first ? b->g_first_k : b->g_more_k) = b->launches - k0;
+    b->launches = k0;   // counted when the graph is launched
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return zt_cuda_check(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return zt_cuda_check(e, "cudaGraphInstantiate");
+    return ZT_OK;
+}
+
+void drop_graphs(zt_batch* b) {
+    if (b->g_first) cudaGraphExecDestroy(b->g_first);
+    if (b->g_more) cudaGraphExecDestroy(b->g_more);
+    b->g_first = b->g_more = nullptr;
+    b->g_tol_maxit_set = 0;
+}
+
+}  // namespace
+
+extern "C" void zt_batch_destroy(zt_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    drop_graphs(b);
+    cudaFree(b->dbuf);
+    cudaFree(b->dstates);
+    cudaFree(b->gathered);
+    if (b->hstates) cudaFreeHost(b->hstates);
+    delete b;
+}
+
+extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* W, const double* h,
+                               zt_batch** out) {
+    if (!out) return zt_fail(ZT_EINVAL, "zt_batch_create: out is NULL");
+    *out = nullptr;
+    if (count < 1 || !plans || !W || !h) return zt_fail(ZT_EINVAL, "zt_batch_create: empty batch or NULL array");
+    zt_batch* b = new (std::nothrow) zt_batch();
+    if (!b) return zt_fail(ZT_ENOMEM, "host allocation failed");
+    auto fail = [&](int rc) {
+        zt_batch_destroy(b);
+        return rc;
+    };
+    b->n = count;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    b->device = dev;
+    int cluster = 0;
+    for (int i = 0; i < count; ++i) {
+        zt_plan* p = plans[i];
+        if (!p || !W[i]) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: instance %d has a NULL plan or W", i));
+        if (((uintptr_t)W[i]) & 15u) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: W[%d] not 16-byte aligned", i));
+        if (!std::isfinite(h[i])) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: h[%d] not finite", i));
+        if (p->device != dev) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: plans on different devices"));
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == p) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: plan %d appears twice", i));
+        if (i == 0) b->final_mode = p->tun.final_mode;
+        if (p->tun.final_mode != b->final_mode)
+            return fail(zt_fail(ZT_EINVAL, "zt_batch_create: instances must share the final mode"));
+        if (p->tun.sweeps_per_sync < b->sweeps_per_sync || i == 0) b->sweeps_per_sync = p->tun.sweeps_per_sync;
+        if (p->precision == ZT_PRECISION_SPLIT) {
+            const int cs = p->tun.cluster_m * p->tun.cluster_n;
+            if (cluster && cs != cluster)
+                return fail(zt_fail(ZT_EINVAL, "zt_batch_create: split instances must share the cluster shape"));
+            cluster = cs;
+        }
+        b->plans.push_back(p);
+        b->W.push_back(reinterpret_cast<double2*>(W[i]));
+        b->h.push_back(h[i]);
+    }
+    Builder bl;
+    std::vector<CopyArgs> cp;
+    std::vector<SolveArgs> sv;
+    std::vector<SplitRowsArgs> sP, sW, sA;
+    std::vector<GemmEntry> g1, g2;
+    std::vector<Fp64GemmArgs> fa, fb;
+    std::vector<UpdateArgs> us, uf;
+    std::vector<ConvArgs> cv;
+    std::vector<int> c_cp, c_sv, c_sP, c_g1, c_g2, c_fa, c_fb, c_up;
+    int rc;
+    for (int i = 0; i < count; ++i) {
+        zt_plan* p = plans[i];
+        const int N = p->N;
+        const long long nn = (long long)N * N;
+        cp.push_back({b->W[i], p->Wn, p->Wt, nn});
+        c_cp.push_back((int)((nn + COPY_PER_CTA - 1) / COPY_PER_CTA));
+        SolveArgs sa;
+        zt_solve_args(p, p->Wt, p->P, &sa);
+        sv.push_back(sa);
+        c_sv.push_back(zt_solve_ctas(N));
+        if (p->precision == ZT_PRECISION_SPLIT) {
+            SplitRowsArgs ra;
+            if ((rc = zt_split_rows_args(p, p->P, 1, 1, &ra))) return fail(rc);
+            sP.push_back(ra);
+            if ((rc = zt_split_rows_args(p, p->Wt, 0, 0, &ra))) return fail(rc);
+            sW.push_back(ra);
+            if ((rc = zt_split_rows_args(p, p->A, 1, -1, &ra))) return fail(rc);
+            sA.push_back(ra);
+            c_sP.push_back(N);
+            GemmEntry e;
+            int ctas, cl;
+            if ((rc = zt_split_gemm_entry(p, 0, p->A, -1.0, 0, &e, &ctas, &cl))) return fail(rc);
+            g1.push_back(e);
+            c_g1.push_back(ctas);
+            if ((rc = zt_split_gemm_entry(p, 1, p->B, -1.0, 1, &e, &ctas, &cl))) return fail(rc);
+            g2.push_back(e);
+            c_g2.push_back(ctas);
+        } else {
+            Fp64GemmArgs f;
+            int ctas;
+            zt_fp64_gemm_args(p, p->P, p->Wt, p->A, -1.0, 0, &f, &ctas);
+            fa.push_back(f);
+            c_fa.push_back(ctas);
+            zt_fp64_gemm_args(p, p->A, p->P, p->B, -1.0, 1, &f, &ctas);
+            fb.push_back(f);
+            c_fb.push_back(ctas);
+        }
+        const double hh = b->h[i];
+        UpdateArgs u;
+        u.A = p->A;
+        u.B = p->B;
+        u.h2 = hh / 2.0;
+        u.N = N;
+        u.st = p->state;
+        u.gate = ZT_GATE_NONE;
+        u.base = p->Wn;   // sweep: Wt <- W_n + h/2 (A - A^H) + h^2/4 B
+        u.old = p->Wt;
+        u.out = p->Wt;
+        u.c2 = hh * hh / 4.0;
+        u.partials = p->partials;
+        u.final_write = 0;
+        us.push_back(u);
+        u.base = p->Wt;   // final: W_{n+1} = Wt + h/2 (A - A^H) - h^2/4 B
+        u.old = nullptr;
+        u.out = b->W[i];
+        u.c2 = -hh * hh / 4.0;
+        u.partials = nullptr;
+        u.final_write = 1;
+        uf.push_back(u);
+        c_up.push_back(zt_update_ctas(N));
+        cv.push_back({p->partials, p->npartials, p->state});
+    }
+    bl.add(&b->copy, cp, c_cp);
+    bl.add(&b->solve, sv, c_sv);
+    if (!sP.empty()) {
+        bl.add(&b->split_P, sP, c_sP);
+        bl.add(&b->split_W, sW, c_sP);
+        bl.add(&b->split_A, sA, c_sP);
+        bl.add(&b->gemm1, g1, c_g1, cluster);
+        bl.add(&b->gemm2, g2, c_g2, cluster);
+    }
+    if (!fa.empty()) {
+        bl.add(&b->f64a, fa, c_fa);
+        bl.add(&b->f64b, fb, c_fb);
+    }
+    bl.add(&b->upd_sweep, us, c_up);
+    bl.add(&b->upd_final, uf, c_up);
+    std::vector<int> ones(count, 1);
+    bl.add(&b->conv, cv, ones);
+    if ((rc = bl.upload(b))) return fail(rc);
+    std::vector<zt_dev_state*> sts(count);
+    for (int i = 0; i < count; ++i) sts[i] = plans[i]->state;
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->dstates, count * sizeof(zt_dev_state*))) != cudaSuccess)
+        return fail(zt_cuda_check(e, "cudaMalloc"));
+    if ((e = cudaMemcpy(b->dstates, sts.data(), count * sizeof(zt_dev_state*), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return fail(zt_cuda_check(e, "cudaMemcpy"));
+    if ((e = cudaMalloc(&b->gathered, count * sizeof(zt_dev_state))) != cudaSuccess)
+        return fail(zt_cuda_check(e, "cudaMalloc"));
+    if ((e = cudaMallocHost(&b->hstates, count * sizeof(zt_dev_state))) != cudaSuccess)
+        return fail(zt_cuda_check(e, "cudaMallocHost"));
+    *out = b;
+    return ZT_OK;
+}
+
+extern "C" int zt_batch_set_graph(zt_batch* b, int enable) {
+    if (!b) return zt_fail(ZT_EINVAL, "batch is NULL");
+    ZT_CU(cudaDeviceSynchronize());
+    drop_graphs(b);
+    b->use_graph = enable ? 1 : 0;
+    return ZT_OK;
+}
+
+extern "C" long zt_batch_launch_count(const zt_batch* b) { return b ? b->launches : 0; }
+
+static int batch_step_impl(zt_batch* b, double tol, int maxit, zt_step_stats* stats, cudaStream_t s) {
+    int rc;
+    const int spc = b->sweeps_per_sync;
+    if (b->use_graph) {
+        if (b->g_tol_maxit_set && (b->g_tol != tol || b->g_maxit != maxit || b->g_stream != s)) drop_graphs(b);
+        if (!b->g_first) {
+            if ((rc = capture(b, s, &b->g_first, true, tol, maxit, spc))) return rc;
+            if ((rc = capture(b, s, &b->g_more, false, tol, maxit, spc))) return rc;
+            b->g_tol = tol;
+            b->g_maxit = maxit;
+            b->g_stream = s;
+            b->g_tol_maxit_set = 1;
+        }
+    }
+    int enq = 0;
+    for (int round = 0;; ++round) {
+        const int nsw = (maxit - enq < spc) ? (maxit - enq) : spc;
+        if (b->use_graph && nsw == spc) {
+            ZT_CU(cudaGraphLaunch(round == 0 ? b->g_first : b->g_more, s));
+            b->launches += round == 0 ? b->g_first_k : b->g_more_k;
+        } else if (round == 0) {
+            if ((rc = enqueue_first_round(b, tol, maxit, nsw, s))) return rc;
+        } else {
+            if ((rc = enqueue_more_round(b, nsw, s))) return rc;
+        }
+        enq += nsw;
+        ZT_CU(cudaStreamSynchronize(s));
+        bool all = true;
+        for (int i = 0; i < b->n; ++i) all = all && b->hstates[i].done;
+        if (all) break;
+        if (enq >= maxit) return zt_fail(ZT_ECUDA, "isomp_step_batched: states not done after maxit sweeps");
+    }
+    int worst = ZT_OK;
+    for (int i = 0; i < b->n; ++i) {
+        const zt_dev_state& hs = b->hstates[i];
+        if (stats) {
+            stats[i].iters = hs.iters;
+            stats[i].converged = hs.converged;
+            stats[i].residual = hs.residual;
+        }
+        if (hs.timeout) worst = ZT_ETIMEOUT;
+        else if (hs.nonfinite && worst != ZT_ETIMEOUT) worst = ZT_ENONFINITE;
+        else if (!hs.converged && worst == ZT_OK) worst = ZT_NOT_CONVERGED;
+    }
+    if (worst == ZT_ETIMEOUT) return zt_fail(worst, "isomp_step_batched: a bounded device wait ran out");
+    if (worst == ZT_ENONFINITE) return zt_fail(worst, "isomp_step_batched: a residual is not finite");
+    if (worst == ZT_NOT_CONVERGED) return zt_fail(worst, "isomp_step_batched: some instances did not converge");
+    return ZT_OK;
+}
+
+extern "C" int isomp_step_batched(zt_batch* b, double tol, int maxit, zt_step_stats* stats, void* stream) {
+    if (!b) return zt_fail(ZT_EINVAL, "batch is NULL");
+    if (!(tol >= 0.0)) return zt_fail(ZT_EINVAL, "tol must be >= 0");
+    if (maxit < 1 || maxit > 100000) return zt_fail(ZT_EINVAL, "maxit outside [1, 100000]");
+    return batch_step_impl(b, tol, maxit, stats, (cudaStream_t)stream);
+}
+
+extern "C" int isomp_run_batched(zt_batch* b, long nsteps, double tol, int maxit, zt_run_stats* stats,
+                                 void* stream) {
+    if (!b) return zt_fail(ZT_EINVAL, "batch is NULL");
+    if (nsteps < 0) return zt_fail(ZT_EINVAL, "nsteps < 0");
+    std::vector<zt_step_stats> st(b->n);
+    zt_run_stats tot{};
+    tot.all_converged = 1;
+    int worst = ZT_OK;
+    for (long k = 0; k < nsteps; ++k) {
+        int rc = isomp_step_batched(b, tol, maxit, st.data(), stream);
+        if (rc < 0) {
+            if (stats) *stats = tot;
+            return rc;
+        }
+        if (rc == ZT_NOT_CONVERGED) worst = rc;
+        tot.steps++;
+        for (int i = 0; i < b->n; ++i) {
+            tot.total_iters += st[i].iters;
+            if (st[i].iters > tot.max_iters) tot.max_iters = st[i].iters;
+            if (!st[i].converged) tot.all_converged = 0;
+            if (st[i].residual > tot.max_residual) tot.max_residual = st[i].residual;
+        }
+    }
+    if (stats) *stats = tot;
+    if (worst) return zt_fail(worst, "isomp_run_batched: some instances did not converge");
+    return ZT_OK;
+}

@@ -10,11 +10,11 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 }
 
-__global__ void __launch_bounds__(NT)
-zgemm_fp64_kernel(const double2* __restrict__ X, const double2* __restrict__ Y, double2* __restrict__ C,
-                  double alpha, int N, int lower_only, const zt_dev_state* st, int gate) {
+__device__ __forceinline__ void zgemm_fp64_body(const double2* __restrict__ X, const double2* __restrict__ Y,
+                                                double2* __restrict__ C, double alpha, int N, int lower_only,
+                                                const zt_dev_state* st, int gate, int bx, int by) {
     if (zt_gate_skip(st, gate)) return;
-    const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+    const int i0 = by * BM, j0 = bx * BN;
     if (lower_only && j0 > i0 + BM - 1) return;   // tile lies strictly above the diagonal
     __shared__ double2 Xs[BK][BM + 1];
     __shared__ double2 Ys[BK][BN + 1];
@@ -64,6 +64,43 @@ zgemm_fp64_kernel(const double2* __restrict__ X, const double2* __restrict__ Y, 
             if (j < N) C[(size_t)i * N + j] = make_double2(alpha * cr[a][b], alpha * ci[a][b]);
         }
     }
+}
+
+__global__ void __launch_bounds__(NT)
+zgemm_fp64_kernel(const double2* __restrict__ X, const double2* __restrict__ Y, double2* __restrict__ C,
+                  double alpha, int N, int lower_only, const zt_dev_state* st, int gate) {
+    zgemm_fp64_body(X, Y, C, alpha, N, lower_only, st, gate, blockIdx.x, blockIdx.y);
+}
+
+// Grouped: each instance's tile grid is flattened (gx tiles per row of tiles).
+__global__ void __launch_bounds__(NT) zgemm_fp64_grouped(const Fp64GemmArgs* tab, const int* offs, int n, int gate) {
+    const int inst = zt_group_find(offs, n, blockIdx.x);
+    const Fp64GemmArgs a = tab[inst];
+    const int b = blockIdx.x - offs[inst];
+    zgemm_fp64_body(a.X, a.Y, a.C, a.alpha, a.N, a.lower_only, a.st, gate, b % a.gx, b / a.gx);
+}
+
+int zt_fp64_gemm_args(zt_plan* p, const double2* X, const double2* Y, double2* C, double alpha, int lower_only,
+                      Fp64GemmArgs* out, int* ctas) {
+    const int N = p->N;
+    out->X = X;
+    out->Y = Y;
+    out->C = C;
+    out->alpha = alpha;
+    out->N = N;
+    out->lower_only = lower_only;
+    out->gx = (N + BN - 1) / BN;
+    out->st = p->state;
+    out->gate = ZT_GATE_NONE;
+    *ctas = out->gx * ((N + BM - 1) / BM);
+    return ZT_OK;
+}
+
+int zt_fp64_gemm_grouped(const Fp64GemmArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate) {
+    zgemm_fp64_grouped<<<total, NT, 0, s>>>(tab, offs, n, gate);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "zgemm_fp64_grouped");
+    return ZT_OK;
 }
 
 int zt_launch_zgemm_fp64(zt_plan* p, const double2* X, const double2* Y, double2* C, double alpha,

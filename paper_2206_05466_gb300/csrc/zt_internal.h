@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libzeitlin.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -17,7 +18,8 @@ struct zt_dev_state {
     int    nonfinite;   // residual was NaN/Inf
     int    timeout;     // a bounded device wait ran out (tcgen05 kernels)
     int    maxit;
-    int    pad0, pad1;
+    int    finalized;   // W_{n+1} has been written (the final kernels ran)
+    int    pad1;
     double residual;    // last Frobenius residual
     double tol;
 };
@@ -30,11 +32,25 @@ __host__ __device__ inline bool zt_gate_skip(const zt_dev_state* st, int gate) {
 #ifdef __CUDA_ARCH__
     if (gate == ZT_GATE_NONE || st == nullptr) return false;
     int d = *(volatile const int*)&st->done;
-    return gate == ZT_GATE_SWEEP ? d != 0 : d == 0;
+    if (gate == ZT_GATE_SWEEP) return d != 0;
+    return d == 0 || *(volatile const int*)&st->finalized != 0;
 #else
     (void)st; (void)gate;
     return false;
 #endif
+}
+
+// Grouped launches: one grid covers several instances; offs[0..n] are the
+// prefix sums of the CTAs each instance needs, and a CTA finds its instance
+// by binary search.
+__device__ __forceinline__ int zt_group_find(const int* offs, int n, int b) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (offs[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // Packed lower-triangular index of (r, c), c <= r.
@@ -103,6 +119,93 @@ void zt_timer_end(zt_plan* p, int idx, cudaStream_t s);
 // Fold finished records into the totals; iters >= 0 drops sweeps >= iters.
 int zt_timer_collect(zt_plan* p, int iters);
 
+// ---- per-instance kernel arguments (one table entry per instance in grouped launches)
+
+struct SolveArgs {     // stream solve (zt_solve.cu)
+    const double2* W;
+    double2* P;
+    const double* fl;
+    const double* fnd;
+    double2* seg_z;    // [N][K] end value of z0 in a segment
+    double* seg_g;     // [N][K] product G over the segment
+    double2* seg_x;    // [N][K] start value of x0 in a segment
+    double* seg_h;     // [N][K] H at the segment start
+    double2* sum_x;    // [K] m = 0 only: sum of x0 over the segment
+    double* sum_h;     // [K] m = 0 only: sum of H over the segment
+    int N, K;
+    const zt_dev_state* st;
+    int gate;
+};
+
+struct SplitRowsArgs { // digit splitting of one operand (zt_split.cu)
+    const double2* X;
+    int N, s, beta, ldk;
+    void* dA;          // __nv_bfloat16 planes [s][Mpad][ldk] or NULL
+    int Mpad;
+    int* eA;
+    void* dB;          // __nv_bfloat16 planes [s][Npad][ldk] or NULL
+    int Npad;
+    int* eB;
+    int* occA;         // [ngA][nkb] or NULL
+    int occA_rows, occA_n;
+    int* occB;         // [ngB][nkb] or NULL
+    int occB_rows, occB_n;
+    const zt_dev_state* st;
+    int gate;
+};
+
+struct SplitArgs {     // tcgen05 split product (zt_split.cu)
+    int N, s, beta, ldk, Mpad, Npad, u, exact_groups, ntn, lower_only;
+    // digit occupancy per (row group, K block): s - (first nonzero digit), 0 = all zero;
+    // NULL disables zero-unit skipping
+    const int* occA;
+    const int* occB;
+    unsigned long long* units;   // if not NULL: += MMA units (128 x 256 x 64) issued by each CTA
+    int cm, cn;        // cluster shape: cm row tiles share B'^T slices, cn column tiles share X' slices
+    int ntmg, ntng;    // tile groups (one cluster each) along rows and columns
+    double alpha;
+    const int* eA;
+    const int* eB;
+    double* C;
+    zt_dev_state* st;
+    int gate;
+};
+
+struct alignas(64) GemmEntry {   // grouped split product: tensor maps live in global memory
+    CUtensorMap tmA;
+    CUtensorMap tmB;
+    SplitArgs a;
+};
+
+struct Fp64GemmArgs {  // FP64 product (zt_fp64.cu)
+    const double2* X;
+    const double2* Y;
+    double2* C;
+    double alpha;
+    int N, lower_only, gx;   // gx: tiles along columns
+    const zt_dev_state* st;
+    int gate;
+};
+
+struct UpdateArgs {    // fixed-point update / W_{n+1} assembly (zt_plan.cu)
+    const double2* base;
+    const double2* A;
+    const double2* B;
+    const double2* old;
+    double2* out;
+    double h2, c2;
+    double* partials;
+    int N, final_write;
+    zt_dev_state* st;
+    int gate;
+};
+
+struct ConvArgs {      // residual reduction and stop decision (zt_plan.cu)
+    const double* partials;
+    int n;
+    zt_dev_state* st;
+};
+
 // ---- error handling ---------------------------------------------------------
 int zt_fail(int code, const char* fmt, ...);
 int zt_cuda_check(cudaError_t e, const char* what);
@@ -121,6 +224,23 @@ void zt_solve_destroy(zt_plan* p);
 // touch the lower triangle (i >= j) are computed.
 int zt_launch_zgemm_fp64(zt_plan* p, const double2* X, const double2* Y, double2* C,
                          double alpha, int lower_only, cudaStream_t s, int gate);
+// Grouped launches over n instances: tab[i] holds instance i's arguments,
+// offs[0..n] (device) the prefix sums of CTAs, `total` = offs[n].
+int zt_solve_args(zt_plan* p, const double2* W, double2* P, SolveArgs* out);
+int zt_solve_ctas(int N);
+int zt_solve_grouped(const SolveArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
+int zt_split_rows_args(zt_plan* p, const double2* X, int to_a, int b_slot, SplitRowsArgs* out);
+int zt_split_rows_grouped(const SplitRowsArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
+int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, GemmEntry* out,
+                        int* ctas, int* cluster);
+int zt_split_gemm_grouped(const GemmEntry* tab, const int* offs, int n, int total, int cluster, cudaStream_t s,
+                          int gate);
+int zt_fp64_gemm_args(zt_plan* p, const double2* X, const double2* Y, double2* C, double alpha, int lower_only,
+                      Fp64GemmArgs* out, int* ctas);
+int zt_fp64_gemm_grouped(const Fp64GemmArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
+int zt_update_ctas(int N);
+int zt_update_grouped(const UpdateArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
+int zt_converge_grouped(const ConvArgs* tab, int n, cudaStream_t s);
 // Split-precision version (tcgen05).  Same contract.
 int zt_split_create(zt_plan* p);
 void zt_split_destroy(zt_plan* p);

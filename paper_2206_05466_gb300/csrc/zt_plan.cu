@@ -205,16 +205,19 @@ namespace {
 constexpr int UT = 32;
 }
 
-__global__ void __launch_bounds__(256)
-update_kernel(const double2* __restrict__ base, const double2* __restrict__ A,
-              const double2* __restrict__ B, const double2* old, double2* out,
-              double h2, double c2, double* partials, int N,
-              const zt_dev_state* st, int gate) {
-    if (zt_gate_skip(st, gate)) return;
+__device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
+    if (zt_gate_skip(ua.st, ua.gate)) return;
+    const double2* __restrict__ base = ua.base;
+    const double2* __restrict__ A = ua.A;
+    const double2* __restrict__ B = ua.B;
+    const double2* old = ua.old;
+    double2* out = ua.out;
+    const double h2 = ua.h2, c2 = ua.c2;
+    double* partials = ua.partials;
+    const int N = ua.N;
     __shared__ double2 sAT[UT][UT + 1];
     __shared__ double2 sOut[UT][UT + 1];
     __shared__ double sred[256];
-    const int t = blockIdx.x;
     int bi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
     while (bi * (bi + 1) / 2 > t) --bi;
     while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
@@ -263,10 +266,32 @@ update_kernel(const double2* __restrict__ base, const double2* __restrict__ A,
         }
         if (threadIdx.x == 0) partials[t] = sred[0];
     }
+    if (ua.final_write && t == 0 && threadIdx.x == 0) ua.st->finalized = 1;
+}
+
+__global__ void __launch_bounds__(256) update_kernel(const UpdateArgs a) { update_body(a, blockIdx.x); }
+
+__global__ void __launch_bounds__(256) update_grouped(const UpdateArgs* tab, const int* offs, int n, int gate) {
+    const int inst = zt_group_find(offs, n, blockIdx.x);
+    UpdateArgs a = tab[inst];
+    a.gate = gate;
+    update_body(a, blockIdx.x - offs[inst]);
+}
+
+int zt_update_ctas(int N) {
+    const int nt = (N + UT - 1) / UT;
+    return nt * (nt + 1) / 2;
+}
+
+int zt_update_grouped(const UpdateArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate) {
+    update_grouped<<<total, 256, 0, s>>>(tab, offs, n, gate);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "update_grouped");
+    return ZT_OK;
 }
 
 // Fixed-order reduction of the residual partials and the stop decision.
-__global__ void converge_kernel(const double* __restrict__ partials, int n, zt_dev_state* st) {
+__device__ __forceinline__ void converge_body(const double* __restrict__ partials, int n, zt_dev_state* st) {
     if (st->done) return;
     __shared__ double sh[256];
     double s = 0.0;
@@ -293,6 +318,22 @@ __global__ void converge_kernel(const double* __restrict__ partials, int n, zt_d
     }
 }
 
+__global__ void converge_kernel(const double* __restrict__ partials, int n, zt_dev_state* st) {
+    converge_body(partials, n, st);
+}
+
+__global__ void converge_grouped(const ConvArgs* tab) {
+    const ConvArgs a = tab[blockIdx.x];
+    converge_body(a.partials, a.n, a.st);
+}
+
+int zt_converge_grouped(const ConvArgs* tab, int n, cudaStream_t s) {
+    converge_grouped<<<n, 256, 0, s>>>(tab);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "converge_grouped");
+    return ZT_OK;
+}
+
 __global__ void state_init_kernel(zt_dev_state* st, double tol, int maxit) {
     st->done = 0;
     st->iters = 0;
@@ -302,6 +343,7 @@ __global__ void state_init_kernel(zt_dev_state* st, double tol, int maxit) {
     st->maxit = maxit;
     st->residual = 0.0;
     st->tol = tol;
+    st->finalized = 0;
 }
 
 static int launch_update(zt_plan* p, const double2* base, const double2* old, double2* out,
@@ -312,9 +354,21 @@ static int launch_update(zt_plan* p, const double2* base, const double2* old, do
     // lower triangle: base, A, A^T, B (+ old) read, out written twice
     const double tri = 16.0 * N * (N + 1.0) / 2.0;
     const double bytes = tri * ((resid ? 5.0 : 4.0) + 2.0);
+    UpdateArgs ua;
+    ua.base = base;
+    ua.A = p->A;
+    ua.B = p->B;
+    ua.old = old;
+    ua.out = out;
+    ua.h2 = h / 2.0;
+    ua.c2 = sign_b * h * h / 4.0;
+    ua.partials = resid ? p->partials : nullptr;
+    ua.N = N;
+    ua.final_write = resid ? 0 : 1;
+    ua.st = p->state;
+    ua.gate = gate;
     const int t = zt_timer_begin(p, ZT_KERNEL_UPDATE, bytes, bytes, s);
-    update_kernel<<<ntiles, 256, 0, s>>>(base, p->A, p->B, old, out, h / 2.0, sign_b * h * h / 4.0,
-                                         resid ? p->partials : nullptr, N, p->state, gate);
+    update_kernel<<<ntiles, 256, 0, s>>>(ua);
     zt_timer_end(p, t, s);
     return launch_check(p, "update_kernel");
 }

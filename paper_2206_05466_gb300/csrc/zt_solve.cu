@@ -32,21 +32,6 @@ constexpr size_t TILE_SMEM = (size_t)SROWS * SD * (sizeof(double2) + 2 * sizeof(
 
 enum Phase { F1 = 0, B1 = 1, B3 = 2 };
 
-struct SolveArgs {
-    const double2* W;
-    double2* P;
-    const double* fl;
-    const double* fnd;
-    double2* seg_z;   // [N][K] end value of z0 in a segment
-    double* seg_g;    // [N][K] product G over the segment
-    double2* seg_x;   // [N][K] start value of x0 in a segment
-    double* seg_h;    // [N][K] H at the segment start
-    double2* sum_x;   // [K] m = 0 only: sum of x0 over the segment
-    double* sum_h;    // [K] m = 0 only: sum of H over the segment
-    int N, K;
-    const zt_dev_state* st;
-    int gate;
-};
 
 __device__ __forceinline__ void cp16(void* smem, const void* g, bool ok) {
     unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -84,7 +69,7 @@ __device__ double sum_block(double v, double* sh) {
 }  // namespace
 
 template <int PH>
-__global__ void __launch_bounds__(STH) solve_tile_kernel(const SolveArgs a) {
+__device__ __forceinline__ void solve_tile_body(const SolveArgs& a, int bid) {
     if (zt_gate_skip(a.st, a.gate)) return;
     extern __shared__ __align__(16) unsigned char smem[];
     double2* tv = reinterpret_cast<double2*>(smem);     // [SROWS][SD] values
@@ -93,7 +78,7 @@ __global__ void __launch_bounds__(STH) solve_tile_kernel(const SolveArgs a) {
     __shared__ double red[STH];
     const int N = a.N, K = a.K;
     int band, k;
-    tile_of(blockIdx.x, N, &band, &k);
+    tile_of(bid, N, &band, &k);
     const int m0 = band * SD, r0 = k * SL + m0;
     const int tid = threadIdx.x;
 
@@ -226,6 +211,20 @@ __global__ void __launch_bounds__(STH) solve_tile_kernel(const SolveArgs a) {
     }
 }
 
+template <int PH>
+__global__ void __launch_bounds__(STH) solve_tile_kernel(const SolveArgs a) {
+    solve_tile_body<PH>(a, blockIdx.x);
+}
+
+// Grouped: one grid over several instances (tile counts prefix-summed in offs).
+template <int PH>
+__global__ void __launch_bounds__(STH) solve_tile_grouped(const SolveArgs* tab, const int* offs, int n, int gate) {
+    const int inst = zt_group_find(offs, n, blockIdx.x);
+    SolveArgs a = tab[inst];
+    a.gate = gate;
+    solve_tile_body<PH>(a, blockIdx.x - offs[inst]);
+}
+
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
@@ -248,6 +247,9 @@ int zt_solve_create(zt_plan* p) {
     ZT_CU(cudaFuncSetAttribute(solve_tile_kernel<F1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
     ZT_CU(cudaFuncSetAttribute(solve_tile_kernel<B1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
     ZT_CU(cudaFuncSetAttribute(solve_tile_kernel<B3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
+    ZT_CU(cudaFuncSetAttribute(solve_tile_grouped<F1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
+    ZT_CU(cudaFuncSetAttribute(solve_tile_grouped<B1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
+    ZT_CU(cudaFuncSetAttribute(solve_tile_grouped<B3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
     return ZT_OK;
 }
 
@@ -258,6 +260,36 @@ void zt_solve_destroy(zt_plan* p) {
     cudaFree(p->seg_h);
     cudaFree(p->sum_x);
     cudaFree(p->sum_h);
+}
+
+int zt_solve_ctas(int N) { return solve_tiles(N); }
+
+int zt_solve_args(zt_plan* p, const double2* W, double2* P, SolveArgs* out) {
+    SolveArgs& a = *out;
+    a.W = W;
+    a.P = P;
+    a.fl = p->fac_l;
+    a.fnd = p->fac_nd;
+    a.seg_z = p->seg_z;
+    a.seg_g = p->seg_g;
+    a.seg_x = p->seg_x;
+    a.seg_h = p->seg_h;
+    a.sum_x = p->sum_x;
+    a.sum_h = p->sum_h;
+    a.N = p->N;
+    a.K = p->nseg;
+    a.st = p->state;
+    a.gate = ZT_GATE_NONE;
+    return ZT_OK;
+}
+
+int zt_solve_grouped(const SolveArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate) {
+    solve_tile_grouped<F1><<<total, STH, TILE_SMEM, s>>>(tab, offs, n, gate);
+    solve_tile_grouped<B1><<<total, STH, TILE_SMEM, s>>>(tab, offs, n, gate);
+    solve_tile_grouped<B3><<<total, STH, TILE_SMEM, s>>>(tab, offs, n, gate);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "solve_tile_grouped");
+    return ZT_OK;
 }
 
 int zt_launch_stream_solve(zt_plan* p, const double2* W, double2* P, cudaStream_t s, int gate) {

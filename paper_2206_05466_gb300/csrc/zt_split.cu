@@ -80,22 +80,6 @@ struct zt_split_ws {
     CUtensorMap tmA, tmB[2];
 };
 
-struct SplitArgs {
-    int N, s, beta, ldk, Mpad, Npad, u, exact_groups, ntn, lower_only;
-    // digit occupancy per (row group, K block): s - (first nonzero digit), 0 = all zero;
-    // NULL disables zero-unit skipping
-    const int* occA;
-    const int* occB;
-    unsigned long long* units;   // if not NULL: += MMA units (128 x 256 x 64) issued by each CTA
-    int cm, cn;        // cluster shape: cm row tiles share B'^T slices, cn column tiles share X' slices
-    int ntmg, ntng;    // tile groups (one cluster each) along rows and columns
-    double alpha;
-    const int* eA;
-    const int* eB;
-    double* C;
-    zt_dev_state* st;
-    int gate;
-};
 
 // ---------------------------------------------------------------------------
 // device helpers (inline PTX)
@@ -247,14 +231,17 @@ __device__ __forceinline__ long long to_fixed(double x, int e, int sb) {
     return bits < 0 ? -v : v;
 }
 
-__global__ void __launch_bounds__(256)
-split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk,
-                  __nv_bfloat16* __restrict__ dA, int Mpad, int* __restrict__ eA,
-                  __nv_bfloat16* __restrict__ dB, int Npad, int* __restrict__ eB,
-                  int* __restrict__ occA, int occA_rows, int* __restrict__ occB, int occB_rows,
-                  const zt_dev_state* st, int gate) {
-    if (zt_gate_skip(st, gate)) return;
-    const int j = blockIdx.x;
+__device__ __forceinline__ void split_rows_body(const SplitRowsArgs& ra, int j) {
+    if (zt_gate_skip(ra.st, ra.gate)) return;
+    const double2* __restrict__ X = ra.X;
+    const int N = ra.N, s = ra.s, beta = ra.beta, ldk = ra.ldk, Mpad = ra.Mpad, Npad = ra.Npad;
+    __nv_bfloat16* __restrict__ dA = static_cast<__nv_bfloat16*>(ra.dA);
+    __nv_bfloat16* __restrict__ dB = static_cast<__nv_bfloat16*>(ra.dB);
+    int* __restrict__ eA = ra.eA;
+    int* __restrict__ eB = ra.eB;
+    int* __restrict__ occA = ra.occA;
+    int* __restrict__ occB = ra.occB;
+    const int occA_rows = ra.occA_rows, occB_rows = ra.occB_rows;
     const double2* row = X + (size_t)j * N;
     __shared__ int smax[256];
     int mx = 0;
@@ -347,6 +334,26 @@ split_rows_kernel(const double2* __restrict__ X, int N, int s, int beta, int ldk
     }
 }
 
+__global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsArgs a) { split_rows_body(a, blockIdx.x); }
+
+// Grouped: the occupancy arrays of every instance are cleared first (one CTA
+// per instance), then one CTA per row of every instance splits.
+__global__ void __launch_bounds__(256) occ_clear_grouped(const SplitRowsArgs* tab, int gate) {
+    const SplitRowsArgs a = tab[blockIdx.x];
+    if (zt_gate_skip(a.st, gate)) return;
+    if (a.occA)
+        for (int i = threadIdx.x; i < a.occA_n; i += 256) a.occA[i] = 0;
+    if (a.occB)
+        for (int i = threadIdx.x; i < a.occB_n; i += 256) a.occB[i] = 0;
+}
+
+__global__ void __launch_bounds__(256) split_rows_grouped(const SplitRowsArgs* tab, const int* offs, int n, int gate) {
+    const int inst = zt_group_find(offs, n, blockIdx.x);
+    SplitRowsArgs a = tab[inst];
+    a.gate = gate;
+    split_rows_body(a, blockIdx.x - offs[inst]);
+}
+
 // A segment (digit group g, K blocks [kb0, kend)) has a nonzero unit iff some
 // K block has fa + fb <= g.
 __device__ __forceinline__ bool seg_has_units(const uint8_t* fa, const uint8_t* fb, int g, int kb0, int kend) {
@@ -358,9 +365,8 @@ __device__ __forceinline__ bool seg_has_units(const uint8_t* fa, const uint8_t* 
 // ---------------------------------------------------------------------------
 // The tcgen05 product kernel.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NTHREADS, 1)
-zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const SplitArgs a) {
+__device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const CUtensorMap* tmB_p,
+                                                 const SplitArgs& a, int bid, bool global_maps) {
     if (zt_gate_skip(a.st, a.gate)) return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -380,7 +386,7 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     // tiles and cn column tiles; CTA rank r sits at (r % cm, r / cm).
     const int cs = a.cm * a.cn;
     const int rank = cs > 1 ? (int)cluster_ctarank() : 0;
-    const int grp = blockIdx.x / cs;
+    const int grp = bid / cs;
     int tig, tjg;
     if (a.lower_only && a.cm == a.cn) {   // groups on or below the diagonal, triangular order
         int r = (int)((sqrtf(8.0f * grp + 1.0f) - 1.0f) * 0.5f);
@@ -443,6 +449,10 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
     if (warp == 0) {
         if (lane == 0) {   // ---- TMA producer ----
+            if (global_maps) {   // maps written by the host: visible to the tensormap proxy before use
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmA_p) : "memory");
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmB_p) : "memory");
+            }
             int stage = 0;
             uint32_t ph = 0;
             bool ok = true;
@@ -461,13 +471,13 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
                             uint8_t* dB = sB + stage * B_TILE + b_off * 128;
                             const int ya = p * a.Mpad + i0 + a_off, yb = (g - p) * a.Npad + c0 + b_off;
                             if (a.cn > 1)
-                                tma_load_2d_mc(dA, &tmA, &full[stage], kb * BK, ya, mask_a);
+                                tma_load_2d_mc(dA, tmA_p, &full[stage], kb * BK, ya, mask_a);
                             else
-                                tma_load_2d(dA, &tmA, &full[stage], kb * BK, ya);
+                                tma_load_2d(dA, tmA_p, &full[stage], kb * BK, ya);
                             if (a.cm > 1)
-                                tma_load_2d_mc(dB, &tmB, &full[stage], kb * BK, yb, mask_b);
+                                tma_load_2d_mc(dB, tmB_p, &full[stage], kb * BK, yb, mask_b);
                             else
-                                tma_load_2d(dB, &tmB, &full[stage], kb * BK, yb);
+                                tma_load_2d(dB, tmB_p, &full[stage], kb * BK, yb);
                             if (++stage == STAGES) {
                                 stage = 0;
                                 ph ^= 1;
@@ -621,6 +631,23 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     if (cs > 1) cluster_sync();
 }
 
+__global__ void __launch_bounds__(NTHREADS, 1)
+zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const SplitArgs a) {
+    zgemm_split_body(&tmA, &tmB, a, blockIdx.x, false);
+}
+
+// Grouped: instances (each with its own tensor maps in global memory) share one
+// cluster launch; every instance's CTA count is a multiple of the cluster size.
+__global__ void __launch_bounds__(NTHREADS, 1)
+zgemm_split_grouped(const GemmEntry* tab, const int* offs, int n, int gate) {
+    const int inst = zt_group_find(offs, n, blockIdx.x);
+    const GemmEntry* e = tab + inst;
+    SplitArgs a = e->a;
+    a.gate = gate;
+    zgemm_split_body(&e->tmA, &e->tmB, a, blockIdx.x - offs[inst], true);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -710,6 +737,7 @@ int zt_split_create(zt_plan* p) {
         if ((rc = make_map(&w->tmB[b], w->dB[b], s * w->Npad, w->ldk, BN / cm))) return rc;
     }
     ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    ZT_CU(cudaFuncSetAttribute(zgemm_split_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     return ZT_OK;
 }
 
@@ -728,21 +756,55 @@ void zt_split_destroy(zt_plan* p) {
     p->split = nullptr;
 }
 
+int zt_split_rows_args(zt_plan* p, const double2* X, int to_a, int b_slot, SplitRowsArgs* out) {
+    zt_split_ws* w = p->split;
+    if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
+    SplitRowsArgs& a = *out;
+    a.X = X;
+    a.N = p->N;
+    a.s = w->s;
+    a.beta = w->beta;
+    a.ldk = w->ldk;
+    a.dA = to_a ? w->dA : nullptr;
+    a.Mpad = w->Mpad;
+    a.eA = to_a ? w->eA : nullptr;
+    a.dB = b_slot >= 0 ? w->dB[b_slot] : nullptr;
+    a.Npad = w->Npad;
+    a.eB = b_slot >= 0 ? w->eB[b_slot] : nullptr;
+    a.occA = to_a ? w->occA : nullptr;
+    a.occA_rows = BM * w->cm;
+    a.occA_n = w->ngA * w->nkb;
+    a.occB = b_slot >= 0 ? w->occB[b_slot] : nullptr;
+    a.occB_rows = (BN / 2) * w->cn;
+    a.occB_n = w->ngB * w->nkb;
+    a.st = p->state;
+    a.gate = ZT_GATE_NONE;
+    return ZT_OK;
+}
+
+int zt_split_rows_grouped(const SplitRowsArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate) {
+    occ_clear_grouped<<<n, 256, 0, s>>>(tab, gate);
+    split_rows_grouped<<<total, 256, 0, s>>>(tab, offs, n, gate);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "split_rows_grouped");
+    return ZT_OK;
+}
+
 int zt_split_operand(zt_plan* p, const double2* X, int to_a, int b_slot, cudaStream_t s, int gate) {
     zt_split_ws* w = p->split;
     if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
     const int N = p->N;
+    SplitRowsArgs ra;
+    int rc = zt_split_rows_args(p, X, to_a, b_slot, &ra);
+    if (rc) return rc;
+    ra.gate = gate;
     const double bytes = 16.0 * N * N + (to_a ? 2.0 * w->s * (double)N * w->ldk : 0.0) +
                          (b_slot >= 0 ? 4.0 * w->s * (double)N * w->ldk : 0.0);
     // occupancy is reduced with atomicMax over the rows of each group: start from 0
     if (to_a) ZT_CU(cudaMemsetAsync(w->occA, 0, (size_t)w->ngA * w->nkb * sizeof(int), s));
     if (b_slot >= 0) ZT_CU(cudaMemsetAsync(w->occB[b_slot], 0, (size_t)w->ngB * w->nkb * sizeof(int), s));
     const int t = zt_timer_begin(p, ZT_KERNEL_SPLIT, bytes, bytes, s);
-    split_rows_kernel<<<N, 256, 0, s>>>(X, N, w->s, w->beta, w->ldk, to_a ? w->dA : nullptr, w->Mpad,
-                                        to_a ? w->eA : nullptr, b_slot >= 0 ? w->dB[b_slot] : nullptr, w->Npad,
-                                        b_slot >= 0 ? w->eB[b_slot] : nullptr, to_a ? w->occA : nullptr,
-                                        BM * w->cm, b_slot >= 0 ? w->occB[b_slot] : nullptr, (BN / 2) * w->cn,
-                                        p->state, gate);
+    split_rows_kernel<<<N, 256, 0, s>>>(ra);
     zt_timer_end(p, t, s);
     p->launches++;
     cudaError_t e = cudaGetLastError();
@@ -750,11 +812,10 @@ int zt_split_operand(zt_plan* p, const double2* X, int to_a, int b_slot, cudaStr
     return ZT_OK;
 }
 
-int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, cudaStream_t s, int gate) {
+static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, SplitArgs& a,
+                         int* ngroups_out, int* ntiles_out) {
     zt_split_ws* w = p->split;
-    if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
     const int N = p->N;
-    SplitArgs a;
     a.N = N;
     a.s = w->s;
     a.beta = w->beta;
@@ -771,13 +832,13 @@ int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower
     a.ntng = w->Npad / (BN * w->cn);
     a.occA = w->skip_zero ? w->occA : nullptr;
     a.occB = w->skip_zero ? w->occB[b_slot] : nullptr;
-    a.units = p->timing ? p->d_units : nullptr;
+    a.units = nullptr;
     a.alpha = alpha;
     a.eA = w->eA;
     a.eB = w->eB[b_slot];
     a.C = reinterpret_cast<double*>(C);
     a.st = p->state;
-    a.gate = gate;
+    a.gate = ZT_GATE_NONE;
     const int cs = w->cm * w->cn;
     int ngroups, ntiles;
     if (lower_only && w->cm == w->cn) {
@@ -790,6 +851,58 @@ int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower
             for (int ug = 0; ug < a.ntng; ++ug)
                 if (!lower_only || ug * w->cn < (tg + 1) * w->cm) ntiles += cs;
     }
+    *ngroups_out = ngroups;
+    *ntiles_out = ntiles;
+}
+
+int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, GemmEntry* out,
+                        int* ctas, int* cluster) {
+    zt_split_ws* w = p->split;
+    if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
+    int ngroups, ntiles;
+    product_args(p, b_slot, C, alpha, lower_only, out->a, &ngroups, &ntiles);
+    out->tmA = w->tmA;
+    out->tmB = w->tmB[b_slot];
+    *cluster = w->cm * w->cn;
+    *ctas = ngroups * *cluster;
+    return ZT_OK;
+}
+
+int zt_split_gemm_grouped(const GemmEntry* tab, const int* offs, int n, int total, int cluster, cudaStream_t s,
+                          int gate) {
+    cudaError_t e;
+    if (cluster > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(total);
+        cfg.blockDim = dim3(NTHREADS);
+        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, zgemm_split_grouped, tab, offs, n, gate);
+    } else {
+        zgemm_split_grouped<<<total, NTHREADS, SMEM_BYTES, s>>>(tab, offs, n, gate);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return zt_cuda_check(e, "zgemm_split_grouped");
+    return ZT_OK;
+}
+
+int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, cudaStream_t s, int gate) {
+    zt_split_ws* w = p->split;
+    if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
+    const int N = p->N;
+    SplitArgs a;
+    int ngroups, ntiles;
+    product_args(p, b_slot, C, alpha, lower_only, a, &ngroups, &ntiles);
+    a.gate = gate;
+    a.units = p->timing ? p->d_units : nullptr;
+    const int cs = w->cm * w->cn;
     (void)ntiles;   // issued work is counted on the device (skipped units vary with the data)
     const double alg = lower_only ? 4.0 * N * (double)N * (N + 1.0) : 8.0 * (double)N * N * N;
     const int t = zt_timer_begin(p, ZT_KERNEL_PRODUCT, 0.0, alg, s);
@@ -919,10 +1032,26 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
         bound *= (double)NA_LDK * std::ldexp(1.0, 2 * NA_BETA - 2);
         while (bound >= std::ldexp(1.0, 62 + u)) ++u;
     }
-    split_rows_kernel<<<N, 256, 0, s>>>((const double2*)X, N, NA_S, NA_BETA, NA_LDK, dA, NA_MPAD, eA, nullptr,
-                                        NA_NPAD, nullptr, nullptr, 1, nullptr, 1, st, ZT_GATE_NONE);
-    split_rows_kernel<<<N, 256, 0, s>>>((const double2*)Y, N, NA_S, NA_BETA, NA_LDK, nullptr, NA_MPAD, nullptr, dB,
-                                        NA_NPAD, eB, nullptr, 1, nullptr, 1, st, ZT_GATE_NONE);
+    SplitRowsArgs ra = {};
+    ra.X = (const double2*)X;
+    ra.N = N;
+    ra.s = NA_S;
+    ra.beta = NA_BETA;
+    ra.ldk = NA_LDK;
+    ra.dA = dA;
+    ra.Mpad = NA_MPAD;
+    ra.eA = eA;
+    ra.Npad = NA_NPAD;
+    ra.occA_rows = ra.occB_rows = 1;   // no occupancy tracking (every digit pair is multiplied)
+    ra.st = st;
+    ra.gate = ZT_GATE_NONE;
+    split_rows_kernel<<<N, 256, 0, s>>>(ra);
+    ra.X = (const double2*)Y;
+    ra.dA = nullptr;
+    ra.eA = nullptr;
+    ra.dB = dB;
+    ra.eB = eB;
+    split_rows_kernel<<<N, 256, 0, s>>>(ra);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "split_rows_kernel");
     SplitArgs a;

@@ -101,6 +101,19 @@ def load(build_if_missing: bool = True):
     dp, lp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)
     L.zt_plan_kernel_time.argtypes = [vp, i, lp, dp, dp, dp]
     L.zt_plan_kernel_time.restype = i
+    P = ctypes.POINTER
+    L.zt_batch_create.argtypes = [i, P(vp), P(vp), P(d), P(vp)]
+    L.zt_batch_create.restype = i
+    L.zt_batch_destroy.argtypes = [vp]
+    L.zt_batch_destroy.restype = None
+    L.zt_batch_set_graph.argtypes = [vp, i]
+    L.zt_batch_set_graph.restype = i
+    L.isomp_step_batched.argtypes = [vp, d, i, P(StepStats), vp]
+    L.isomp_step_batched.restype = i
+    L.isomp_run_batched.argtypes = [vp, l, d, i, P(RunStats), vp]
+    L.isomp_run_batched.restype = i
+    L.zt_batch_launch_count.argtypes = [vp]
+    L.zt_batch_launch_count.restype = l
     _lib = L
     return L
 
@@ -204,3 +217,57 @@ def zt_zgemm_skew(plan: Plan, X, Y, C, stream=None):
     _check(load().zt_zgemm_skew(plan.handle, _ptr(X, plan.N), _ptr(Y, plan.N), _ptr(C, plan.N),
                                 _stream(stream)))
     return C
+
+
+class Batch:
+    """A zt_batch: grouped IsoMP steps over several plans (any mix of N and precision).
+
+    The state tensors are bound for the batch's lifetime; each step advances
+    every instance exactly as isomp_step would.
+    """
+
+    def __init__(self, plans, Ws, hs):
+        L = load()
+        if not (len(plans) == len(Ws) == len(hs)) or not plans:
+            raise ValueError("plans, Ws and hs must be non-empty and of equal length")
+        n = len(plans)
+        self.n = n
+        self._plans = list(plans)
+        self._Ws = list(Ws)
+        parr = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+        warr = (ctypes.c_void_p * n)(*[_ptr(W, p.N).value for W, p in zip(Ws, plans)])
+        harr = (ctypes.c_double * n)(*[float(h) for h in hs])
+        h = ctypes.c_void_p()
+        _check(L.zt_batch_create(n, parr, warr, harr, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().zt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_graph(self, enable: bool = True):
+        _check(load().zt_batch_set_graph(self._h, 1 if enable else 0))
+
+    def launch_count(self) -> int:
+        return load().zt_batch_launch_count(self._h)
+
+    def step(self, tol: float = 1e-12, maxit: int = 50, stream=None, allow_not_converged: bool = False):
+        st = (StepStats * self.n)()
+        allow = (ZT_OK, ZT_NOT_CONVERGED) if allow_not_converged else (ZT_OK,)
+        rc = _check(load().isomp_step_batched(self._h, float(tol), int(maxit), st, _stream(stream)), allow)
+        return rc, [{"iters": x.iters, "converged": bool(x.converged), "residual": x.residual} for x in st]
+
+    def run(self, nsteps: int, tol: float = 1e-12, maxit: int = 50, stream=None, allow_not_converged: bool = False):
+        st = RunStats()
+        allow = (ZT_OK, ZT_NOT_CONVERGED) if allow_not_converged else (ZT_OK,)
+        rc = _check(load().isomp_run_batched(self._h, int(nsteps), float(tol), int(maxit), ctypes.byref(st),
+                                             _stream(stream)), allow)
+        return {"status": rc, "steps": st.steps, "total_iters": st.total_iters, "max_iters": st.max_iters,
+                "all_converged": bool(st.all_converged), "max_residual": st.max_residual}
