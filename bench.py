@@ -239,6 +239,79 @@ def run_casimir(args):
     return 0
 
 
+def _ensemble(args, tun, steps, graph=True):
+    """Ensemble of independent instances advanced by grouped (batched) steps."""
+    import numpy as np
+    import torch
+
+    from paper_2206_05466_gb300 import zeitlin as z
+    from paper_2206_05466_gb300.inputs import ensemble_sizes, vorticity_w0
+
+    sizes = ensemble_sizes(args.ens_count, seed=0)
+    cache = {}
+    plans, Ws = [], []
+    for k, N in enumerate(sizes):
+        key = (N, k % 8)   # W0 recipe, 8 seeds per size (generation is host-side and slow at large N)
+        if key not in cache:
+            cache[key] = vorticity_w0(N, seed=key[1])
+        plans.append(z.Plan(N, z.PRECISION_SPLIT, **tun))
+        Ws.append(torch.from_numpy(cache[key]).cuda())
+    b = z.Batch(plans, Ws, [0.01] * len(plans))
+    b.set_graph(graph)
+    for _ in range(2):
+        b.step()
+    torch.cuda.synchronize()
+    l0 = b.launch_count()
+    t0 = time.perf_counter()
+    r = b.run(steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    launches = b.launch_count() - l0
+    # the same instances stepped one plan at a time (a few steps) for comparison
+    seq_steps = 2
+    t1 = time.perf_counter()
+    for _ in range(seq_steps):
+        for p, W in zip(plans, Ws):
+            z.isomp_step(p, W, 0.01)
+    torch.cuda.synchronize()
+    dts = time.perf_counter() - t1
+    b.close()
+    for p in plans:
+        p.close()
+    n = len(plans)
+    return {"instances": n, "sizes": {str(N): sizes.count(N) for N in sorted(set(sizes))}, "h": 0.01,
+            "steps": steps, "graph": graph, "value": n * steps / dt, "unit": "instance-steps/s",
+            "batched_steps_per_s": steps / dt, "ms_per_batched_step": 1e3 * dt / steps,
+            "launches_per_batched_step": launches / steps, "all_converged": r["all_converged"],
+            "max_sweeps": r["max_iters"],
+            "one_plan_at_a_time": {"value": n * seq_steps / dts, "unit": "instance-steps/s"}}
+
+
+def _serving(args, duration):
+    """Poisson job stream, admission by device footprint, continuous batching."""
+    import numpy as np
+
+    from paper_2206_05466_gb300 import serving
+    from paper_2206_05466_gb300 import zeitlin as z
+    from paper_2206_05466_gb300.inputs import serving_jobs, vorticity_w0
+
+    stream = serving_jobs(duration, rate_per_s=50.0, seed=0)
+    cache = {}
+    jobs = []
+    for (t, N, nsteps, jid) in stream:
+        key = (N, jid % 4)
+        if key not in cache:
+            cache[key] = vorticity_w0(N, seed=key[1])
+        prec = z.PRECISION_SPLIT if jid % 2 == 0 else z.PRECISION_FP64
+        jobs.append(serving.Job(jid=jid, N=N, nsteps=nsteps, h=0.01, precision=prec, arrival=t, W0=cache[key]))
+    rep = serving.Server(int(args.serve_budget_gb * 1e9)).run(jobs, time_limit=duration)
+    rep.pop("results", None)
+    rep.update({"arrivals": len(jobs), "rate_per_s": 50.0, "duration_s": duration,
+                "budget_gb": args.serve_budget_gb, "precision_mix": "even job ids split, odd FP64",
+                "sizes": "N in {256,512,1024,2048} w.p. .4/.3/.2/.1, 200-2000 steps"})
+    return rep
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -352,6 +425,11 @@ def run_gpu(args):
                 pl.close()
         accuracy = acc
 
+    ens = serve = None
+    if rank == 0 and args.ens_steps > 0:
+        ens = _ensemble(args, tun, args.ens_steps)
+    if rank == 0 and args.serve_seconds > 0:
+        serve = _serving(args, args.serve_seconds)
     if rank != 0:
         return 0
     pairs = tun["slices"] * (tun["slices"] + 1) / 2
@@ -391,6 +469,8 @@ def run_gpu(args):
                       "peak_gbs": peaks["hbm_gbs"]},
         "cpu_baseline": cpu_baseline,
         "accuracy": accuracy,
+        "ensemble": ens,
+        "serving": serve,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -404,7 +484,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--mode", default="bench", choices=["bench", "casimir"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "casimir", "ensemble", "serving"])
+    ap.add_argument("--ens-count", type=int, default=256)
+    ap.add_argument("--ens-steps", type=int, default=20)
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--tuning", default="auto", choices=["auto", "fixed"])
     ap.add_argument("--tune-target", type=float, default=1e-11)
     ap.add_argument("--slices", type=int, default=7)
@@ -421,6 +505,18 @@ def main():
         return run_reference(args)
     if args.mode == "casimir":
         return run_casimir(args)
+    if args.mode in ("ensemble", "serving"):
+        import torch
+
+        torch.cuda.set_device(0)
+        if args.mode == "ensemble":
+            tun, _ = _tuning(args, 512)
+            out = _ensemble(args, tun, args.steps)
+        else:
+            out = _serving(args, args.serve_seconds)
+        out["mode"] = args.mode
+        print(json.dumps(out), flush=True)
+        return 0
     return run_gpu(args)
 
 

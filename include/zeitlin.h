@@ -133,6 +133,10 @@ ZT_API int isomp_run(zt_plan* plan, double* W, double h, long nsteps, double tol
  * ZT_ECUDA, ZT_ETIMEOUT. */
 ZT_API int zt_zgemm_skew(zt_plan* plan, const double* X, const double* Y, double* C, void* stream);
 
+/* Device bytes a plan for (N, precision, tuning) allocates (for admission by
+ * memory footprint); -1 for an invalid N.  `opt` may be NULL. */
+ZT_API long long zt_plan_estimate_bytes(int N, int precision, const zt_tuning* opt);
+
 /* Number of kernel launches the library enqueued since the plan was created
  * (every launch of every entry point on this plan). */
 ZT_API long zt_plan_launch_count(const zt_plan* plan);

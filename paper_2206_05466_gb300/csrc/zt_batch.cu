@@ -87,7 +87,9 @@ struct zt_batch {
     int use_graph = 0;
     cudaGraphExec_t g_first = nullptr, g_more = nullptr;
     long g_first_k = 0, g_more_k = 0;   // kernels in each graph
-    cudaStream_t g_stream = nullptr;
+    cudaStream_t g_stream = nullptr;   // stream the graphs were captured for (the caller's)
+    cudaStream_t own = nullptr;        // non-blocking stream the graphs are captured on and replayed on
+    cudaEvent_t ev_in = nullptr;
     int g_tol_maxit_set = 0;
     double g_tol = 0.0;
     int g_maxit = 0;
@@ -259,6 +261,8 @@ extern "C" void zt_batch_destroy(zt_batch* b) {
     if (!b) return;
     cudaDeviceSynchronize();
     drop_graphs(b);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->own) cudaStreamDestroy(b->own);
     cudaFree(b->dbuf);
     cudaFree(b->dstates);
     cudaFree(b->gathered);
@@ -415,6 +419,10 @@ extern "C" int zt_batch_set_graph(zt_batch* b, int enable) {
     ZT_CU(cudaDeviceSynchronize());
     drop_graphs(b);
     b->use_graph = enable ? 1 : 0;
+    if (b->use_graph && !b->own) {   // the legacy default stream cannot be captured
+        ZT_CU(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking));
+        ZT_CU(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+    }
     return ZT_OK;
 }
 
@@ -423,7 +431,10 @@ extern "C" long zt_batch_launch_count(const zt_batch* b) { return b ? b->launche
 static int batch_step_impl(zt_batch* b, double tol, int maxit, zt_step_stats* stats, cudaStream_t s) {
     int rc;
     const int spc = b->sweeps_per_sync;
-    if (b->use_graph) {
+    if (b->use_graph) {   // work goes to the batch's own stream, after what the caller queued on s
+        ZT_CU(cudaEventRecord(b->ev_in, s));
+        ZT_CU(cudaStreamWaitEvent(b->own, b->ev_in, 0));
+        s = b->own;
         if (b->g_tol_maxit_set && (b->g_tol != tol || b->g_maxit != maxit || b->g_stream != s)) drop_graphs(b);
         if (!b->g_first) {
             if ((rc = capture(b, s, &b->g_first, true, tol, maxit, spc))) return rc;

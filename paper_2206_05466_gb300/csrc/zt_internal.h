@@ -243,6 +243,7 @@ int zt_update_grouped(const UpdateArgs* tab, const int* offs, int n, int total, 
 int zt_converge_grouped(const ConvArgs* tab, int n, cudaStream_t s);
 // Split-precision version (tcgen05).  Same contract.
 int zt_split_create(zt_plan* p);
+size_t zt_split_bytes(int N, const zt_tuning& t);   // device bytes of the split workspace
 void zt_split_destroy(zt_plan* p);
 int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double2* C,
                           double alpha, int lower_only, cudaStream_t s, int gate);

@@ -409,6 +409,27 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     delete p;
 }
 
+static void fill_tuning_defaults(zt_tuning& t) {
+    if (t.slices == 0) t.slices = 7;
+    if (t.digit_bits == 0) t.digit_bits = 7;
+    if (t.exact_groups == 0) t.exact_groups = 4;
+    if (t.sweeps_per_sync == 0) t.sweeps_per_sync = 4;
+    if (t.cluster_m == 0) t.cluster_m = 2;
+    if (t.cluster_n == 0) t.cluster_n = 1;
+}
+
+extern "C" long long zt_plan_estimate_bytes(int N, int precision, const zt_tuning* opt) {
+    if (N < 1 || N > 16384) return -1;
+    zt_tuning t{};
+    if (opt) t = *opt;
+    fill_tuning_defaults(t);
+    const size_t nn = (size_t)N * N, ntri = (size_t)N * (N + 1) / 2;
+    const size_t nt = (N + 31) / 32, nseg = (N + 63) / 64;
+    size_t b = 4 * ntri * 8 + 5 * nn * 16 + nt * (nt + 1) / 2 * 8 + (size_t)N * nseg * 48 + nseg * 24 + 1024;
+    if (precision == ZT_PRECISION_SPLIT) b += zt_split_bytes(N, t);
+    return (long long)b;
+}
+
 extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_plan** out) {
     if (!out) return zt_fail(ZT_EINVAL, "zt_plan_create: out is NULL");
     *out = nullptr;
@@ -420,12 +441,7 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     p->N = N;
     p->precision = precision;
     if (opt) p->tun = *opt;
-    if (p->tun.slices == 0) p->tun.slices = 7;
-    if (p->tun.digit_bits == 0) p->tun.digit_bits = 7;
-    if (p->tun.exact_groups == 0) p->tun.exact_groups = 4;
-    if (p->tun.sweeps_per_sync == 0) p->tun.sweeps_per_sync = 4;
-    if (p->tun.cluster_m == 0) p->tun.cluster_m = 2;
-    if (p->tun.cluster_n == 0) p->tun.cluster_n = 1;
+    fill_tuning_defaults(p->tun);
     if (p->tun.final_mode != ZT_FINAL_FRESH && p->tun.final_mode != ZT_FINAL_REUSE) {
         delete p;
         return zt_fail(ZT_EINVAL, "zt_plan_create: bad final_mode %d", opt->final_mode);

@@ -741,6 +741,15 @@ int zt_split_create(zt_plan* p) {
     return ZT_OK;
 }
 
+size_t zt_split_bytes(int N, const zt_tuning& t) {
+    const int s = t.slices, cm = t.cluster_m, cn = t.cluster_n;
+    const size_t ldk = (size_t)round_up(2 * N, BK), Mpad = (size_t)round_up(N, BM * cm),
+                 Npad = (size_t)round_up(2 * N, BN * cn);
+    const size_t nkb = ldk / BK, ngA = Mpad / (BM * cm), ngB = Npad / (BN * cn);
+    return (size_t)s * Mpad * ldk * 2 + 2 * (size_t)s * Npad * ldk * 2 + Mpad * 4 + 2 * Npad * 4 +
+           ngA * nkb * 4 + 2 * ngB * nkb * 4;
+}
+
 void zt_split_destroy(zt_plan* p) {
     zt_split_ws* w = p->split;
     if (!w) return;

@@ -102,6 +102,8 @@ def load(build_if_missing: bool = True):
     L.zt_plan_kernel_time.argtypes = [vp, i, lp, dp, dp, dp]
     L.zt_plan_kernel_time.restype = i
     P = ctypes.POINTER
+    L.zt_plan_estimate_bytes.argtypes = [i, i, P(Tuning)]
+    L.zt_plan_estimate_bytes.restype = ctypes.c_longlong
     L.zt_batch_create.argtypes = [i, P(vp), P(vp), P(d), P(vp)]
     L.zt_batch_create.restype = i
     L.zt_batch_destroy.argtypes = [vp]
@@ -271,3 +273,14 @@ class Batch:
                                              _stream(stream)), allow)
         return {"status": rc, "steps": st.steps, "total_iters": st.total_iters, "max_iters": st.max_iters,
                 "all_converged": bool(st.all_converged), "max_residual": st.max_residual}
+
+
+def plan_estimate_bytes(N: int, precision: int = PRECISION_FP64, **tuning) -> int:
+    """Device bytes a plan would allocate (library formula)."""
+    t = Tuning(tuning.get("slices", 0), tuning.get("digit_bits", 0), tuning.get("exact_groups", 0),
+               tuning.get("final_mode", 0), tuning.get("sweeps_per_sync", 0), tuning.get("cluster_m", 0),
+               tuning.get("cluster_n", 0), 1 if tuning.get("dense", 0) else 0)
+    v = load().zt_plan_estimate_bytes(int(N), int(precision), ctypes.byref(t))
+    if v < 0:
+        raise ValueError(f"invalid N={N}")
+    return int(v)
