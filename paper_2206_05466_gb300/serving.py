@@ -3,21 +3,23 @@
 Jobs (N, number of steps, h, precision, initial state) arrive over time.  A job
 is admitted when its plan's device footprint fits the memory budget (first
 come, first served); its state then stays resident on the device until its
-last step.  Every loop iteration advances all resident jobs by one IsoMP step
-in one batched step (grouped kernels over jobs of any mix of N), so jobs that
-arrive while others are running join the next step -- their work overlaps on
-the device with the jobs already resident.  The batch is rebuilt only when the
-resident set changes.  All arithmetic runs in the library's kernels; this
-module only schedules.
+last step.  Resident jobs of like N and precision form a class; each class is
+advanced by its own worker thread on its own CUDA stream, one batched step
+(grouped kernels over all the class's jobs) per iteration.  Jobs that arrive
+while others are running join their class's batch at its next step, and
+classes run concurrently on the device, so small jobs do not wait for large
+ones.  A class's batch is rebuilt only when its resident set changes.  All
+arithmetic runs in the library's kernels; this module only schedules.
 
 Reported: per-step latency of resident jobs (time between a job's consecutive
-completed steps; p50/p99), aggregate job-steps/s, queueing delay (arrival to
-admission), and the peak of admitted footprint.
+completed steps; p50/p99, overall and per class), aggregate job-steps/s,
+queueing delay (arrival to admission) and the peak of admitted footprint.
 """
 from __future__ import annotations
 
 import collections
 import dataclasses
+import threading
 import time
 
 import numpy as np
@@ -43,8 +45,11 @@ class _Resident:
     W: object               # device tensor
     bytes: int
     remaining: int
-    admitted: float
     last_done: float
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs) * 1e3, q)) if len(xs) else None
 
 
 class Server:
@@ -55,91 +60,145 @@ class Server:
         self.graph = graph
 
     def run(self, jobs, time_limit: float | None = None, keep_results: bool = False, clock=time.perf_counter):
-        """Serve `jobs` (sorted or not by arrival).  Returns a report dict."""
+        """Serve `jobs`; returns a report dict (results by job id if keep_results)."""
         import torch
 
+        dev = torch.cuda.current_device()
+        lock = threading.Lock()
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
         queue = collections.deque()
-        active: dict[int, _Resident] = {}
-        used = peak = 0
-        batch, dirty = None, True
-        lat, qdelay, results = [], [], {}
-        steps_done = 0
-        completed = 0
-        batched_steps = 0
+        classes: dict[tuple, dict[int, _Resident]] = {}
+        dirty: dict[tuple, bool] = {}
+        workers: dict[tuple, threading.Thread] = {}
+        lat: dict[tuple, list] = collections.defaultdict(list)
+        qdelay, results, errors = [], {}, []
+        st = {"used": 0, "peak": 0, "steps": 0, "completed": 0, "batched": 0, "stop": False}
         t0 = clock()
-        while pending or queue or active:
+
+        def worker(cls):
+            torch.cuda.set_device(dev)
+            stream = torch.cuda.Stream()
+            batch, order = None, []
+            try:
+                while True:
+                    with lock:
+                        res = dict(classes[cls])
+                        changed = dirty[cls]
+                        dirty[cls] = False
+                        stop = st["stop"]
+                    if stop or not res:
+                        if batch is not None:
+                            batch.close()
+                            batch = None
+                        if stop or (not pending and not queue):
+                            with lock:
+                                if not classes[cls] and (st["stop"] or (not pending and not queue)):
+                                    return
+                        time.sleep(0.001)
+                        continue
+                    if changed or batch is None:
+                        if batch is not None:
+                            batch.close()
+                        order = sorted(res)
+                        batch = z.Batch([res[j].plan for j in order], [res[j].W for j in order],
+                                        [res[j].job.h for j in order])
+                        if self.graph:
+                            batch.set_graph(True)
+                    with torch.cuda.stream(stream):
+                        batch.step(self.tol, self.maxit, stream=stream, allow_not_converged=True)
+                    t_done = clock() - t0
+                    finished = []
+                    with lock:
+                        st["batched"] += 1
+                        for j in order:
+                            r = classes[cls][j]
+                            lat[cls].append(t_done - r.last_done)
+                            r.last_done = t_done
+                            r.remaining -= 1
+                            st["steps"] += 1
+                            if r.remaining == 0:
+                                finished.append(r)
+                    if finished:
+                        batch.close()
+                        batch = None
+                        for r in finished:
+                            if keep_results:
+                                results[r.job.jid] = r.W.cpu().numpy()
+                            r.plan.close()
+                        with lock:
+                            for r in finished:
+                                del classes[cls][r.job.jid]
+                                st["used"] -= r.bytes
+                                st["completed"] += 1
+                            dirty[cls] = True
+            except Exception as e:   # surfaced to the caller after the run
+                errors.append(repr(e))
+                with lock:
+                    st["stop"] = True
+
+        while True:
             now = clock() - t0
-            if time_limit is not None and now > time_limit:
+            if time_limit is not None and now > time_limit or errors:
+                with lock:
+                    st["stop"] = True
                 break
-            while pending and pending[0].arrival <= now:
-                queue.append(pending.popleft())
+            with lock:
+                while pending and pending[0].arrival <= now:
+                    queue.append(pending.popleft())
+            admitted = False
             while queue:   # first come, first served, by device footprint
                 job = queue[0]
                 need = z.plan_estimate_bytes(job.N, job.precision)
-                if used + need > self.budget and active:
-                    break
-                queue.popleft()
+                with lock:
+                    resident = sum(len(c) for c in classes.values())
+                    if st["used"] + need > self.budget and resident:
+                        break
+                    queue.popleft()
                 plan = z.Plan(job.N, job.precision)
                 W = torch.from_numpy(np.ascontiguousarray(job.W0)).cuda()
+                torch.cuda.synchronize()
                 t_adm = clock() - t0
-                active[job.jid] = _Resident(job, plan, W, need, job.nsteps, t_adm, t_adm)
-                qdelay.append(t_adm - job.arrival)
-                used += need
-                peak = max(peak, used)
-                dirty = True
-            if not active:
-                if pending:   # idle until the next arrival
-                    time.sleep(max(0.0, min(0.01, pending[0].arrival - (clock() - t0))))
-                continue
-            if dirty:
-                if batch is not None:
-                    batch.close()
-                res = list(active.values())
-                batch = z.Batch([r.plan for r in res], [r.W for r in res], [r.job.h for r in res])
-                if self.graph:
-                    batch.set_graph(True)
-                order = [r.job.jid for r in res]
-                dirty = False
-            rc, st = batch.step(self.tol, self.maxit, allow_not_converged=True)
-            t_done = clock() - t0
-            batched_steps += 1
-            for jid in order:
-                r = active[jid]
-                lat.append(t_done - r.last_done)
-                r.last_done = t_done
-                r.remaining -= 1
-                steps_done += 1
-            for jid in list(order):
-                r = active[jid]
-                if r.remaining == 0:
-                    if keep_results:
-                        results[jid] = r.W.cpu().numpy()
-                    used -= r.bytes
-                    r.plan.close()
-                    del active[jid]
-                    completed += 1
-                    dirty = True
-            if dirty and batch is not None:
-                batch.close()
-                batch = None
+                cls = (job.N, job.precision)
+                with lock:
+                    classes.setdefault(cls, {})[job.jid] = _Resident(job, plan, W, need, job.nsteps, t_adm)
+                    dirty[cls] = True
+                    st["used"] += need
+                    st["peak"] = max(st["peak"], st["used"])
+                    qdelay.append(t_adm - job.arrival)
+                    if cls not in workers or not workers[cls].is_alive():
+                        th = threading.Thread(target=worker, args=(cls,), daemon=True)
+                        workers[cls] = th
+                        th.start()
+                admitted = True
+            with lock:
+                empty = not pending and not queue and not any(classes.values())
+            if empty:
+                break
+            if not admitted:
+                time.sleep(0.001)
+        for th in list(workers.values()):
+            th.join()
         wall = clock() - t0
-        if batch is not None:
-            batch.close()
-        for r in active.values():
-            r.plan.close()
-        lat_ms = np.asarray(lat) * 1e3
+        for c in classes.values():
+            for r in c.values():
+                r.plan.close()
+        if errors:
+            raise RuntimeError("serving worker failed: " + errors[0])
+        allat = [x for v in lat.values() for x in v]
         return {
             "wall_s": wall,
-            "job_steps": steps_done,
-            "job_steps_per_s": steps_done / wall if wall > 0 else 0.0,
-            "batched_steps": batched_steps,
-            "jobs_completed": completed,
+            "job_steps": st["steps"],
+            "job_steps_per_s": st["steps"] / wall if wall > 0 else 0.0,
+            "batched_steps": st["batched"],
+            "jobs_completed": st["completed"],
             "jobs_admitted": len(qdelay),
             "jobs_left_queued": len(queue) + len(pending),
-            "step_latency_ms_p50": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
-            "step_latency_ms_p99": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
+            "step_latency_ms_p50": _pct(allat, 50),
+            "step_latency_ms_p99": _pct(allat, 99),
+            "per_class": {f"N={k[0]},{'split' if k[1] == z.PRECISION_SPLIT else 'fp64'}":
+                          {"job_steps": len(v), "p50_ms": _pct(v, 50), "p99_ms": _pct(v, 99)}
+                          for k, v in lat.items()},
             "queue_delay_s_p50": float(np.percentile(qdelay, 50)) if qdelay else None,
-            "peak_admitted_bytes": peak,
+            "peak_admitted_bytes": st["peak"],
             "results": results,
         }
