@@ -259,7 +259,10 @@ void drop_graphs(zt_batch* b) {
 
 extern "C" void zt_batch_destroy(zt_batch* b) {
     if (!b) return;
-    cudaDeviceSynchronize();
+    // steps end with a host synchronisation; only graph replays on the own
+    // stream can still be in flight (no device-wide sync: another thread may
+    // be capturing a graph)
+    if (b->own) cudaStreamSynchronize(b->own);
     drop_graphs(b);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->own) cudaStreamDestroy(b->own);
@@ -416,7 +419,7 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
 
 extern "C" int zt_batch_set_graph(zt_batch* b, int enable) {
     if (!b) return zt_fail(ZT_EINVAL, "batch is NULL");
-    ZT_CU(cudaDeviceSynchronize());
+    if (b->own) ZT_CU(cudaStreamSynchronize(b->own));
     drop_graphs(b);
     b->use_graph = enable ? 1 : 0;
     if (b->use_graph && !b->own) {   // the legacy default stream cannot be captured
