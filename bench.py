@@ -104,6 +104,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_T0 = time.perf_counter()
+
+
+def _log(msg):
+    print(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -334,12 +341,14 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
 
     # ---- warm-up ----
+    _log('warm-up')
     iters = []
     for _ in range(args.warmup):
         iters.append(z.isomp_step(plan, Wd, H, TOL, MAXIT)["iters"])
     torch.cuda.synchronize()
 
     # ---- timed region: exactly K steps, inputs resident in HBM ----
+    _log('timed region')
     clk = ClockSampler(local)
     clk.start()
     plan.set_timing(True)
@@ -366,6 +375,7 @@ def run_gpu(args):
     value = ws * args.steps / (t_max / 1e3)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed ----
+    _log('e2e')
     Wh = torch.from_numpy(W0).pin_memory()
     Wout = torch.empty_like(Wh).pin_memory()
     Wd2 = torch.empty_like(Wd)
@@ -383,6 +393,7 @@ def run_gpu(args):
            "d2h_bytes_per_step": int(Wout.numel() * 16), "steps": e2e_steps}
 
     # ---- plain FP64 form on the same GPU (same workload) ----
+    _log('fp64 form')
     fp64 = None
     if args.fp64_steps > 0:
         plan64 = z.Plan(N, z.PRECISION_FP64)
@@ -405,6 +416,7 @@ def run_gpu(args):
         del W64
 
     # ---- accuracy and CPU baseline (rank 0): oracle vs both forms after the same steps ----
+    _log('oracle baseline')
     cpu_baseline, accuracy = None, None
     if rank == 0 and args.oracle_steps > 0:
         k = args.oracle_steps
@@ -426,10 +438,13 @@ def run_gpu(args):
         accuracy = acc
 
     ens = serve = None
+    _log("ensemble")
     if rank == 0 and args.ens_steps > 0:
         ens = _ensemble(args, tun, args.ens_steps)
     if rank == 0 and args.serve_seconds > 0:
+        _log("serving")
         serve = _serving(args, args.serve_seconds)
+    _log("done")
     if rank != 0:
         return 0
     pairs = tun["slices"] * (tun["slices"] + 1) / 2

@@ -477,19 +477,25 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     ZT_TRY(cudaMalloc(&p->partials, (size_t)p->npartials * sizeof(double)));
     ZT_TRY(cudaMalloc(&p->state, sizeof(zt_dev_state)));
     ZT_TRY(cudaMalloc(&p->d_units, sizeof(unsigned long long)));
-    ZT_TRY(cudaMemset(p->d_units, 0, sizeof(unsigned long long)));
     ZT_TRY(cudaMallocHost(&p->h_state, sizeof(zt_dev_state)));
-    ZT_TRY(cudaMemset(p->state, 0, sizeof(zt_dev_state)));
+    // set-up work runs on a private stream so that creating a plan does not
+    // wait for work other threads have queued on the device
     rc = zt_solve_create(p);
     if (rc != ZT_OK) return fail(rc);
-    factor_kernel<<<(N + 127) / 128, 128>>>(N, p->lap_a, p->lap_b, p->fac_l, p->fac_nd);
-    ZT_TRY(cudaGetLastError());
+    cudaStream_t cs = nullptr;
+    ZT_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaMemsetAsync(p->state, 0, sizeof(zt_dev_state), cs);
+    cudaMemsetAsync(p->d_units, 0, sizeof(unsigned long long), cs);
+    factor_kernel<<<(N + 127) / 128, 128, 0, cs>>>(N, p->lap_a, p->lap_b, p->fac_l, p->fac_nd);
     p->launches++;
+    cudaError_t se = cudaGetLastError();
+    if (se == cudaSuccess) se = cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+    if (se != cudaSuccess) return fail(zt_cuda_check(se, "plan set-up (factor_kernel)"));
     if (precision == ZT_PRECISION_SPLIT) {
         rc = zt_split_create(p);
         if (rc != ZT_OK) return fail(rc);
     }
-    ZT_TRY(cudaDeviceSynchronize());
 #undef ZT_TRY
     *out = p;
     return ZT_OK;

@@ -713,12 +713,23 @@ int zt_split_create(zt_plan* p) {
         while (bound >= std::ldexp(1.0, 62 + u)) ++u;
         w->u = u;
     }
+    cudaStream_t cs = nullptr;   // set-up on a private stream (no wait on other threads' work)
+    ZT_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() {
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+        }
+    } guard{cs};
     const size_t szA = (size_t)s * w->Mpad * w->ldk * sizeof(__nv_bfloat16);
     const size_t szB = (size_t)s * w->Npad * w->ldk * sizeof(__nv_bfloat16);
     ZT_CU(cudaMalloc(&w->dA, szA));
-    ZT_CU(cudaMemset(w->dA, 0, szA));   // padding rows/columns stay zero
+    ZT_CU(cudaMemsetAsync(w->dA, 0, szA, cs));   // padding rows/columns stay zero
     ZT_CU(cudaMalloc(&w->eA, (size_t)w->Mpad * sizeof(int)));
-    ZT_CU(cudaMemset(w->eA, 0, (size_t)w->Mpad * sizeof(int)));
+    ZT_CU(cudaMemsetAsync(w->eA, 0, (size_t)w->Mpad * sizeof(int), cs));
     int rc;
     if ((rc = make_map(&w->tmA, w->dA, s * w->Mpad, w->ldk, BM / cn))) return rc;
     w->nkb = w->ldk / BK;
@@ -726,14 +737,14 @@ int zt_split_create(zt_plan* p) {
     w->ngA = w->Mpad / (BM * cm);
     w->ngB = w->Npad / (BN * cn);
     ZT_CU(cudaMalloc(&w->occA, (size_t)w->ngA * w->nkb * sizeof(int)));
-    ZT_CU(cudaMemset(w->occA, 0, (size_t)w->ngA * w->nkb * sizeof(int)));
+    ZT_CU(cudaMemsetAsync(w->occA, 0, (size_t)w->ngA * w->nkb * sizeof(int), cs));
     for (int b = 0; b < 2; ++b) {
         ZT_CU(cudaMalloc(&w->occB[b], (size_t)w->ngB * w->nkb * sizeof(int)));
-        ZT_CU(cudaMemset(w->occB[b], 0, (size_t)w->ngB * w->nkb * sizeof(int)));
+        ZT_CU(cudaMemsetAsync(w->occB[b], 0, (size_t)w->ngB * w->nkb * sizeof(int), cs));
         ZT_CU(cudaMalloc(&w->dB[b], szB));
-        ZT_CU(cudaMemset(w->dB[b], 0, szB));
+        ZT_CU(cudaMemsetAsync(w->dB[b], 0, szB, cs));
         ZT_CU(cudaMalloc(&w->eB[b], (size_t)w->Npad * sizeof(int)));
-        ZT_CU(cudaMemset(w->eB[b], 0, (size_t)w->Npad * sizeof(int)));
+        ZT_CU(cudaMemsetAsync(w->eB[b], 0, (size_t)w->Npad * sizeof(int), cs));
         if ((rc = make_map(&w->tmB[b], w->dB[b], s * w->Npad, w->ldk, BN / cm))) return rc;
     }
     ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));

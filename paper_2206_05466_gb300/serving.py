@@ -86,13 +86,17 @@ class Server:
                         changed = dirty[cls]
                         dirty[cls] = False
                         stop = st["stop"]
-                    if stop or not res:
+                    if stop:   # time limit: leave; resident jobs are released by the caller
+                        if batch is not None:
+                            batch.close()
+                        return
+                    if not res:
                         if batch is not None:
                             batch.close()
                             batch = None
-                        if stop or (not pending and not queue):
+                        if not pending and not queue:
                             with lock:
-                                if not classes[cls] and (st["stop"] or (not pending and not queue)):
+                                if not classes[cls] and not pending and not queue:
                                     return
                         time.sleep(0.001)
                         continue
@@ -147,6 +151,8 @@ class Server:
                     queue.append(pending.popleft())
             admitted = False
             while queue:   # first come, first served, by device footprint
+                if time_limit is not None and clock() - t0 > time_limit:
+                    break
                 job = queue[0]
                 need = z.plan_estimate_bytes(job.N, job.precision)
                 with lock:
