@@ -198,6 +198,8 @@ int enqueue_final(zt_batch* b, cudaStream_t s) {
                                 b->upd_final.total, s, ZT_GATE_FINAL)))
         return rc;
     b->launches++;
+    if ((rc = zt_finalize_mark_grouped(b->dstates, b->n, s))) return rc;
+    b->launches++;
     return ZT_OK;
 }
 

@@ -18,7 +18,7 @@ struct zt_dev_state {
     int    nonfinite;   // residual was NaN/Inf
     int    timeout;     // a bounded device wait ran out (tcgen05 kernels)
     int    maxit;
-    int    finalized;   // W_{n+1} has been written (the final kernels ran)
+    int    finalized;   // W_{n+1} has been written (set after the final assembly completed)
     int    pad1;
     double residual;    // last Frobenius residual
     double tol;
@@ -241,6 +241,7 @@ int zt_fp64_gemm_grouped(const Fp64GemmArgs* tab, const int* offs, int n, int to
 int zt_update_ctas(int N);
 int zt_update_grouped(const UpdateArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
 int zt_converge_grouped(const ConvArgs* tab, int n, cudaStream_t s);
+int zt_finalize_mark_grouped(zt_dev_state* const* sts, int n, cudaStream_t s);
 // Split-precision version (tcgen05).  Same contract.
 int zt_split_create(zt_plan* p);
 size_t zt_split_bytes(int N, const zt_tuning& t);   // device bytes of the split workspace

@@ -266,7 +266,25 @@ __device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
         }
         if (threadIdx.x == 0) partials[t] = sred[0];
     }
-    if (ua.final_write && t == 0 && threadIdx.x == 0) ua.st->finalized = 1;
+}
+
+// After the final assembly has completed (a separate launch: CTAs of the
+// assembly itself may still be waiting to start when its first CTA ends),
+// mark converged-and-assembled states so later rounds skip their final kernels.
+__global__ void finalize_mark_kernel(zt_dev_state* st) {
+    if (st->done) st->finalized = 1;
+}
+
+__global__ void finalize_mark_grouped(zt_dev_state* const* sts, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && sts[i]->done) sts[i]->finalized = 1;
+}
+
+int zt_finalize_mark_grouped(zt_dev_state* const* sts, int n, cudaStream_t s) {
+    finalize_mark_grouped<<<(n + 127) / 128, 128, 0, s>>>(sts, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "finalize_mark_grouped");
+    return ZT_OK;
 }
 
 __global__ void __launch_bounds__(256) update_kernel(const UpdateArgs a) { update_body(a, blockIdx.x); }
@@ -581,7 +599,9 @@ static int enqueue_final(zt_plan* p, int tag, double2* W, double h, cudaStream_t
     if (p->tun.final_mode == ZT_FINAL_FRESH && (rc = enqueue_products(p, s, ZT_GATE_FINAL))) return rc;
     rc = launch_update(p, p->Wt, nullptr, W, h, -1.0, false, s, ZT_GATE_FINAL);
     p->cur_sweep = -1;
-    return rc;
+    if (rc) return rc;
+    finalize_mark_kernel<<<1, 1, 0, s>>>(p->state);
+    return launch_check(p, "finalize_mark_kernel");
 }
 
 static int step_impl(zt_plan* p, double2* W, double h, double tol, int maxit, zt_step_stats* stats,
