@@ -64,6 +64,7 @@ class Server:
         import torch
 
         dev = torch.cuda.current_device()
+        upload = torch.cuda.Stream()   # admissions copy state here, never waiting on running steps
         lock = threading.Lock()
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
         queue = collections.deque()
@@ -161,8 +162,9 @@ class Server:
                         break
                     queue.popleft()
                 plan = z.Plan(job.N, job.precision)
-                W = torch.from_numpy(np.ascontiguousarray(job.W0)).cuda()
-                torch.cuda.synchronize()
+                with torch.cuda.stream(upload):
+                    W = torch.from_numpy(np.ascontiguousarray(job.W0)).cuda(non_blocking=False)
+                upload.synchronize()
                 t_adm = clock() - t0
                 cls = (job.N, job.precision)
                 with lock:
