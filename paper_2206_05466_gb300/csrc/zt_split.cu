@@ -195,15 +195,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// K blocks per accumulation segment of digit group g: short enough that the
-// FP32 sums of the leading groups stay exact integers.
-__device__ __host__ inline int seg_kblocks(int g, int beta, int exact_groups, int nkb) {
-    if (g >= exact_groups) return nkb;
-    // (g+1) * kc * BK * 2^(2 beta - 2) <= 2^24
-    long long lim = (1LL << (26 - 2 * beta)) / ((long long)BK * (g + 1));
-    if (lim < 1) lim = 1;
-    return (int)(lim < nkb ? lim : nkb);
-}
 
 // ---------------------------------------------------------------------------
 // Splitting: one CTA per row of X (complex, N entries).  Writes X' digits
@@ -354,12 +345,25 @@ __global__ void __launch_bounds__(256) split_rows_grouped(const SplitRowsArgs* t
     split_rows_body(a, blockIdx.x - offs[inst]);
 }
 
-// A segment (digit group g, K blocks [kb0, kend)) has a nonzero unit iff some
-// K block has fa + fb <= g.
-__device__ __forceinline__ bool seg_has_units(const uint8_t* fa, const uint8_t* fb, int g, int kb0, int kend) {
-    for (int kb = kb0; kb < kend; ++kb)
-        if (fa[kb] + fb[kb] <= g) return true;
-    return false;
+// Accumulation segments are counted in issued MMA units (one digit pair on
+// one K block of 64): a leading (exact) group may sum at most
+// 2^(26 - 2 beta) / 64 units in FP32 before it must be drained, so that every
+// partial sum stays an exact integer; later groups run to the end.  Units
+// skipped because they are all zero do not count, so sparse tiles drain
+// rarely.
+__device__ __forceinline__ int seg_units(int g, int beta, int exact_groups) {
+    if (g >= exact_groups) return 0x7fffffff;
+    const int lim = (1 << (26 - 2 * beta)) / BK;
+    return lim < 1 ? 1 : lim;
+}
+// Active units of digit group g on this tile: pairs p in [fa, g - fb] per K block.
+__device__ __forceinline__ int group_units(const uint8_t* fa, const uint8_t* fb, int g, int nkb) {
+    int n = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int c = g - fb[kb] - fa[kb] + 1;
+        n += c > 0 ? c : 0;
+    }
+    return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -457,10 +461,8 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
             uint32_t ph = 0;
             bool ok = true;
             for (int g = 0; g < a.s && ok; ++g) {
-                const int kc = seg_kblocks(g, a.beta, a.exact_groups, nkb);
-                for (int kb0 = 0; kb0 < nkb && ok; kb0 += kc) {
-                    const int kend = min(kb0 + kc, nkb);
-                    for (int kb = kb0; kb < kend && ok; ++kb) {
+                {
+                    for (int kb = 0; kb < nkb && ok; ++kb) {
                         for (int p = fa[kb]; p <= g - fb[kb]; ++p) {
                             if (!mbar_wait(&empty[stage], ph ^ 1, abort_flag)) {
                                 ok = false;
@@ -494,45 +496,51 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
             uint32_t ph = 0;
             bool ok = true;
             for (int g = 0; g < a.s && ok; ++g) {
-                const int kc = seg_kblocks(g, a.beta, a.exact_groups, nkb);
-                for (int kb0 = 0; kb0 < nkb && ok; kb0 += kc) {
-                    const int kend = min(kb0 + kc, nkb);
-                    if (!seg_has_units(fa, fb, g, kb0, kend)) continue;
-                    const int b = seg & 1;
-                    ++seg;
-                    if (!mbar_wait(&acce[b], (((seg - 1) >> 1) & 1) ^ 1, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(b * BN);
-                    bool first = true;
-                    for (int kb = kb0; kb < kend && ok; ++kb) {
-                        for (int p = fa[kb]; p <= g - fb[kb]; ++p) {
-                            if (!mbar_wait(&full[stage], ph, abort_flag)) {
+                const int ulim = seg_units(g, a.beta, a.exact_groups);
+                int cnt = 0, b = 0;
+                bool open = false;
+                uint32_t d = 0;
+                for (int kb = 0; kb < nkb && ok; ++kb) {
+                    for (int p = fa[kb]; p <= g - fb[kb]; ++p) {
+                        if (!open) {   // next accumulation segment: wait for its TMEM buffer to be drained
+                            b = seg & 1;
+                            ++seg;
+                            if (!mbar_wait(&acce[b], (((seg - 1) >> 1) & 1) ^ 1, abort_flag)) {
                                 ok = false;
                                 break;
                             }
                             tc_fence_after();
-                            const uint64_t ad = sw128_desc(smem_u32(sA + stage * A_TILE));
-                            const uint64_t bd = sw128_desc(smem_u32(sB + stage * B_TILE));
+                            d = tmem + (uint32_t)(b * BN);
+                            open = true;
+                            cnt = 0;
+                        }
+                        if (!mbar_wait(&full[stage], ph, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ad = sw128_desc(smem_u32(sA + stage * A_TILE));
+                        const uint64_t bd = sw128_desc(smem_u32(sB + stage * B_TILE));
 #pragma unroll
-                            for (int k = 0; k < BK / 16; ++k)
-                                umma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (first && k == 0) ? 0u : 1u);
-                            first = false;
-                            ++issued;
-                            if (cs > 1)
-                                umma_commit_mc(&empty[stage], mask_all);
-                            else
-                                umma_commit(&empty[stage]);
-                            if (++stage == STAGES) {
-                                stage = 0;
-                                ph ^= 1;
-                            }
+                        for (int k = 0; k < BK / 16; ++k)
+                            umma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (cnt == 0 && k == 0) ? 0u : 1u);
+                        ++cnt;
+                        ++issued;
+                        if (cs > 1)
+                            umma_commit_mc(&empty[stage], mask_all);
+                        else
+                            umma_commit(&empty[stage]);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            ph ^= 1;
+                        }
+                        if (cnt == ulim) {   // exactness budget of this segment used up
+                            umma_commit(&accf[b]);
+                            open = false;
                         }
                     }
-                    if (ok) umma_commit(&accf[b]);
                 }
+                if (ok && open) umma_commit(&accf[b]);
             }
             if (a.units) atomicAdd(a.units, issued);
             // all MMAs issued by this thread retire before TMEM is released
@@ -550,10 +558,11 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
         int seg = 0;
         bool ok = true;
         for (int g = 0; g < a.s && ok; ++g) {
-            const int kc = seg_kblocks(g, a.beta, a.exact_groups, nkb);
+            const int ulim = seg_units(g, a.beta, a.exact_groups);
+            const int units = group_units(fa, fb, g, nkb);
+            const int nsegs = units == 0 ? 0 : (units - 1) / ulim + 1;
             const int sh = (a.s - 1 - g) * a.beta - a.u;
-            for (int kb0 = 0; kb0 < nkb; kb0 += kc) {
-                if (!seg_has_units(fa, fb, g, kb0, min(kb0 + kc, nkb))) continue;
+            for (int q = 0; q < nsegs; ++q) {
                 const int b = seg & 1;
                 ++seg;
                 if (!mbar_wait(&accf[b], (((seg - 1) >> 1) & 1), abort_flag)) {
