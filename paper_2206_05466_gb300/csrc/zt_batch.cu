@@ -80,7 +80,8 @@ struct zt_batch {
     unsigned char* dbuf = nullptr;   // all tables
     zt_dev_state** dstates = nullptr;
     zt_dev_state* gathered = nullptr;
-    zt_dev_state* hstates = nullptr;   // pinned
+    zt_dev_state* hstates = nullptr;   // host copy of the states (pageable)
+    zt_dev_state* hpinned = nullptr;   // pinned copy, graph mode only (captured memcpy target)
     Op copy, solve, split_P, split_W, split_A, gemm1, gemm2, f64a, f64b, upd_sweep, upd_final, conv;
     int sweeps_per_sync = 4;
     long launches = 0;
@@ -207,7 +208,8 @@ int enqueue_read_states(zt_batch* b, cudaStream_t s) {
     state_gather<<<(b->n + 127) / 128, 128, 0, s>>>(b->dstates, b->n, b->gathered);
     int rc = count_launch(b, "state_gather");
     if (rc) return rc;
-    ZT_CU(cudaMemcpyAsync(b->hstates, b->gathered, (size_t)b->n * sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
+    zt_dev_state* dst = b->use_graph ? b->hpinned : b->hstates;
+    ZT_CU(cudaMemcpyAsync(dst, b->gathered, (size_t)b->n * sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
     return ZT_OK;
 }
 
@@ -271,7 +273,8 @@ extern "C" void zt_batch_destroy(zt_batch* b) {
     cudaFree(b->dbuf);
     cudaFree(b->dstates);
     cudaFree(b->gathered);
-    if (b->hstates) cudaFreeHost(b->hstates);
+    delete[] b->hstates;
+    if (b->hpinned) cudaFreeHost(b->hpinned);
     delete b;
 }
 
@@ -413,8 +416,8 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
         return fail(zt_cuda_check(e, "cudaMemcpy"));
     if ((e = cudaMalloc(&b->gathered, count * sizeof(zt_dev_state))) != cudaSuccess)
         return fail(zt_cuda_check(e, "cudaMalloc"));
-    if ((e = cudaMallocHost(&b->hstates, count * sizeof(zt_dev_state))) != cudaSuccess)
-        return fail(zt_cuda_check(e, "cudaMallocHost"));
+    b->hstates = new (std::nothrow) zt_dev_state[count];   // pinned copy only for graph mode
+    if (!b->hstates) return fail(zt_fail(ZT_ENOMEM, "host allocation failed"));
     *out = b;
     return ZT_OK;
 }
@@ -428,6 +431,7 @@ extern "C" int zt_batch_set_graph(zt_batch* b, int enable) {
         ZT_CU(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking));
         ZT_CU(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     }
+    if (b->use_graph && !b->hpinned) ZT_CU(cudaMallocHost(&b->hpinned, (size_t)b->n * sizeof(zt_dev_state)));
     return ZT_OK;
 }
 
@@ -463,6 +467,7 @@ static int batch_step_impl(zt_batch* b, double tol, int maxit, zt_step_stats* st
         }
         enq += nsw;
         ZT_CU(cudaStreamSynchronize(s));
+        if (b->use_graph) std::memcpy(b->hstates, b->hpinned, (size_t)b->n * sizeof(zt_dev_state));
         bool all = true;
         for (int i = 0; i < b->n; ++i) all = all && b->hstates[i].done;
         if (all) break;

@@ -418,7 +418,7 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     cudaFree(p->partials);
     cudaFree(p->state);
     cudaFree(p->d_units);
-    if (p->h_state) cudaFreeHost(p->h_state);
+    delete p->h_state;
     for (int i = 0; i < p->caprecs; ++i) {
         if (p->recs[i].a) cudaEventDestroy(p->recs[i].a);
         if (p->recs[i].b) cudaEventDestroy(p->recs[i].b);
@@ -495,7 +495,8 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     ZT_TRY(cudaMalloc(&p->partials, (size_t)p->npartials * sizeof(double)));
     ZT_TRY(cudaMalloc(&p->state, sizeof(zt_dev_state)));
     ZT_TRY(cudaMalloc(&p->d_units, sizeof(unsigned long long)));
-    ZT_TRY(cudaMallocHost(&p->h_state, sizeof(zt_dev_state)));
+    p->h_state = new (std::nothrow) zt_dev_state();   // pageable: pinning per plan is slow
+    if (!p->h_state) return fail(zt_fail(ZT_ENOMEM, "host allocation failed"));
     // set-up work runs on a private stream so that creating a plan does not
     // wait for work other threads have queued on the device
     rc = zt_solve_create(p);

@@ -72,7 +72,7 @@ class Server:
         dirty: dict[tuple, bool] = {}
         workers: dict[tuple, threading.Thread] = {}
         lat: dict[tuple, list] = collections.defaultdict(list)
-        qdelay, results, errors = [], {}, []
+        qdelay, results, errors, admit_times = [], {}, [], []
         st = {"used": 0, "peak": 0, "steps": 0, "completed": 0, "batched": 0, "stop": False}
         t0 = clock()
 
@@ -161,10 +161,13 @@ class Server:
                     if st["used"] + need > self.budget and resident:
                         break
                     queue.popleft()
+                ta = clock()
                 plan = z.Plan(job.N, job.precision)
+                tb = clock()
                 with torch.cuda.stream(upload):
                     W = torch.from_numpy(np.ascontiguousarray(job.W0)).cuda(non_blocking=False)
                 upload.synchronize()
+                admit_times.append((tb - ta, clock() - tb))
                 t_adm = clock() - t0
                 cls = (job.N, job.precision)
                 with lock:
@@ -208,5 +211,7 @@ class Server:
                           for k, v in lat.items()},
             "queue_delay_s_p50": float(np.percentile(qdelay, 50)) if qdelay else None,
             "peak_admitted_bytes": st["peak"],
+            "admit_plan_ms_mean": float(np.mean([a for a, _ in admit_times]) * 1e3) if admit_times else None,
+            "admit_upload_ms_mean": float(np.mean([b for _, b in admit_times]) * 1e3) if admit_times else None,
             "results": results,
         }
