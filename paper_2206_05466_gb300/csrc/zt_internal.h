@@ -163,6 +163,7 @@ struct SplitArgs {     // tcgen05 split product (zt_split.cu)
     unsigned long long* units;   // if not NULL: += MMA units (128 x 256 x 64) issued by each CTA
     int cm, cn;        // cluster shape: cm row tiles share B'^T slices, cn column tiles share X' slices
     int ntmg, ntng;    // tile groups (one cluster each) along rows and columns
+    const int* order;  // launch order of tile groups (linear index tig * ntng + tjg), heaviest first
     double alpha;
     const int* eA;
     const int* eB;
@@ -205,6 +206,15 @@ struct ConvArgs {      // residual reduction and stop decision (zt_plan.cu)
     int n;
     zt_dev_state* st;
 };
+
+// Plan set-up work goes to a private non-blocking stream of the greatest
+// priority, so that it is scheduled ahead of long-running work other threads
+// keep on the device.
+inline cudaError_t zt_setup_stream(cudaStream_t* s) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, greatest);
+}
 
 // ---- error handling ---------------------------------------------------------
 int zt_fail(int code, const char* fmt, ...);

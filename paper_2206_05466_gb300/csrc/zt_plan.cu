@@ -502,7 +502,7 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     rc = zt_solve_create(p);
     if (rc != ZT_OK) return fail(rc);
     cudaStream_t cs = nullptr;
-    ZT_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    ZT_TRY(zt_setup_stream(&cs));
     cudaMemsetAsync(p->state, 0, sizeof(zt_dev_state), cs);
     cudaMemsetAsync(p->d_units, 0, sizeof(unsigned long long), cs);
     factor_kernel<<<(N + 127) / 128, 128, 0, cs>>>(N, p->lap_a, p->lap_b, p->fac_l, p->fac_nd);

@@ -41,6 +41,8 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <algorithm>
+#include <vector>
 
 #include "zt_internal.h"
 
@@ -74,6 +76,9 @@ struct zt_split_ws {
     int* eA = nullptr;                           // [Mpad]
     int* eB[2] = {nullptr, nullptr};             // [Npad]
     int nkb = 0, ngA = 0, ngB = 0;               // K blocks; row groups of X'; column groups of B'^T
+    int* order_full = nullptr;                   // tile-group launch orders (device), near-diagonal first
+    int* order_lower = nullptr;
+    int n_full = 0, n_lower = 0;
     int skip_zero = 1;                           // skip digit-pair units whose tiles are all zero
     int* occA = nullptr;                         // [ngA][nkb]
     int* occB[2] = {nullptr, nullptr};           // [ngB][nkb]
@@ -392,7 +397,11 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
     const int rank = cs > 1 ? (int)cluster_ctarank() : 0;
     const int grp = bid / cs;
     int tig, tjg;
-    if (a.lower_only && a.cm == a.cn) {   // groups on or below the diagonal, triangular order
+    if (a.order) {   // explicit order (only groups that have work are listed)
+        const int gl = a.order[grp];
+        tig = gl / a.ntng;
+        tjg = gl % a.ntng;
+    } else if (a.lower_only && a.cm == a.cn) {   // groups on or below the diagonal, triangular order
         int r = (int)((sqrtf(8.0f * grp + 1.0f) - 1.0f) * 0.5f);
         while (r * (r + 1) / 2 > grp) --r;
         while ((r + 1) * (r + 2) / 2 <= grp) ++r;
@@ -723,7 +732,7 @@ int zt_split_create(zt_plan* p) {
         w->u = u;
     }
     cudaStream_t cs = nullptr;   // set-up on a private stream (no wait on other threads' work)
-    ZT_CU(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    ZT_CU(zt_setup_stream(&cs));
     struct StreamGuard {
         cudaStream_t s;
         ~StreamGuard() {
@@ -756,6 +765,33 @@ int zt_split_create(zt_plan* p) {
         ZT_CU(cudaMemsetAsync(w->eB[b], 0, (size_t)w->Npad * sizeof(int), cs));
         if ((rc = make_map(&w->tmB[b], w->dB[b], s * w->Npad, w->ldk, BN / cm))) return rc;
     }
+    // Launch orders: with all-zero digit tiles skipped, tiles near the diagonal
+    // (where the leading digits of both operands are nonzero) carry most of
+    // the work, so they are dispatched first and the light far tiles fill the
+    // tail (longest-first ordering).
+    {
+        const int ntmg = w->Mpad / (BM * cm), ntng = w->Npad / (BN * cn);
+        std::vector<std::pair<double, int>> full, lower;
+        for (int tg = 0; tg < ntmg; ++tg)
+            for (int ug = 0; ug < ntng; ++ug) {
+                const double rc = tg * cm + 0.5 * (cm - 1), cc = ug * cn + 0.5 * (cn - 1);
+                const double dist = std::fabs(rc - cc);
+                full.push_back({dist, tg * ntng + ug});
+                if (ug * cn < (tg + 1) * cm) lower.push_back({dist, tg * ntng + ug});
+            }
+        std::stable_sort(full.begin(), full.end(), [](auto& x, auto& y) { return x.first < y.first; });
+        std::stable_sort(lower.begin(), lower.end(), [](auto& x, auto& y) { return x.first < y.first; });
+        std::vector<int> of, ol;
+        for (auto& e : full) of.push_back(e.second);
+        for (auto& e : lower) ol.push_back(e.second);
+        w->n_full = (int)of.size();
+        w->n_lower = (int)ol.size();
+        ZT_CU(cudaMalloc(&w->order_full, of.size() * sizeof(int)));
+        ZT_CU(cudaMalloc(&w->order_lower, ol.size() * sizeof(int)));
+        ZT_CU(cudaMemcpyAsync(w->order_full, of.data(), of.size() * sizeof(int), cudaMemcpyHostToDevice, cs));
+        ZT_CU(cudaMemcpyAsync(w->order_lower, ol.data(), ol.size() * sizeof(int), cudaMemcpyHostToDevice, cs));
+        ZT_CU(cudaStreamSynchronize(cs));   // host vectors go out of scope
+    }
     ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     ZT_CU(cudaFuncSetAttribute(zgemm_split_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     return ZT_OK;
@@ -776,6 +812,8 @@ void zt_split_destroy(zt_plan* p) {
     cudaFree(w->dA);
     cudaFree(w->eA);
     cudaFree(w->occA);
+    cudaFree(w->order_full);
+    cudaFree(w->order_lower);
     for (int b = 0; b < 2; ++b) {
         cudaFree(w->dB[b]);
         cudaFree(w->eB[b]);
@@ -869,19 +907,10 @@ static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int l
     a.st = p->state;
     a.gate = ZT_GATE_NONE;
     const int cs = w->cm * w->cn;
-    int ngroups, ntiles;
-    if (lower_only && w->cm == w->cn) {
-        ngroups = a.ntmg * (a.ntmg + 1) / 2;
-        ntiles = ngroups * cs;
-    } else {
-        ngroups = a.ntmg * a.ntng;
-        ntiles = 0;   // tiles of groups that touch the lower triangle (or all)
-        for (int tg = 0; tg < a.ntmg; ++tg)
-            for (int ug = 0; ug < a.ntng; ++ug)
-                if (!lower_only || ug * w->cn < (tg + 1) * w->cm) ntiles += cs;
-    }
+    a.order = lower_only ? w->order_lower : w->order_full;   // only groups with work, heaviest first
+    const int ngroups = lower_only ? w->n_lower : w->n_full;
     *ngroups_out = ngroups;
-    *ntiles_out = ntiles;
+    *ntiles_out = ngroups * cs;
 }
 
 int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, GemmEntry* out,
@@ -1101,6 +1130,7 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
     a.occA = nullptr;   // no zero-unit skipping: every digit pair is multiplied
     a.occB = nullptr;
     a.units = nullptr;
+    a.order = nullptr;
     a.alpha = -1.0;
     a.eA = eA;
     a.eB = eB;

@@ -64,7 +64,15 @@ class Server:
         import torch
 
         dev = torch.cuda.current_device()
-        upload = torch.cuda.Stream()   # admissions copy state here, never waiting on running steps
+        low, high = torch.cuda.Stream.priority_range()   # e.g. (0, -5): lower number = higher priority
+        # admissions copy state on the highest-priority stream, never waiting on running steps
+        upload = torch.cuda.Stream(priority=high)
+        sizes = sorted({j.N for j in jobs})
+
+        def class_priority(N):   # smaller matrices are the latency-sensitive classes
+            rank = sizes.index(N)
+            span = max(1, len(sizes) - 1)
+            return int(round(high + (low - high) * rank / span))
         lock = threading.Lock()
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
         queue = collections.deque()
@@ -78,7 +86,7 @@ class Server:
 
         def worker(cls):
             torch.cuda.set_device(dev)
-            stream = torch.cuda.Stream()
+            stream = torch.cuda.Stream(priority=class_priority(cls[0]))
             batch, order = None, []
             try:
                 while True:
