@@ -216,6 +216,12 @@ inline cudaError_t zt_setup_stream(cudaStream_t* s) {
     return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, greatest);
 }
 
+// Kernel attributes (dynamic shared-memory limits) are set once per device
+// and process: setting them again while other threads run the kernels is
+// unnecessary and can stall.  `bit` names the kernel family.
+enum zt_attr_bit : unsigned { ZT_ATTR_SOLVE = 1u, ZT_ATTR_SPLIT = 2u };
+bool zt_attr_needed(unsigned bit);   // true once per (device, bit); marks it set
+
 // ---- error handling ---------------------------------------------------------
 int zt_fail(int code, const char* fmt, ...);
 int zt_cuda_check(cudaError_t e, const char* what);

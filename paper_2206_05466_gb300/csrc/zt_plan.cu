@@ -30,6 +30,20 @@ int zt_cuda_check(cudaError_t e, const char* what) {
 
 extern "C" const char* zt_last_error(void) { return g_err; }
 
+#include <mutex>
+static std::mutex g_attr_mu;
+static unsigned g_attr_done[64];
+
+bool zt_attr_needed(unsigned bit) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return true;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (g_attr_done[dev] & bit) return false;
+    g_attr_done[dev] |= bit;
+    return true;
+}
+
 static int launch_check(zt_plan* p, const char* what) {
     p->launches++;
     cudaError_t e = cudaGetLastError();

@@ -244,6 +244,7 @@ int zt_solve_create(zt_plan* p) {
     ZT_CU(cudaMalloc(&p->seg_h, ns * sizeof(double)));
     ZT_CU(cudaMalloc(&p->sum_x, (size_t)p->nseg * sizeof(double2)));
     ZT_CU(cudaMalloc(&p->sum_h, (size_t)p->nseg * sizeof(double)));
+    if (!zt_attr_needed(ZT_ATTR_SOLVE)) return ZT_OK;
     ZT_CU(cudaFuncSetAttribute(solve_tile_kernel<F1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
     ZT_CU(cudaFuncSetAttribute(solve_tile_kernel<B1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
     ZT_CU(cudaFuncSetAttribute(solve_tile_kernel<B3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));

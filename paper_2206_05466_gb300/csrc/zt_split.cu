@@ -792,8 +792,11 @@ int zt_split_create(zt_plan* p) {
         ZT_CU(cudaMemcpyAsync(w->order_lower, ol.data(), ol.size() * sizeof(int), cudaMemcpyHostToDevice, cs));
         ZT_CU(cudaStreamSynchronize(cs));   // host vectors go out of scope
     }
-    ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    ZT_CU(cudaFuncSetAttribute(zgemm_split_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    if (zt_attr_needed(ZT_ATTR_SPLIT)) {
+        ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        ZT_CU(cudaFuncSetAttribute(zgemm_split_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)SMEM_BYTES));
+    }
     return ZT_OK;
 }
 

@@ -81,6 +81,7 @@ class Server:
         workers: dict[tuple, threading.Thread] = {}
         lat: dict[tuple, list] = collections.defaultdict(list)
         qdelay, results, errors, admit_times = [], {}, [], []
+        pinned = {}
         st = {"used": 0, "peak": 0, "steps": 0, "completed": 0, "batched": 0, "stop": False}
         t0 = clock()
 
@@ -172,8 +173,12 @@ class Server:
                 ta = clock()
                 plan = z.Plan(job.N, job.precision)
                 tb = clock()
+                src = pinned.get(id(job.W0))   # initial states shared by jobs are pinned once
+                if src is None:
+                    src = torch.from_numpy(np.ascontiguousarray(job.W0)).pin_memory()
+                    pinned[id(job.W0)] = src
                 with torch.cuda.stream(upload):
-                    W = torch.from_numpy(np.ascontiguousarray(job.W0)).cuda(non_blocking=False)
+                    W = src.to("cuda", non_blocking=True)
                 upload.synchronize()
                 admit_times.append((tb - ta, clock() - tb))
                 t_adm = clock() - t0
