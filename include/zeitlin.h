@@ -59,6 +59,7 @@ typedef struct zt_tuning {
     int cluster_n;       /* SPLIT: CTAs sharing each X' tile by TMA multicast (1, 2, 4; def. 1) */
     int dense;           /* SPLIT: 1 = multiply every digit pair; 0 (default) = skip digit-pair
                             tiles that are exactly zero (identical results)                  */
+    int tile_order;      /* SPLIT: 0 (default) = tiles near the diagonal first, 1 = row-major */
 } zt_tuning;
 
 typedef struct zt_step_stats {

@@ -4,8 +4,8 @@ For a matrix size N it times each candidate tuning on seeded probe operands
 (the first product of an IsoMP sweep: X = Delta_N^{-1} W0, Y = W0, W0 from the
 seeded su(N) recipe) through the C ABI, measures
 the candidate's error against a reference product with more digits (8 slices
-of 7 bits, ~2^-55 relative), and keeps the fastest candidate whose relative
-Frobenius error is within `target`.  Choices are cached as JSON keyed by
+of 7 bits, ~2^-55 relative), times whole IsoMP steps of the workload for the
+candidates within `target` (relative Frobenius error), and keeps the fastest.  Choices are cached as JSON keyed by
 (N, GPU name) in $ZEITLIN_TUNE_CACHE (default ~/.cache/zeitlin_gb300/tune.json).
 All arithmetic runs in the library's kernels; this module only orchestrates.
 """
@@ -15,13 +15,8 @@ import json
 import os
 
 DEFAULT_CANDIDATES = [
-    dict(slices=7, digit_bits=7, exact_groups=4, cluster_m=2, cluster_n=1),
-    dict(slices=7, digit_bits=7, exact_groups=4, cluster_m=4, cluster_n=1),
-    dict(slices=6, digit_bits=7, exact_groups=4, cluster_m=2, cluster_n=1),
-    dict(slices=6, digit_bits=7, exact_groups=4, cluster_m=4, cluster_n=1),
-    dict(slices=6, digit_bits=7, exact_groups=3, cluster_m=2, cluster_n=1),
-    dict(slices=7, digit_bits=7, exact_groups=3, cluster_m=2, cluster_n=1),
-    dict(slices=7, digit_bits=7, exact_groups=4, cluster_m=1, cluster_n=1),
+    dict(slices=s, digit_bits=7, exact_groups=eg, cluster_m=cm, cluster_n=1, tile_order=to)
+    for s in (7, 6) for eg in (4, 3) for cm in (2, 4, 1) for to in (0, 1)
 ]
 REFERENCE = dict(slices=8, digit_bits=7, exact_groups=8, cluster_m=2, cluster_n=1)
 
@@ -44,7 +39,8 @@ def load_cached(N):
         return None
 
 
-def autotune(N: int, target: float = 1e-11, candidates=None, reps: int = 2, use_cache: bool = True) -> dict:
+def autotune(N: int, target: float = 1e-11, candidates=None, reps: int = 2, use_cache: bool = True,
+             step_h: float = 0.005) -> dict:
     """Return {"tuning": {...}, "rel_err": e, "ms": t, "trials": [...]} for size N."""
     import numpy as np
     import torch
@@ -84,13 +80,21 @@ def autotune(N: int, target: float = 1e-11, candidates=None, reps: int = 2, use_
         z.zt_zgemm_skew(plan, X, Y, C)
         torch.cuda.synchronize()
         err = float(np.linalg.norm(C.cpu().numpy() - ref_h)) / nref
-        plan.set_timing(True)
-        for _ in range(reps):
-            z.zt_zgemm_skew(plan, X, Y, C)
+        if err > target:   # too coarse: not worth timing
+            trials.append({"tuning": tun, "rel_err": err})
+            plan.close()
+            continue
+        # speed: whole IsoMP steps of the workload (8 products of changing sparsity)
+        W = Y.clone()
+        z.isomp_step(plan, W, step_h)
         torch.cuda.synchronize()
-        kp = plan.kernel_time(z.KERNEL_PRODUCT)
-        ks = plan.kernel_time(z.KERNEL_SPLIT)
-        ms = (kp["total_ms"] + ks["total_ms"]) / reps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            z.isomp_step(plan, W, step_h)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
         trials.append({"tuning": tun, "rel_err": err, "ms": ms})
         plan.close()
     ok = [t for t in trials if "rel_err" in t and t["rel_err"] <= target]

@@ -133,14 +133,14 @@ extern "C" int zt_plan_kernel_time(zt_plan* p, int kind, long* launches, double*
 }
 
 // ---------------------------------------------------------------------------
-// Constant per-diagonal data (Sec. 3.2, Eq. delta_tria) and LDL^T factors.
-// One thread per diagonal m; entries go to packed lower-triangular arrays at
-// (r, c) = (i + m, i).  For m = 0 only the leading N-1 equations are factored
-// (the l = 0 mode is projected out); the dropped row gets l = 0, -1/d = 0.
+// Constant per-diagonal data (Sec. 3.2, Eq. delta_tria) and LDL^T factors,
+// computed once per plan on the host (the recurrence is sequential along each
+// diagonal; on the device it would compete for the FP64 pipe with running
+// work).  Entries go to packed lower-triangular arrays at (r, c) = (i + m, i).
+// For m = 0 only the leading N-1 equations are factored (the l = 0 mode is
+// projected out); the dropped row gets l = 0, -1/d = 0.
 // ---------------------------------------------------------------------------
-__global__ void factor_kernel(int N, double* lap_a, double* lap_b, double* fac_l, double* fac_nd) {
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= N) return;
+static void factor_diagonal(int N, int m, double* lap_a, double* lap_b, double* fac_l, double* fac_nd) {
     const int n = N - m;
     const int ns = (m == 0) ? N - 1 : n;   // size of the factored system
     const double s = (N - 1) / 2.0;
@@ -168,6 +168,21 @@ __global__ void factor_kernel(int N, double* lap_a, double* lap_b, double* fac_l
         fac_nd[at] = nd;
         bprev = b;
     }
+}
+
+#include <thread>
+#include <vector>
+
+static void factor_host(int N, double* lap_a, double* lap_b, double* fac_l, double* fac_nd) {
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = nt == 0 ? 1 : (nt > 16 ? 16 : nt);
+    if ((long long)N * N < 1 << 20) nt = 1;
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([=] {
+            for (int m = (int)t; m < N; m += (int)nt) factor_diagonal(N, m, lap_a, lap_b, fac_l, fac_nd);
+        });
+    for (auto& x : th) x.join();
 }
 
 // ---------------------------------------------------------------------------
@@ -519,12 +534,27 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     ZT_TRY(zt_setup_stream(&cs));
     cudaMemsetAsync(p->state, 0, sizeof(zt_dev_state), cs);
     cudaMemsetAsync(p->d_units, 0, sizeof(unsigned long long), cs);
-    factor_kernel<<<(N + 127) / 128, 128, 0, cs>>>(N, p->lap_a, p->lap_b, p->fac_l, p->fac_nd);
-    p->launches++;
-    cudaError_t se = cudaGetLastError();
-    if (se == cudaSuccess) se = cudaStreamSynchronize(cs);
-    cudaStreamDestroy(cs);
-    if (se != cudaSuccess) return fail(zt_cuda_check(se, "plan set-up (factor_kernel)"));
+    {
+        std::vector<double> ha, hb, hl, hn;
+        try {
+            ha.resize(ntri);
+            hb.resize(ntri);
+            hl.resize(ntri);
+            hn.resize(ntri);
+        } catch (...) {
+            cudaStreamDestroy(cs);
+            return fail(zt_fail(ZT_ENOMEM, "host allocation for the Laplacian factors failed"));
+        }
+        factor_host(N, ha.data(), hb.data(), hl.data(), hn.data());
+        cudaMemcpyAsync(p->lap_a, ha.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
+        cudaMemcpyAsync(p->lap_b, hb.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
+        cudaMemcpyAsync(p->fac_l, hl.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
+        cudaMemcpyAsync(p->fac_nd, hn.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
+        cudaError_t se = cudaGetLastError();
+        if (se == cudaSuccess) se = cudaStreamSynchronize(cs);   // host vectors go out of scope
+        cudaStreamDestroy(cs);
+        if (se != cudaSuccess) return fail(zt_cuda_check(se, "plan set-up (factor upload)"));
+    }
     if (precision == ZT_PRECISION_SPLIT) {
         rc = zt_split_create(p);
         if (rc != ZT_OK) return fail(rc);

@@ -779,8 +779,10 @@ int zt_split_create(zt_plan* p) {
                 full.push_back({dist, tg * ntng + ug});
                 if (ug * cn < (tg + 1) * cm) lower.push_back({dist, tg * ntng + ug});
             }
-        std::stable_sort(full.begin(), full.end(), [](auto& x, auto& y) { return x.first < y.first; });
-        std::stable_sort(lower.begin(), lower.end(), [](auto& x, auto& y) { return x.first < y.first; });
+        if (p->tun.tile_order == 0) {   // row-major otherwise (the enumeration order above)
+            std::stable_sort(full.begin(), full.end(), [](auto& x, auto& y) { return x.first < y.first; });
+            std::stable_sort(lower.begin(), lower.end(), [](auto& x, auto& y) { return x.first < y.first; });
+        }
         std::vector<int> of, ol;
         for (auto& e : full) of.push_back(e.second);
         for (auto& e : lower) ol.push_back(e.second);
