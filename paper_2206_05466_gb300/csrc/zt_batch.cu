@@ -78,6 +78,7 @@ struct zt_batch {
     std::vector<double2*> W;
     std::vector<double> h;
     unsigned char* dbuf = nullptr;   // all tables
+    cudaStream_t mstream = nullptr;  // private stream of the stream-ordered allocations (no device syncs)
     zt_dev_state** dstates = nullptr;
     zt_dev_state* gathered = nullptr;
     zt_dev_state* hstates = nullptr;   // host copy of the states (pageable)
@@ -126,8 +127,9 @@ struct Builder {
     }
     int upload(zt_batch* b) {
         if (bytes.empty()) return ZT_OK;
-        ZT_CU(cudaMalloc(&b->dbuf, bytes.size()));
-        ZT_CU(cudaMemcpy(b->dbuf, bytes.data(), bytes.size(), cudaMemcpyHostToDevice));
+        ZT_CU(ZT_DMALLOC(b->dbuf, bytes.size(), b->mstream));
+        ZT_CU(cudaMemcpyAsync(b->dbuf, bytes.data(), bytes.size(), cudaMemcpyHostToDevice, b->mstream));
+        ZT_CU(cudaStreamSynchronize(b->mstream));   // host staging goes out of scope
         for (auto& q : pend) {
             q.op->tab = b->dbuf + q.tab_off;
             q.op->offs = reinterpret_cast<int*>(b->dbuf + q.offs_off);
@@ -270,9 +272,12 @@ extern "C" void zt_batch_destroy(zt_batch* b) {
     drop_graphs(b);
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->own) cudaStreamDestroy(b->own);
-    cudaFree(b->dbuf);
-    cudaFree(b->dstates);
-    cudaFree(b->gathered);
+    if (b->mstream) {   // every step ended with a host synchronisation: nothing of the batch is in flight
+        zt_dfree(b->dbuf, b->mstream);
+        zt_dfree(b->dstates, b->mstream);
+        zt_dfree(b->gathered, b->mstream);
+        cudaStreamDestroy(b->mstream);
+    }
     delete[] b->hstates;
     if (b->hpinned) cudaFreeHost(b->hpinned);
     delete b;
@@ -290,6 +295,10 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
         return rc;
     };
     b->n = count;
+    {
+        cudaError_t e0 = zt_setup_stream(&b->mstream);
+        if (e0 != cudaSuccess) return fail(zt_cuda_check(e0, "stream create"));
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     b->device = dev;
@@ -409,13 +418,14 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
     std::vector<zt_dev_state*> sts(count);
     for (int i = 0; i < count; ++i) sts[i] = plans[i]->state;
     cudaError_t e;
-    if ((e = cudaMalloc(&b->dstates, count * sizeof(zt_dev_state*))) != cudaSuccess)
-        return fail(zt_cuda_check(e, "cudaMalloc"));
-    if ((e = cudaMemcpy(b->dstates, sts.data(), count * sizeof(zt_dev_state*), cudaMemcpyHostToDevice)) !=
-        cudaSuccess)
-        return fail(zt_cuda_check(e, "cudaMemcpy"));
-    if ((e = cudaMalloc(&b->gathered, count * sizeof(zt_dev_state))) != cudaSuccess)
-        return fail(zt_cuda_check(e, "cudaMalloc"));
+    if ((e = ZT_DMALLOC(b->dstates, count * sizeof(zt_dev_state*), b->mstream)) != cudaSuccess)
+        return fail(zt_cuda_check(e, "cudaMallocAsync"));
+    if ((e = cudaMemcpyAsync(b->dstates, sts.data(), count * sizeof(zt_dev_state*), cudaMemcpyHostToDevice,
+                             b->mstream)) != cudaSuccess)
+        return fail(zt_cuda_check(e, "cudaMemcpyAsync"));
+    if ((e = ZT_DMALLOC(b->gathered, count * sizeof(zt_dev_state), b->mstream)) != cudaSuccess)
+        return fail(zt_cuda_check(e, "cudaMallocAsync"));
+    if ((e = cudaStreamSynchronize(b->mstream)) != cudaSuccess) return fail(zt_cuda_check(e, "set-up"));
     b->hstates = new (std::nothrow) zt_dev_state[count];   // pinned copy only for graph mode
     if (!b->hstates) return fail(zt_fail(ZT_ENOMEM, "host allocation failed"));
     *out = b;

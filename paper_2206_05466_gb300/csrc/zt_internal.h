@@ -101,6 +101,12 @@ struct zt_plan {
     zt_dev_state* h_state = nullptr;   // pinned host mirror
     zt_split_ws* split = nullptr;
     long launches = 0;
+    // Device memory of the plan comes from the stream-ordered allocator on a
+    // private stream: creating or freeing a plan never synchronises the
+    // device (other threads may keep long-running work on it).  Frees are
+    // ordered after `last_use`, recorded after every launch sequence.
+    cudaStream_t mstream = nullptr;
+    cudaEvent_t last_use = nullptr;
     // measurement hook
     int timing = 0;
     unsigned long long* d_units = nullptr;   // MMA units (128 x 256 x 64) issued by split products
@@ -221,6 +227,16 @@ inline cudaError_t zt_setup_stream(cudaStream_t* s) {
 // unnecessary and can stall.  `bit` names the kernel family.
 enum zt_attr_bit : unsigned { ZT_ATTR_SOLVE = 1u, ZT_ATTR_SPLIT = 2u };
 bool zt_attr_needed(unsigned bit);   // true once per (device, bit); marks it set
+
+// Stream-ordered device allocation on the plan's private stream.
+#define ZT_DMALLOC(ptr, bytes, stream) cudaMallocAsync((void**)&(ptr), (bytes), (stream))
+inline void zt_dfree(void* ptr, cudaStream_t s) {
+    if (ptr) cudaFreeAsync(ptr, s);
+}
+// Remember the last work enqueued on the plan (frees wait for it).
+inline void zt_note_use(zt_plan* p, cudaStream_t s) {
+    if (p && p->last_use) cudaEventRecord(p->last_use, s);
+}
 
 // ---- error handling ---------------------------------------------------------
 int zt_fail(int code, const char* fmt, ...);

@@ -432,27 +432,35 @@ static int zgemm(zt_plan* p, const double2* X, const double2* Y, double2* C, dou
 
 extern "C" void zt_plan_destroy(zt_plan* p) {
     if (!p) return;
-    cudaDeviceSynchronize();
+    cudaStream_t ms = p->mstream;
+    if (!ms) {   // creation failed before the private stream existed: nothing was allocated
+        delete p->h_state;
+        delete p;
+        return;
+    }
+    if (p->last_use) cudaStreamWaitEvent(ms, p->last_use, 0);   // frees after the plan's last work
     if (p->split) zt_split_destroy(p);
     zt_solve_destroy(p);
-    cudaFree(p->lap_a);
-    cudaFree(p->lap_b);
-    cudaFree(p->fac_l);
-    cudaFree(p->fac_nd);
-    cudaFree(p->Wn);
-    cudaFree(p->Wt);
-    cudaFree(p->P);
-    cudaFree(p->A);
-    cudaFree(p->B);
-    cudaFree(p->partials);
-    cudaFree(p->state);
-    cudaFree(p->d_units);
+    zt_dfree(p->lap_a, ms);
+    zt_dfree(p->lap_b, ms);
+    zt_dfree(p->fac_l, ms);
+    zt_dfree(p->fac_nd, ms);
+    zt_dfree(p->Wn, ms);
+    zt_dfree(p->Wt, ms);
+    zt_dfree(p->P, ms);
+    zt_dfree(p->A, ms);
+    zt_dfree(p->B, ms);
+    zt_dfree(p->partials, ms);
+    zt_dfree(p->state, ms);
+    zt_dfree(p->d_units, ms);
     delete p->h_state;
     for (int i = 0; i < p->caprecs; ++i) {
         if (p->recs[i].a) cudaEventDestroy(p->recs[i].a);
         if (p->recs[i].b) cudaEventDestroy(p->recs[i].b);
     }
     delete[] p->recs;
+    if (p->last_use) cudaEventDestroy(p->last_use);
+    cudaStreamDestroy(ms);   // returns at once; the frees complete in stream order
     delete p;
 }
 
@@ -508,30 +516,31 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         if (_e != cudaSuccess) return fail(zt_cuda_check(_e, #call)); \
     } while (0)
     ZT_TRY(cudaGetDevice(&p->device));
+    ZT_TRY(zt_setup_stream(&p->mstream));
+    ZT_TRY(cudaEventCreateWithFlags(&p->last_use, cudaEventDisableTiming));
+    cudaStream_t cs = p->mstream;
     const size_t ntri = (size_t)N * (N + 1) / 2;
     const size_t mat = (size_t)N * N * sizeof(double2);
-    ZT_TRY(cudaMalloc(&p->lap_a, ntri * sizeof(double)));
-    ZT_TRY(cudaMalloc(&p->lap_b, ntri * sizeof(double)));
-    ZT_TRY(cudaMalloc(&p->fac_l, ntri * sizeof(double)));
-    ZT_TRY(cudaMalloc(&p->fac_nd, ntri * sizeof(double)));
-    ZT_TRY(cudaMalloc(&p->Wn, mat));
-    ZT_TRY(cudaMalloc(&p->Wt, mat));
-    ZT_TRY(cudaMalloc(&p->P, mat));
-    ZT_TRY(cudaMalloc(&p->A, mat));
-    ZT_TRY(cudaMalloc(&p->B, mat));
+    ZT_TRY(ZT_DMALLOC(p->lap_a, ntri * sizeof(double), cs));
+    ZT_TRY(ZT_DMALLOC(p->lap_b, ntri * sizeof(double), cs));
+    ZT_TRY(ZT_DMALLOC(p->fac_l, ntri * sizeof(double), cs));
+    ZT_TRY(ZT_DMALLOC(p->fac_nd, ntri * sizeof(double), cs));
+    ZT_TRY(ZT_DMALLOC(p->Wn, mat, cs));
+    ZT_TRY(ZT_DMALLOC(p->Wt, mat, cs));
+    ZT_TRY(ZT_DMALLOC(p->P, mat, cs));
+    ZT_TRY(ZT_DMALLOC(p->A, mat, cs));
+    ZT_TRY(ZT_DMALLOC(p->B, mat, cs));
     const int nt = (N + UT - 1) / UT;
     p->npartials = nt * (nt + 1) / 2;
-    ZT_TRY(cudaMalloc(&p->partials, (size_t)p->npartials * sizeof(double)));
-    ZT_TRY(cudaMalloc(&p->state, sizeof(zt_dev_state)));
-    ZT_TRY(cudaMalloc(&p->d_units, sizeof(unsigned long long)));
+    ZT_TRY(ZT_DMALLOC(p->partials, (size_t)p->npartials * sizeof(double), cs));
+    ZT_TRY(ZT_DMALLOC(p->state, sizeof(zt_dev_state), cs));
+    ZT_TRY(ZT_DMALLOC(p->d_units, sizeof(unsigned long long), cs));
     p->h_state = new (std::nothrow) zt_dev_state();   // pageable: pinning per plan is slow
     if (!p->h_state) return fail(zt_fail(ZT_ENOMEM, "host allocation failed"));
     // set-up work runs on a private stream so that creating a plan does not
     // wait for work other threads have queued on the device
     rc = zt_solve_create(p);
     if (rc != ZT_OK) return fail(rc);
-    cudaStream_t cs = nullptr;
-    ZT_TRY(zt_setup_stream(&cs));
     cudaMemsetAsync(p->state, 0, sizeof(zt_dev_state), cs);
     cudaMemsetAsync(p->d_units, 0, sizeof(unsigned long long), cs);
     {
@@ -542,7 +551,6 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
             hl.resize(ntri);
             hn.resize(ntri);
         } catch (...) {
-            cudaStreamDestroy(cs);
             return fail(zt_fail(ZT_ENOMEM, "host allocation for the Laplacian factors failed"));
         }
         factor_host(N, ha.data(), hb.data(), hl.data(), hn.data());
@@ -552,13 +560,13 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         cudaMemcpyAsync(p->fac_nd, hn.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
         cudaError_t se = cudaGetLastError();
         if (se == cudaSuccess) se = cudaStreamSynchronize(cs);   // host vectors go out of scope
-        cudaStreamDestroy(cs);
         if (se != cudaSuccess) return fail(zt_cuda_check(se, "plan set-up (factor upload)"));
     }
     if (precision == ZT_PRECISION_SPLIT) {
         rc = zt_split_create(p);
         if (rc != ZT_OK) return fail(rc);
     }
+    ZT_TRY(cudaStreamSynchronize(cs));   // allocations and set-up visible to every stream
 #undef ZT_TRY
     *out = p;
     return ZT_OK;
@@ -580,7 +588,9 @@ extern "C" int zeitlin_laplacian_apply(zt_plan* p, const double* P, double* W, v
     int rc;
     if ((rc = check_ptr(P, "P")) || (rc = check_ptr(W, "W"))) return rc;
     if (P == W) return zt_fail(ZT_EINVAL, "W must not alias P");
-    return zt_launch_laplacian(p, (const double2*)P, (double2*)W, (cudaStream_t)stream);
+    rc = zt_launch_laplacian(p, (const double2*)P, (double2*)W, (cudaStream_t)stream);
+    zt_note_use(p, (cudaStream_t)stream);
+    return rc;
 }
 
 extern "C" int zeitlin_stream_solve(zt_plan* p, const double* W, double* P, void* stream) {
@@ -588,7 +598,9 @@ extern "C" int zeitlin_stream_solve(zt_plan* p, const double* W, double* P, void
     int rc;
     if ((rc = check_ptr(P, "P")) || (rc = check_ptr(W, "W"))) return rc;
     if (P == W) return zt_fail(ZT_EINVAL, "P must not alias W");
-    return zt_launch_stream_solve(p, (const double2*)W, (double2*)P, (cudaStream_t)stream, ZT_GATE_NONE);
+    rc = zt_launch_stream_solve(p, (const double2*)W, (double2*)P, (cudaStream_t)stream, ZT_GATE_NONE);
+    zt_note_use(p, (cudaStream_t)stream);
+    return rc;
 }
 
 extern "C" int zt_zgemm_skew(zt_plan* p, const double* X, const double* Y, double* C, void* stream) {
@@ -606,7 +618,9 @@ extern "C" int zt_zgemm_skew(zt_plan* p, const double* X, const double* Y, doubl
         if (p->h_state->timeout) return zt_fail(ZT_ETIMEOUT, "zt_zgemm_skew: bounded device wait ran out");
         return ZT_OK;
     }
-    return zgemm(p, (const double2*)X, (const double2*)Y, (double2*)C, -1.0, 0, s, ZT_GATE_NONE);
+    rc = zgemm(p, (const double2*)X, (const double2*)Y, (double2*)C, -1.0, 0, s, ZT_GATE_NONE);
+    zt_note_use(p, s);
+    return rc;
 }
 
 // One fixed-point sweep (Eq. isomp_iter): Pt = solve(Wt), A = Pt Wt,
@@ -649,8 +663,16 @@ static int enqueue_final(zt_plan* p, int tag, double2* W, double h, cudaStream_t
     return launch_check(p, "finalize_mark_kernel");
 }
 
+static int step_impl_(zt_plan* p, double2* W, double h, double tol, int maxit, zt_step_stats* stats,
+                      cudaStream_t s);
 static int step_impl(zt_plan* p, double2* W, double h, double tol, int maxit, zt_step_stats* stats,
                      cudaStream_t s) {
+    const int rc = step_impl_(p, W, h, tol, maxit, stats, s);
+    zt_note_use(p, s);
+    return rc;
+}
+static int step_impl_(zt_plan* p, double2* W, double h, double tol, int maxit, zt_step_stats* stats,
+                      cudaStream_t s) {
     const size_t mat = (size_t)p->N * p->N * sizeof(double2);
     ZT_CU(cudaMemcpyAsync(p->Wn, W, mat, cudaMemcpyDeviceToDevice, s));
     ZT_CU(cudaMemcpyAsync(p->Wt, W, mat, cudaMemcpyDeviceToDevice, s));

@@ -238,12 +238,12 @@ int zt_solve_create(zt_plan* p) {
     const int N = p->N;
     p->nseg = (N + SL - 1) / SL;
     const size_t ns = (size_t)N * p->nseg;
-    ZT_CU(cudaMalloc(&p->seg_z, ns * sizeof(double2)));
-    ZT_CU(cudaMalloc(&p->seg_g, ns * sizeof(double)));
-    ZT_CU(cudaMalloc(&p->seg_x, ns * sizeof(double2)));
-    ZT_CU(cudaMalloc(&p->seg_h, ns * sizeof(double)));
-    ZT_CU(cudaMalloc(&p->sum_x, (size_t)p->nseg * sizeof(double2)));
-    ZT_CU(cudaMalloc(&p->sum_h, (size_t)p->nseg * sizeof(double)));
+    ZT_CU(ZT_DMALLOC(p->seg_z, ns * sizeof(double2), p->mstream));
+    ZT_CU(ZT_DMALLOC(p->seg_g, ns * sizeof(double), p->mstream));
+    ZT_CU(ZT_DMALLOC(p->seg_x, ns * sizeof(double2), p->mstream));
+    ZT_CU(ZT_DMALLOC(p->seg_h, ns * sizeof(double), p->mstream));
+    ZT_CU(ZT_DMALLOC(p->sum_x, (size_t)p->nseg * sizeof(double2), p->mstream));
+    ZT_CU(ZT_DMALLOC(p->sum_h, (size_t)p->nseg * sizeof(double), p->mstream));
     if (!zt_attr_needed(ZT_ATTR_SOLVE)) return ZT_OK;
     ZT_CU(cudaFuncSetAttribute(solve_tile_kernel<F1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
     ZT_CU(cudaFuncSetAttribute(solve_tile_kernel<B1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TILE_SMEM));
@@ -255,12 +255,12 @@ int zt_solve_create(zt_plan* p) {
 }
 
 void zt_solve_destroy(zt_plan* p) {
-    cudaFree(p->seg_z);
-    cudaFree(p->seg_g);
-    cudaFree(p->seg_x);
-    cudaFree(p->seg_h);
-    cudaFree(p->sum_x);
-    cudaFree(p->sum_h);
+    zt_dfree(p->seg_z, p->mstream);
+    zt_dfree(p->seg_g, p->mstream);
+    zt_dfree(p->seg_x, p->mstream);
+    zt_dfree(p->seg_h, p->mstream);
+    zt_dfree(p->sum_x, p->mstream);
+    zt_dfree(p->sum_h, p->mstream);
 }
 
 int zt_solve_ctas(int N) { return solve_tiles(N); }

@@ -731,22 +731,12 @@ int zt_split_create(zt_plan* p) {
         while (bound >= std::ldexp(1.0, 62 + u)) ++u;
         w->u = u;
     }
-    cudaStream_t cs = nullptr;   // set-up on a private stream (no wait on other threads' work)
-    ZT_CU(zt_setup_stream(&cs));
-    struct StreamGuard {
-        cudaStream_t s;
-        ~StreamGuard() {
-            if (s) {
-                cudaStreamSynchronize(s);
-                cudaStreamDestroy(s);
-            }
-        }
-    } guard{cs};
+    cudaStream_t cs = p->mstream;   // the plan's private stream (synchronised at the end of plan creation)
     const size_t szA = (size_t)s * w->Mpad * w->ldk * sizeof(__nv_bfloat16);
     const size_t szB = (size_t)s * w->Npad * w->ldk * sizeof(__nv_bfloat16);
-    ZT_CU(cudaMalloc(&w->dA, szA));
+    ZT_CU(ZT_DMALLOC(w->dA, szA, cs));
     ZT_CU(cudaMemsetAsync(w->dA, 0, szA, cs));   // padding rows/columns stay zero
-    ZT_CU(cudaMalloc(&w->eA, (size_t)w->Mpad * sizeof(int)));
+    ZT_CU(ZT_DMALLOC(w->eA, (size_t)w->Mpad * sizeof(int), cs));
     ZT_CU(cudaMemsetAsync(w->eA, 0, (size_t)w->Mpad * sizeof(int), cs));
     int rc;
     if ((rc = make_map(&w->tmA, w->dA, s * w->Mpad, w->ldk, BM / cn))) return rc;
@@ -754,14 +744,14 @@ int zt_split_create(zt_plan* p) {
     if (w->nkb > MAX_KB) return zt_fail(ZT_EINVAL, "N too large for the split product (K blocks > %d)", MAX_KB);
     w->ngA = w->Mpad / (BM * cm);
     w->ngB = w->Npad / (BN * cn);
-    ZT_CU(cudaMalloc(&w->occA, (size_t)w->ngA * w->nkb * sizeof(int)));
+    ZT_CU(ZT_DMALLOC(w->occA, (size_t)w->ngA * w->nkb * sizeof(int), cs));
     ZT_CU(cudaMemsetAsync(w->occA, 0, (size_t)w->ngA * w->nkb * sizeof(int), cs));
     for (int b = 0; b < 2; ++b) {
-        ZT_CU(cudaMalloc(&w->occB[b], (size_t)w->ngB * w->nkb * sizeof(int)));
+        ZT_CU(ZT_DMALLOC(w->occB[b], (size_t)w->ngB * w->nkb * sizeof(int), cs));
         ZT_CU(cudaMemsetAsync(w->occB[b], 0, (size_t)w->ngB * w->nkb * sizeof(int), cs));
-        ZT_CU(cudaMalloc(&w->dB[b], szB));
+        ZT_CU(ZT_DMALLOC(w->dB[b], szB, cs));
         ZT_CU(cudaMemsetAsync(w->dB[b], 0, szB, cs));
-        ZT_CU(cudaMalloc(&w->eB[b], (size_t)w->Npad * sizeof(int)));
+        ZT_CU(ZT_DMALLOC(w->eB[b], (size_t)w->Npad * sizeof(int), cs));
         ZT_CU(cudaMemsetAsync(w->eB[b], 0, (size_t)w->Npad * sizeof(int), cs));
         if ((rc = make_map(&w->tmB[b], w->dB[b], s * w->Npad, w->ldk, BN / cm))) return rc;
     }
@@ -788,8 +778,8 @@ int zt_split_create(zt_plan* p) {
         for (auto& e : lower) ol.push_back(e.second);
         w->n_full = (int)of.size();
         w->n_lower = (int)ol.size();
-        ZT_CU(cudaMalloc(&w->order_full, of.size() * sizeof(int)));
-        ZT_CU(cudaMalloc(&w->order_lower, ol.size() * sizeof(int)));
+        ZT_CU(ZT_DMALLOC(w->order_full, of.size() * sizeof(int), cs));
+        ZT_CU(ZT_DMALLOC(w->order_lower, ol.size() * sizeof(int), cs));
         ZT_CU(cudaMemcpyAsync(w->order_full, of.data(), of.size() * sizeof(int), cudaMemcpyHostToDevice, cs));
         ZT_CU(cudaMemcpyAsync(w->order_lower, ol.data(), ol.size() * sizeof(int), cudaMemcpyHostToDevice, cs));
         ZT_CU(cudaStreamSynchronize(cs));   // host vectors go out of scope
@@ -814,15 +804,16 @@ size_t zt_split_bytes(int N, const zt_tuning& t) {
 void zt_split_destroy(zt_plan* p) {
     zt_split_ws* w = p->split;
     if (!w) return;
-    cudaFree(w->dA);
-    cudaFree(w->eA);
-    cudaFree(w->occA);
-    cudaFree(w->order_full);
-    cudaFree(w->order_lower);
+    cudaStream_t ms = p->mstream;
+    zt_dfree(w->dA, ms);
+    zt_dfree(w->eA, ms);
+    zt_dfree(w->occA, ms);
+    zt_dfree(w->order_full, ms);
+    zt_dfree(w->order_lower, ms);
     for (int b = 0; b < 2; ++b) {
-        cudaFree(w->dB[b]);
-        cudaFree(w->eB[b]);
-        cudaFree(w->occB[b]);
+        zt_dfree(w->dB[b], ms);
+        zt_dfree(w->eB[b], ms);
+        zt_dfree(w->occB[b], ms);
     }
     delete w;
     p->split = nullptr;
