@@ -30,6 +30,30 @@ int zt_cuda_check(cudaError_t e, const char* what) {
 
 extern "C" const char* zt_last_error(void) { return g_err; }
 
+// Opt-in tracing of host-side phases (environment variable ZT_TRACE=1).
+#include <chrono>
+static bool trace_on() {
+    static int on = -1;
+    if (on < 0) {
+        const char* e = getenv("ZT_TRACE");
+        on = (e && e[0] == '1') ? 1 : 0;
+    }
+    return on == 1;
+}
+struct ZtTrace {
+    const char* scope;
+    std::chrono::steady_clock::time_point t0, last;
+    explicit ZtTrace(const char* s) : scope(s) { t0 = last = std::chrono::steady_clock::now(); }
+    void mark(const char* what) {
+        if (!trace_on()) return;
+        auto now = std::chrono::steady_clock::now();
+        fprintf(stderr, "[zt-trace] %s %-28s %9.3f ms (total %9.3f ms)\n", scope, what,
+                std::chrono::duration<double, std::milli>(now - last).count(),
+                std::chrono::duration<double, std::milli>(now - t0).count());
+        last = now;
+    }
+};
+
 #include <mutex>
 static std::mutex g_attr_mu;
 static unsigned g_attr_done[64];
@@ -515,8 +539,10 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         cudaError_t _e = (call);                             \
         if (_e != cudaSuccess) return fail(zt_cuda_check(_e, #call)); \
     } while (0)
+    ZtTrace tr("zt_plan_create");
     ZT_TRY(cudaGetDevice(&p->device));
     ZT_TRY(zt_setup_stream(&p->mstream));
+    tr.mark("stream");
     ZT_TRY(cudaEventCreateWithFlags(&p->last_use, cudaEventDisableTiming));
     cudaStream_t cs = p->mstream;
     const size_t ntri = (size_t)N * (N + 1) / 2;
@@ -535,12 +561,14 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     ZT_TRY(ZT_DMALLOC(p->partials, (size_t)p->npartials * sizeof(double), cs));
     ZT_TRY(ZT_DMALLOC(p->state, sizeof(zt_dev_state), cs));
     ZT_TRY(ZT_DMALLOC(p->d_units, sizeof(unsigned long long), cs));
+    tr.mark("allocations");
     p->h_state = new (std::nothrow) zt_dev_state();   // pageable: pinning per plan is slow
     if (!p->h_state) return fail(zt_fail(ZT_ENOMEM, "host allocation failed"));
     // set-up work runs on a private stream so that creating a plan does not
     // wait for work other threads have queued on the device
     rc = zt_solve_create(p);
     if (rc != ZT_OK) return fail(rc);
+    tr.mark("solve workspace");
     cudaMemsetAsync(p->state, 0, sizeof(zt_dev_state), cs);
     cudaMemsetAsync(p->d_units, 0, sizeof(unsigned long long), cs);
     {
@@ -553,7 +581,9 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         } catch (...) {
             return fail(zt_fail(ZT_ENOMEM, "host allocation for the Laplacian factors failed"));
         }
+        tr.mark("host vectors");
         factor_host(N, ha.data(), hb.data(), hl.data(), hn.data());
+        tr.mark("host factors");
         cudaMemcpyAsync(p->lap_a, ha.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
         cudaMemcpyAsync(p->lap_b, hb.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
         cudaMemcpyAsync(p->fac_l, hl.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
@@ -561,12 +591,15 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         cudaError_t se = cudaGetLastError();
         if (se == cudaSuccess) se = cudaStreamSynchronize(cs);   // host vectors go out of scope
         if (se != cudaSuccess) return fail(zt_cuda_check(se, "plan set-up (factor upload)"));
+        tr.mark("factor upload + sync");
     }
     if (precision == ZT_PRECISION_SPLIT) {
         rc = zt_split_create(p);
         if (rc != ZT_OK) return fail(rc);
     }
+    tr.mark("split workspace");
     ZT_TRY(cudaStreamSynchronize(cs));   // allocations and set-up visible to every stream
+    tr.mark("final sync");
 #undef ZT_TRY
     *out = p;
     return ZT_OK;
