@@ -295,7 +295,7 @@ def _ensemble(args, tun, steps, graph=True):
 
 
 def _serving(args, duration):
-    """Poisson job stream, admission by device footprint, continuous batching."""
+    """Poisson job stream, admission by device footprint and class step latency, continuous batching."""
     import numpy as np
 
     from paper_2206_05466_gb300 import serving
@@ -311,7 +311,8 @@ def _serving(args, duration):
             cache[key] = vorticity_w0(N, seed=key[1])
         prec = z.PRECISION_SPLIT if jid % 2 == 0 else z.PRECISION_FP64
         jobs.append(serving.Job(jid=jid, N=N, nsteps=nsteps, h=0.01, precision=prec, arrival=t, W0=cache[key]))
-    rep = serving.Server(int(args.serve_budget_gb * 1e9)).run(jobs, time_limit=duration)
+    rep = serving.Server(int(args.serve_budget_gb * 1e9), target_step_ms=args.serve_target_ms).run(
+        jobs, time_limit=duration)
     rep.pop("results", None)
     rep.update({"arrivals": len(jobs), "rate_per_s": 50.0, "duration_s": duration,
                 "budget_gb": args.serve_budget_gb, "precision_mix": "even job ids split, odd FP64",
@@ -504,6 +505,8 @@ def main():
     ap.add_argument("--ens-steps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-target-ms", type=float, default=100.0,
+                    help="step latency above which a serving class admits no further job")
     ap.add_argument("--tuning", default="auto", choices=["auto", "fixed"])
     ap.add_argument("--tune-target", type=float, default=1e-11)
     ap.add_argument("--slices", type=int, default=7)

@@ -81,8 +81,7 @@ struct zt_batch {
     cudaStream_t mstream = nullptr;  // private stream of the stream-ordered allocations (no device syncs)
     zt_dev_state** dstates = nullptr;
     zt_dev_state* gathered = nullptr;
-    zt_dev_state* hstates = nullptr;   // host copy of the states (pageable)
-    zt_dev_state* hpinned = nullptr;   // pinned copy, graph mode only (captured memcpy target)
+    zt_dev_state* hstates = nullptr;   // pinned host copy of the states (also the captured memcpy target)
     Op copy, solve, split_P, split_W, split_A, gemm1, gemm2, f64a, f64b, upd_sweep, upd_final, conv;
     int sweeps_per_sync = 4;
     long launches = 0;
@@ -210,8 +209,7 @@ int enqueue_read_states(zt_batch* b, cudaStream_t s) {
     state_gather<<<(b->n + 127) / 128, 128, 0, s>>>(b->dstates, b->n, b->gathered);
     int rc = count_launch(b, "state_gather");
     if (rc) return rc;
-    zt_dev_state* dst = b->use_graph ? b->hpinned : b->hstates;
-    ZT_CU(cudaMemcpyAsync(dst, b->gathered, (size_t)b->n * sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
+    ZT_CU(cudaMemcpyAsync(b->hstates, b->gathered, (size_t)b->n * sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
     return ZT_OK;
 }
 
@@ -278,8 +276,7 @@ extern "C" void zt_batch_destroy(zt_batch* b) {
         zt_dfree(b->gathered, b->mstream);
         cudaStreamDestroy(b->mstream);
     }
-    delete[] b->hstates;
-    if (b->hpinned) cudaFreeHost(b->hpinned);
+    zt_host_states_release(b->hstates, b->n);
     delete b;
 }
 
@@ -426,8 +423,8 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
     if ((e = ZT_DMALLOC(b->gathered, count * sizeof(zt_dev_state), b->mstream)) != cudaSuccess)
         return fail(zt_cuda_check(e, "cudaMallocAsync"));
     if ((e = cudaStreamSynchronize(b->mstream)) != cudaSuccess) return fail(zt_cuda_check(e, "set-up"));
-    b->hstates = new (std::nothrow) zt_dev_state[count];   // pinned copy only for graph mode
-    if (!b->hstates) return fail(zt_fail(ZT_ENOMEM, "host allocation failed"));
+    b->hstates = zt_host_states_acquire(count);
+    if (!b->hstates) return fail(zt_fail(ZT_ENOMEM, "pinned host allocation failed"));
     *out = b;
     return ZT_OK;
 }
@@ -441,7 +438,6 @@ extern "C" int zt_batch_set_graph(zt_batch* b, int enable) {
         ZT_CU(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking));
         ZT_CU(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
     }
-    if (b->use_graph && !b->hpinned) ZT_CU(cudaMallocHost(&b->hpinned, (size_t)b->n * sizeof(zt_dev_state)));
     return ZT_OK;
 }
 
@@ -477,7 +473,6 @@ static int batch_step_impl(zt_batch* b, double tol, int maxit, zt_step_stats* st
         }
         enq += nsw;
         ZT_CU(cudaStreamSynchronize(s));
-        if (b->use_graph) std::memcpy(b->hstates, b->hpinned, (size_t)b->n * sizeof(zt_dev_state));
         bool all = true;
         for (int i = 0; i < b->n; ++i) all = all && b->hstates[i].done;
         if (all) break;

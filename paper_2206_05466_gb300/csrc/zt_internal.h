@@ -216,6 +216,15 @@ struct ConvArgs {      // residual reduction and stop decision (zt_plan.cu)
 // Plan set-up work goes to a private non-blocking stream of the greatest
 // priority, so that it is scheduled ahead of long-running work other threads
 // keep on the device.
+// Host mirrors of device state records live in a process-wide pinned arena
+// (chunks from cudaHostAlloc, kept for the life of the process), so that the
+// per-step device-to-host copy of the states is asynchronous.  A copy into
+// pageable memory would hold the calling thread inside the driver until its
+// stream drained, stalling other threads' driver calls (stream creation,
+// allocation) for as long.  Returns nullptr when pinned memory is exhausted.
+zt_dev_state* zt_host_states_acquire(int n);
+void zt_host_states_release(zt_dev_state* p, int n);
+
 inline cudaError_t zt_setup_stream(cudaStream_t* s) {
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);

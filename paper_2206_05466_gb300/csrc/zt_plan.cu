@@ -30,6 +30,66 @@ int zt_cuda_check(cudaError_t e, const char* what) {
 
 extern "C" const char* zt_last_error(void) { return g_err; }
 
+// ---- pinned arena of host state mirrors ------------------------------------
+#include <mutex>
+#include <vector>
+namespace {
+struct HostChunk {
+    zt_dev_state* base;
+    int cap;
+    std::vector<std::pair<int, int>> free;   // [start, length) ranges, sorted by start
+};
+std::mutex g_host_mu;
+std::vector<HostChunk> g_host_chunks;
+constexpr int kHostChunkSlots = 4096;
+}  // namespace
+
+zt_dev_state* zt_host_states_acquire(int n) {
+    if (n < 1) return nullptr;
+    std::lock_guard<std::mutex> g(g_host_mu);
+    for (auto& c : g_host_chunks)   // first fit
+        for (size_t i = 0; i < c.free.size(); ++i)
+            if (c.free[i].second >= n) {
+                zt_dev_state* r = c.base + c.free[i].first;
+                c.free[i].first += n;
+                c.free[i].second -= n;
+                if (c.free[i].second == 0) c.free.erase(c.free.begin() + (long)i);
+                return r;
+            }
+    const int cap = n > kHostChunkSlots ? n : kHostChunkSlots;
+    void* m = nullptr;
+    if (cudaHostAlloc(&m, (size_t)cap * sizeof(zt_dev_state), cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    HostChunk c{(zt_dev_state*)m, cap, {}};
+    if (cap > n) c.free.push_back({n, cap - n});
+    g_host_chunks.push_back(std::move(c));
+    return (zt_dev_state*)m;
+}
+
+void zt_host_states_release(zt_dev_state* p, int n) {
+    if (!p || n < 1) return;
+    std::lock_guard<std::mutex> g(g_host_mu);
+    for (auto& c : g_host_chunks) {
+        if (p < c.base || p >= c.base + c.cap) continue;
+        const int off = (int)(p - c.base);
+        size_t i = 0;
+        while (i < c.free.size() && c.free[i].first < off) ++i;
+        c.free.insert(c.free.begin() + (long)i, {off, n});
+        // coalesce with the neighbours
+        if (i + 1 < c.free.size() && c.free[i].first + c.free[i].second == c.free[i + 1].first) {
+            c.free[i].second += c.free[i + 1].second;
+            c.free.erase(c.free.begin() + (long)i + 1);
+        }
+        if (i > 0 && c.free[i - 1].first + c.free[i - 1].second == c.free[i].first) {
+            c.free[i - 1].second += c.free[i].second;
+            c.free.erase(c.free.begin() + (long)i);
+        }
+        return;
+    }
+}
+
 // Opt-in tracing of host-side phases (environment variable ZT_TRACE=1).
 #include <chrono>
 static bool trace_on() {
@@ -458,7 +518,7 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     if (!p) return;
     cudaStream_t ms = p->mstream;
     if (!ms) {   // creation failed before the private stream existed: nothing was allocated
-        delete p->h_state;
+        zt_host_states_release(p->h_state, 1);
         delete p;
         return;
     }
@@ -477,7 +537,7 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     zt_dfree(p->partials, ms);
     zt_dfree(p->state, ms);
     zt_dfree(p->d_units, ms);
-    delete p->h_state;
+    zt_host_states_release(p->h_state, 1);   // no copy into it is in flight: steps end synchronised
     for (int i = 0; i < p->caprecs; ++i) {
         if (p->recs[i].a) cudaEventDestroy(p->recs[i].a);
         if (p->recs[i].b) cudaEventDestroy(p->recs[i].b);
@@ -562,8 +622,8 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     ZT_TRY(ZT_DMALLOC(p->state, sizeof(zt_dev_state), cs));
     ZT_TRY(ZT_DMALLOC(p->d_units, sizeof(unsigned long long), cs));
     tr.mark("allocations");
-    p->h_state = new (std::nothrow) zt_dev_state();   // pageable: pinning per plan is slow
-    if (!p->h_state) return fail(zt_fail(ZT_ENOMEM, "host allocation failed"));
+    p->h_state = zt_host_states_acquire(1);
+    if (!p->h_state) return fail(zt_fail(ZT_ENOMEM, "pinned host allocation failed"));
     // set-up work runs on a private stream so that creating a plan does not
     // wait for work other threads have queued on the device
     rc = zt_solve_create(p);

@@ -1,15 +1,21 @@
 """Continuous-batching serving loop for IsoMP simulation jobs.
 
-Jobs (N, number of steps, h, precision, initial state) arrive over time.  A job
-is admitted when its plan's device footprint fits the memory budget (first
-come, first served); its state then stays resident on the device until its
-last step.  Resident jobs of like N and precision form a class; each class is
-advanced by its own worker thread on its own CUDA stream, one batched step
-(grouped kernels over all the class's jobs) per iteration.  Jobs that arrive
-while others are running join their class's batch at its next step, and
-classes run concurrently on the device, so small jobs do not wait for large
-ones.  A class's batch is rebuilt only when its resident set changes.  All
-arithmetic runs in the library's kernels; this module only schedules.
+Jobs (N, number of steps, h, precision, initial state) arrive over time.  Jobs
+of like N and precision form a class; each class has its own first-come,
+first-served queue.  The head of a class's queue is admitted when its plan's
+device footprint fits the memory budget and the class's step latency allows
+it: a class with no resident job always takes its head job; otherwise a new job
+joins only after the class has completed a step with its current set and while
+the class's measured step latency (moving average) is below the target.  Under
+overload the queues absorb the excess (reported as queueing delay) instead of
+the batches growing until every resident job's step takes seconds.  An admitted
+job's state stays resident on the device until its last step.  Each class is
+advanced by its own worker thread on its own CUDA stream (smaller N at higher
+priority), one batched step (grouped kernels over all the class's jobs) per
+iteration.  Jobs that are admitted while others are running join their class's
+batch at its next step, and classes run concurrently on the device.  A class's
+batch is rebuilt only when its resident set changes.  All arithmetic runs in
+the library's kernels; this module only schedules.
 
 Reported: per-step latency of resident jobs (time between a job's consecutive
 completed steps; p50/p99, overall and per class), aggregate job-steps/s,
@@ -53,11 +59,15 @@ def _pct(xs, q):
 
 
 class Server:
-    def __init__(self, budget_bytes: int, tol: float = 1e-12, maxit: int = 50, graph: bool = False):
+    def __init__(self, budget_bytes: int, tol: float = 1e-12, maxit: int = 50, graph: bool = False,
+                 target_step_ms: float | None = 100.0):
+        """target_step_ms: step latency above which a class admits no further job
+        (None: admission by memory footprint alone)."""
         self.budget = int(budget_bytes)
         self.tol = tol
         self.maxit = maxit
         self.graph = graph
+        self.target = None if target_step_ms is None else float(target_step_ms) * 1e-3
 
     def run(self, jobs, time_limit: float | None = None, keep_results: bool = False, clock=time.perf_counter):
         """Serve `jobs`; returns a report dict (results by job id if keep_results)."""
@@ -75,11 +85,14 @@ class Server:
             return int(round(high + (low - high) * rank / span))
         lock = threading.Lock()
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
-        queue = collections.deque()
+        queues: dict[tuple, collections.deque] = collections.defaultdict(collections.deque)
+        ema: dict[tuple, float] = {}            # moving average of the class's step time (s)
+        stepped: dict[tuple, bool] = {}         # a step completed since the class's last admission
         classes: dict[tuple, dict[int, _Resident]] = {}
         dirty: dict[tuple, bool] = {}
         workers: dict[tuple, threading.Thread] = {}
         lat: dict[tuple, list] = collections.defaultdict(list)
+        max_res: dict[tuple, int] = collections.defaultdict(int)   # peak resident jobs per class
         qdelay, results, errors, admit_times = [], {}, [], []
         pinned = {}
         st = {"used": 0, "peak": 0, "steps": 0, "completed": 0, "batched": 0, "stop": False}
@@ -104,9 +117,9 @@ class Server:
                         if batch is not None:
                             batch.close()
                             batch = None
-                        if not pending and not queue:
+                        if not pending and not queues[cls]:
                             with lock:
-                                if not classes[cls] and not pending and not queue:
+                                if not classes[cls] and not pending and not queues[cls]:
                                     return
                         time.sleep(0.001)
                         continue
@@ -118,12 +131,16 @@ class Server:
                                         [res[j].job.h for j in order])
                         if self.graph:
                             batch.set_graph(True)
+                    t_start = clock() - t0
                     with torch.cuda.stream(stream):
                         batch.step(self.tol, self.maxit, stream=stream, allow_not_converged=True)
                     t_done = clock() - t0
                     finished = []
                     with lock:
                         st["batched"] += 1
+                        dt = t_done - t_start
+                        ema[cls] = dt if cls not in ema else 0.7 * ema[cls] + 0.3 * dt
+                        stepped[cls] = True
                         for j in order:
                             r = classes[cls][j]
                             lat[cls].append(t_done - r.last_done)
@@ -158,18 +175,28 @@ class Server:
                 break
             with lock:
                 while pending and pending[0].arrival <= now:
-                    queue.append(pending.popleft())
+                    j = pending.popleft()
+                    queues[(j.N, j.precision)].append(j)
             admitted = False
-            while queue:   # first come, first served, by device footprint
+            while True:   # per class first come, first served; classes by their head's arrival
                 if time_limit is not None and clock() - t0 > time_limit:
                     break
-                job = queue[0]
-                need = z.plan_estimate_bytes(job.N, job.precision)
+                job = None
                 with lock:
                     resident = sum(len(c) for c in classes.values())
-                    if st["used"] + need > self.budget and resident:
+                    for cls in sorted((c for c in queues if queues[c]), key=lambda c: queues[c][0].arrival):
+                        head = queues[cls][0]
+                        need = z.plan_estimate_bytes(head.N, head.precision)
+                        if st["used"] + need > self.budget and resident:
+                            continue
+                        if classes.get(cls) and self.target is not None and not (
+                                stepped.get(cls) and ema.get(cls, 0.0) < self.target):
+                            continue
+                        job = queues[cls].popleft()
+                        stepped[cls] = False
                         break
-                    queue.popleft()
+                if job is None:
+                    break
                 ta = clock()
                 plan = z.Plan(job.N, job.precision)
                 tb = clock()
@@ -185,6 +212,7 @@ class Server:
                 cls = (job.N, job.precision)
                 with lock:
                     classes.setdefault(cls, {})[job.jid] = _Resident(job, plan, W, need, job.nsteps, t_adm)
+                    max_res[cls] = max(max_res[cls], len(classes[cls]))
                     dirty[cls] = True
                     st["used"] += need
                     st["peak"] = max(st["peak"], st["used"])
@@ -195,7 +223,7 @@ class Server:
                         th.start()
                 admitted = True
             with lock:
-                empty = not pending and not queue and not any(classes.values())
+                empty = not pending and not any(queues.values()) and not any(classes.values())
             if empty:
                 break
             if not admitted:
@@ -216,11 +244,13 @@ class Server:
             "batched_steps": st["batched"],
             "jobs_completed": st["completed"],
             "jobs_admitted": len(qdelay),
-            "jobs_left_queued": len(queue) + len(pending),
+            "jobs_left_queued": sum(len(q) for q in queues.values()) + len(pending),
+            "target_step_ms": None if self.target is None else self.target * 1e3,
             "step_latency_ms_p50": _pct(allat, 50),
             "step_latency_ms_p99": _pct(allat, 99),
             "per_class": {f"N={k[0]},{'split' if k[1] == z.PRECISION_SPLIT else 'fp64'}":
-                          {"job_steps": len(v), "p50_ms": _pct(v, 50), "p99_ms": _pct(v, 99)}
+                          {"job_steps": len(v), "p50_ms": _pct(v, 50), "p99_ms": _pct(v, 99),
+                           "max_resident": max_res[k]}
                           for k, v in lat.items()},
             "queue_delay_s_p50": float(np.percentile(qdelay, 50)) if qdelay else None,
             "peak_admitted_bytes": st["peak"],
