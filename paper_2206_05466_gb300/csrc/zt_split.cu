@@ -30,8 +30,9 @@
 //   warp 0  TMA producer: digit tiles (128 x 64 of X', 256 x 64 of B'^T,
 //           128-byte swizzle) into a 4-stage shared-memory ring;
 //   warp 1  TMEM allocation and the single MMA-issuing thread;
-//   warps 2-5  drain TMEM (double-buffered accumulator) into the int64
-//           accumulator, then the FP64 epilogue.
+//   warps 2-9  drain TMEM (double-buffered accumulator) into the int64
+//           accumulator, two warps per TMEM lane quadrant (128 columns
+//           each); the last drain of a tile adds, scales and stores FP64.
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the kernel
 // records a timeout in the step state, lets in-flight work retire and exits.
 #include <cuda.h>
@@ -54,7 +55,9 @@ constexpr int STAGES = 4;
 constexpr int A_TILE = BM * BK * 2;
 constexpr int B_TILE = BN * BK * 2;
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
-constexpr int NTHREADS = 192;
+constexpr int NDRAIN = 256;        // drain / epilogue threads: 8 warps, two per TMEM lane quadrant
+constexpr int NTHREADS = 64 + NDRAIN;
+constexpr int MAX_S = 8;
 constexpr uint32_t TMEM_COLS = 512;  // two 128 x 256 FP32 accumulators
 constexpr int MAX_KB = 512;        // K blocks of 64 for N <= 16384
 constexpr size_t SMEM_BYTES =
@@ -155,6 +158,8 @@ __device__ __forceinline__ void cluster_sync() {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// barrier 1 among the drain warps only
+__device__ __forceinline__ void drain_bar() { asm volatile("bar.sync 1, %0;" ::"n"(NDRAIN) : "memory"); }
 
 // K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms of 1 KiB.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -361,16 +366,6 @@ __device__ __forceinline__ int seg_units(int g, int beta, int exact_groups) {
     const int lim = (1 << (26 - 2 * beta)) / BK;
     return lim < 1 ? 1 : lim;
 }
-// Active units of digit group g on this tile: pairs p in [fa, g - fb] per K block.
-__device__ __forceinline__ int group_units(const uint8_t* fa, const uint8_t* fb, int g, int nkb) {
-    int n = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-        const int c = g - fb[kb] - fa[kb] + 1;
-        n += c > 0 ? c : 0;
-    }
-    return n;
-}
-
 // ---------------------------------------------------------------------------
 // The tcgen05 product kernel.
 // ---------------------------------------------------------------------------
@@ -388,6 +383,7 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
     uint64_t* drain = acce + 2;        // [1]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* gunits = reinterpret_cast<int*>(tmem_slot + 2);     // [MAX_S] active units per digit group
     uint8_t* fa = reinterpret_cast<uint8_t*>(full) + 256;   // [MAX_KB] first nonzero X' digit per K block
     uint8_t* fb = fa + MAX_KB;                               // [MAX_KB] first nonzero B'^T digit
 
@@ -434,7 +430,7 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&accf[i], 1);
-            mbar_init(&acce[i], 128);
+            mbar_init(&acce[i], NDRAIN);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -557,18 +553,50 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
             volatile int dummy = 0;
             if (!mbar_wait(drain, 0, &dummy)) *abort_flag = 1;
         }
-    } else {   // ---- drain / epilogue: warps 2..5 ----
-        const int wq = warp & 3;
-        const int row = wq * 32 + lane;
-        const int gi = i0 + row;
+    } else {   // ---- drain / epilogue: warps 2..9 ----
+        const int wq = warp & 3;                 // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;        // column half of the tile this warp drains
+        const int dt = threadIdx.x - 64;         // 0 .. NDRAIN-1
+        const int gi = i0 + wq * 32 + lane;
+        const bool row_ok = gi < a.N;
         const int ncols = 2 * a.N;
         const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
         long long* Crow = reinterpret_cast<long long*>(a.C) + (size_t)gi * ncols;
+        // active units of every digit group on this tile, counted once
+        if (dt < MAX_S) gunits[dt] = 0;
+        drain_bar();
+        {
+            int u[MAX_S];
+#pragma unroll
+            for (int g = 0; g < MAX_S; ++g) u[g] = 0;
+            for (int kb = dt; kb < nkb; kb += NDRAIN) {
+                const int c = fa[kb] + fb[kb];
+#pragma unroll
+                for (int g = 0; g < MAX_S; ++g) u[g] += max(0, g - c + 1);
+            }
+#pragma unroll
+            for (int g = 0; g < MAX_S; ++g) {
+                int v = u[g];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && g < a.s && v) atomicAdd(&gunits[g], v);
+            }
+        }
+        drain_bar();
+        int total = 0;
+        for (int g = 0; g < a.s; ++g) {
+            const int ulim = seg_units(g, a.beta, a.exact_groups);
+            total += gunits[g] == 0 ? 0 : (gunits[g] - 1) / ulim + 1;
+        }
+        // FP32 segment sums are integers below 2^31 unless K' and the digits are large
+        const bool fits32 = (double)a.s * (double)ncols * (double)(1LL << (2 * a.beta - 2)) < 2147483647.0;
+        const bool v32 = (a.N & 1) == 0 && ((uintptr_t)a.C & 31) == 0;   // rows start on 32-byte boundaries
+        const int ea = row_ok ? a.eA[gi] : 0;
+        const int eoff = -(a.s + 1) * a.beta + 2 + a.u;
         int seg = 0;
         bool ok = true;
         for (int g = 0; g < a.s && ok; ++g) {
             const int ulim = seg_units(g, a.beta, a.exact_groups);
-            const int units = group_units(fa, fb, g, nkb);
+            const int units = gunits[g];
             const int nsegs = units == 0 ? 0 : (units - 1) / ulim + 1;
             const int sh = (a.s - 1 - g) * a.beta - a.u;
             for (int q = 0; q < nsegs; ++q) {
@@ -579,33 +607,91 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
                     break;
                 }
                 tc_fence_after();
+                const bool first = seg == 1, last = seg == total;
 #pragma unroll 1
-                for (int ch = 0; ch < BN / 32; ++ch) {
+                for (int ch = 0; ch < BN / 64; ++ch) {
+                    const int col0 = half * (BN / 2) + ch * 32;
                     uint32_t r[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + ch * 32), r);
-                    const int cb = c0 + ch * 32;
-                    if (gi < a.N && cb < ncols) {
-                        long long* dst = Crow + cb;
+                    tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + col0), r);
+                    const int cb0 = c0 + col0;
+                    if (!row_ok || cb0 >= ncols) continue;
 #pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const int c = cb + 2 * q;
-                            if (c >= ncols) break;
-                            long long v0 = __float2ll_rn(__uint_as_float(r[2 * q]));
-                            long long v1 = __float2ll_rn(__uint_as_float(r[2 * q + 1]));
-                            if (sh >= 0) {
-                                v0 <<= sh;
-                                v1 <<= sh;
+                    for (int hh = 0; hh < 2; ++hh) {   // 16 columns at a time (register pressure)
+                        const int cb = cb0 + 16 * hh;
+                        if (cb >= ncols) break;
+                        const int lim = min(16, ncols - cb);   // even; a multiple of 4 when v32
+                        long long v[16];
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            const float f = __uint_as_float(r[16 * hh + t]);
+                            long long x = fits32 ? (long long)__float2int_rn(f) : __float2ll_rn(f);
+                            if (sh >= 0)
+                                x <<= sh;
+                            else
+                                x = (x + (1LL << (-sh - 1))) >> (-sh);
+                            v[t] = x;
+                        }
+                        long long* dst = Crow + cb;
+                        if (!first) {   // add the accumulator (all loads first)
+                            long long o[16];
+                            if (v32) {
+#pragma unroll
+                                for (int t = 0; t < 16; t += 4) {
+                                    if (t < lim)
+                                        asm volatile("ld.global.v4.b64 {%0,%1,%2,%3}, [%4];"
+                                                     : "=l"(o[t]), "=l"(o[t + 1]), "=l"(o[t + 2]), "=l"(o[t + 3])
+                                                     : "l"(dst + t));
+                                    else
+                                        o[t] = o[t + 1] = o[t + 2] = o[t + 3] = 0;
+                                }
                             } else {
-                                v0 = (v0 + (1LL << (-sh - 1))) >> (-sh);
-                                v1 = (v1 + (1LL << (-sh - 1))) >> (-sh);
+#pragma unroll
+                                for (int t = 0; t < 16; t += 2) {
+                                    if (t < lim) {
+                                        const longlong2 w = *reinterpret_cast<const longlong2*>(dst + t);
+                                        o[t] = w.x;
+                                        o[t + 1] = w.y;
+                                    } else {
+                                        o[t] = o[t + 1] = 0;
+                                    }
+                                }
                             }
-                            longlong2* p2 = reinterpret_cast<longlong2*>(dst + 2 * q);
-                            if (seg != 1) {   // the first drained segment initialises the accumulator
-                                const longlong2 o = *p2;
-                                v0 += o.x;
-                                v1 += o.y;
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) v[t] += o[t];
+                        }
+                        if (last) {   // int64 fixed point -> FP64, in place
+#pragma unroll
+                            for (int t = 0; t < 16; t += 4) {
+                                if (t >= lim) break;
+                                const int4 eb4 = *reinterpret_cast<const int4*>(a.eB + cb + t);
+                                const int ebv[4] = {eb4.x, eb4.y, eb4.z, eb4.w};
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    double out;
+                                    if (ea == EXP_NAN || ebv[k] == EXP_NAN) {
+                                        out = __longlong_as_double(0x7ff8000000000000LL);
+                                    } else {
+                                        const int E = ea + ebv[k] + eoff;
+                                        const double scale = (E >= -1022 && E <= 1023)
+                                                                 ? __longlong_as_double((long long)(E + 1023) << 52)
+                                                                 : ldexp(1.0, E);
+                                        out = (double)v[t + k] * (scale * a.alpha);
+                                    }
+                                    v[t + k] = __double_as_longlong(out);
+                                }
                             }
-                            *p2 = make_longlong2(v0, v1);
+                        }
+                        if (v32) {
+#pragma unroll
+                            for (int t = 0; t < 16; t += 4)
+                                if (t < lim)
+                                    asm volatile("st.global.v4.b64 [%0], {%1,%2,%3,%4};" ::"l"(dst + t), "l"(v[t]),
+                                                 "l"(v[t + 1]), "l"(v[t + 2]), "l"(v[t + 3])
+                                                 : "memory");
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < 16; t += 2)
+                                if (t < lim) *reinterpret_cast<longlong2*>(dst + t) = make_longlong2(v[t], v[t + 1]);
                         }
                     }
                 }
@@ -613,22 +699,11 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
                 mbar_arrive(&acce[b]);
             }
         }
-        if (ok && gi < a.N) {   // int64 fixed point -> FP64
-            const int ea = a.eA[gi];
-            const int off = -(a.s + 1) * a.beta + 2 + a.u;
-            for (int c = c0; c < c0 + BN && c < ncols; ++c) {
-                const int eb = a.eB[c];
-                const long long v = seg ? Crow[c] : 0;   // no drained segment: all digit products were zero
-                double out;
-                if (ea == EXP_NAN || eb == EXP_NAN) {
-                    out = __longlong_as_double(0x7ff8000000000000LL);
-                } else {
-                    const int E = ea + eb + off;
-                    double scale = (E >= -1022 && E <= 1023) ? __longlong_as_double((long long)(E + 1023) << 52)
-                                                             : ldexp(1.0, E);
-                    out = (double)v * (scale * a.alpha);
-                }
-                reinterpret_cast<double*>(Crow)[c] = out;
+        if (ok && total == 0 && row_ok) {   // every digit product of the tile is zero
+            const int cbeg = c0 + half * (BN / 2);
+            for (int c = cbeg; c < cbeg + BN / 2 && c < ncols; ++c) {
+                const bool nan = ea == EXP_NAN || a.eB[c] == EXP_NAN;
+                reinterpret_cast<double*>(Crow)[c] = nan ? __longlong_as_double(0x7ff8000000000000LL) : 0.0;
             }
         }
     }
