@@ -74,6 +74,7 @@ struct zt_batch {
     int n = 0;
     int device = 0;
     int final_mode = ZT_FINAL_FRESH;
+    int maxN = 0;                    // largest instance
     std::vector<zt_plan*> plans;
     std::vector<double2*> W;
     std::vector<double> h;
@@ -147,10 +148,10 @@ int count_launch(zt_batch* b, const char* what) {
 // Pt = solve(Wt), A = Pt Wt, B = A Pt for every instance (grouped launches).
 int enqueue_products(zt_batch* b, cudaStream_t s, int gate) {
     int rc;
-    if ((rc = zt_solve_grouped((const SolveArgs*)b->solve.tab, b->solve.offs, b->solve.n, b->solve.total, s,
-                               gate)))
+    if ((rc = zt_solve_grouped((const SolveArgs*)b->solve.tab, b->solve.offs, b->solve.n, b->solve.total, b->maxN,
+                               s, gate)))
         return rc;
-    b->launches += 3;
+    b->launches += ZT_SOLVE_LAUNCHES;
     if (b->gemm1.n) {
         if ((rc = zt_split_rows_grouped((const SplitRowsArgs*)b->split_P.tab, b->split_P.offs, b->split_P.n,
                                         b->split_P.total, s, gate)))
@@ -303,6 +304,7 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
     for (int i = 0; i < count; ++i) {
         zt_plan* p = plans[i];
         if (!p || !W[i]) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: instance %d has a NULL plan or W", i));
+        if (p->N > b->maxN) b->maxN = p->N;
         if (((uintptr_t)W[i]) & 15u) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: W[%d] not 16-byte aligned", i));
         if (!std::isfinite(h[i])) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: h[%d] not finite", i));
         if (p->device != dev) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: plans on different devices"));

@@ -79,8 +79,6 @@ struct zt_plan {
     // (r, c) belongs to diagonal m = r - c at position i = c.
     double* lap_a = nullptr;   // T_m diagonal a_i
     double* lap_b = nullptr;   // T_m off-diagonal b_i (coupling i, i+1)
-    double* fac_l = nullptr;   // LDL^T multiplier l_i  (l_0 = 0)
-    double* fac_nd = nullptr;  // -1 / d_i              (0 for the dropped m=0 row)
     // Step workspace, complex N x N interleaved.
     double2* Wn = nullptr;
     double2* Wt = nullptr;
@@ -89,14 +87,24 @@ struct zt_plan {
     double2* B = nullptr;
     double* partials = nullptr;
     int npartials = 0;
-    // segmented stream solve: per-(diagonal, segment) end/start values
+    // segmented stream solve: factors and their products within a segment,
+    // diagonal-major (diagonal m at dof[m], padded to 8 entries), constant
+    double* fac_l = nullptr;   // LDL^T multiplier l_i  (l_0 = 0)
+    double* fac_nd = nullptr;  // -1 / d_i              (0 for the dropped m=0 row)
+    double* fac_g = nullptr;   // G_i = prod_{j = segment start .. i} (-l_j)
+    double* fac_h = nullptr;   // H_i = prod_{j = i+1 .. segment end} (-l_j)
+    long long* dof = nullptr;  // [N + 1]
+    // per-(diagonal, segment) end/start values and inflows
     int nseg = 0;
     double2* seg_z = nullptr;
     double* seg_g = nullptr;
     double2* seg_x = nullptr;
     double* seg_h = nullptr;
+    double2* carry_f = nullptr;
+    double2* carry_b = nullptr;
     double2* sum_x = nullptr;
     double* sum_h = nullptr;
+    double2* sol_mu = nullptr;   // mean of the m = 0 solution
     zt_dev_state* state = nullptr;
     zt_dev_state* h_state = nullptr;   // pinned host mirror
     zt_split_ws* split = nullptr;
@@ -130,14 +138,20 @@ int zt_timer_collect(zt_plan* p, int iters);
 struct SolveArgs {     // stream solve (zt_solve.cu)
     const double2* W;
     double2* P;
-    const double* fl;
+    const double* fl;  // diagonal-major l, nd, G_i, H_i (constant)
     const double* fnd;
+    const double* fg;
+    const double* fh;
+    const long long* dof;  // diagonal offsets
     double2* seg_z;    // [N][K] end value of z0 in a segment
-    double* seg_g;     // [N][K] product G over the segment
+    const double* seg_g;   // [N][K] product G over the segment (constant)
     double2* seg_x;    // [N][K] start value of x0 in a segment
-    double* seg_h;     // [N][K] H at the segment start
+    const double* seg_h;   // [N][K] H at the segment start (constant)
+    double2* cf;       // [N][K] forward inflow z_{kL-1} of a segment
+    double2* cb;       // [N][K] backward inflow x_{kL+L} of a segment
     double2* sum_x;    // [K] m = 0 only: sum of x0 over the segment
-    double* sum_h;     // [K] m = 0 only: sum of H over the segment
+    const double* sum_h;   // [K] m = 0 only: sum of H over the segment (constant)
+    double2* mu;       // m = 0 only: mean of the solution
     int N, K;
     const zt_dev_state* st;
     int gate;
@@ -260,6 +274,11 @@ int zt_cuda_check(cudaError_t e, const char* what);
 int zt_launch_laplacian(zt_plan* p, const double2* P, double2* W, cudaStream_t s);
 int zt_launch_stream_solve(zt_plan* p, const double2* W, double2* P, cudaStream_t s, int gate);
 int zt_solve_create(zt_plan* p);
+// Factors (host l and nd, packed lower-triangular) and their segment products
+// uploaded to the plan in the solve's layout; waits for its own copies.
+int zt_solve_upload_factors(zt_plan* p, const double* host_l, const double* host_nd);
+size_t zt_solve_bytes(int N);   // device bytes of the solve workspace
+constexpr int ZT_SOLVE_LAUNCHES = 5;
 void zt_solve_destroy(zt_plan* p);
 // C = alpha * X conj(Y)^T, FP64 DFMA.  With lower_only, only tiles that
 // touch the lower triangle (i >= j) are computed.
@@ -269,7 +288,7 @@ int zt_launch_zgemm_fp64(zt_plan* p, const double2* X, const double2* Y, double2
 // offs[0..n] (device) the prefix sums of CTAs, `total` = offs[n].
 int zt_solve_args(zt_plan* p, const double2* W, double2* P, SolveArgs* out);
 int zt_solve_ctas(int N);
-int zt_solve_grouped(const SolveArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
+int zt_solve_grouped(const SolveArgs* tab, const int* offs, int n, int total, int maxN, cudaStream_t s, int gate);
 int zt_split_rows_args(zt_plan* p, const double2* X, int to_a, int b_slot, SplitRowsArgs* out);
 int zt_split_rows_grouped(const SplitRowsArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
 int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, GemmEntry* out,

@@ -527,8 +527,6 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     zt_solve_destroy(p);
     zt_dfree(p->lap_a, ms);
     zt_dfree(p->lap_b, ms);
-    zt_dfree(p->fac_l, ms);
-    zt_dfree(p->fac_nd, ms);
     zt_dfree(p->Wn, ms);
     zt_dfree(p->Wt, ms);
     zt_dfree(p->P, ms);
@@ -563,8 +561,8 @@ extern "C" long long zt_plan_estimate_bytes(int N, int precision, const zt_tunin
     if (opt) t = *opt;
     fill_tuning_defaults(t);
     const size_t nn = (size_t)N * N, ntri = (size_t)N * (N + 1) / 2;
-    const size_t nt = (N + 31) / 32, nseg = (N + 63) / 64;
-    size_t b = 4 * ntri * 8 + 5 * nn * 16 + nt * (nt + 1) / 2 * 8 + (size_t)N * nseg * 48 + nseg * 24 + 1024;
+    const size_t nt = (N + 31) / 32;
+    size_t b = 2 * ntri * 8 + 5 * nn * 16 + nt * (nt + 1) / 2 * 8 + zt_solve_bytes(N) + 1024;
     if (precision == ZT_PRECISION_SPLIT) b += zt_split_bytes(N, t);
     return (long long)b;
 }
@@ -609,8 +607,6 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     const size_t mat = (size_t)N * N * sizeof(double2);
     ZT_TRY(ZT_DMALLOC(p->lap_a, ntri * sizeof(double), cs));
     ZT_TRY(ZT_DMALLOC(p->lap_b, ntri * sizeof(double), cs));
-    ZT_TRY(ZT_DMALLOC(p->fac_l, ntri * sizeof(double), cs));
-    ZT_TRY(ZT_DMALLOC(p->fac_nd, ntri * sizeof(double), cs));
     ZT_TRY(ZT_DMALLOC(p->Wn, mat, cs));
     ZT_TRY(ZT_DMALLOC(p->Wt, mat, cs));
     ZT_TRY(ZT_DMALLOC(p->P, mat, cs));
@@ -646,12 +642,13 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         tr.mark("host factors");
         cudaMemcpyAsync(p->lap_a, ha.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
         cudaMemcpyAsync(p->lap_b, hb.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
-        cudaMemcpyAsync(p->fac_l, hl.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
-        cudaMemcpyAsync(p->fac_nd, hn.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
         cudaError_t se = cudaGetLastError();
         if (se == cudaSuccess) se = cudaStreamSynchronize(cs);   // host vectors go out of scope
         if (se != cudaSuccess) return fail(zt_cuda_check(se, "plan set-up (factor upload)"));
         tr.mark("factor upload + sync");
+        rc = zt_solve_upload_factors(p, hl.data(), hn.data());
+        if (rc != ZT_OK) return fail(rc);
+        tr.mark("solve factors");
     }
     if (precision == ZT_PRECISION_SPLIT) {
         rc = zt_split_create(p);
