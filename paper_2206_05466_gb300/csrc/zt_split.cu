@@ -232,6 +232,35 @@ __device__ __forceinline__ long long to_fixed(double x, int e, int sb) {
     return bits < 0 ? -v : v;
 }
 
+// v * 2^E rounded to the nearest double (ties to even) with integer operations
+// only (the FP64 pipe is narrow); the same value as (double)v * 2^E.  Results
+// outside the normal range take the FP64 route.
+__device__ __forceinline__ double fixed_to_double(long long v, int E) {
+    if (v == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)v & 0x8000000000000000ull;
+    const unsigned long long u = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int nb = 64 - __clzll((long long)u);   // significant bits
+    int ex = E + nb - 1;                           // unbiased exponent of the result
+    unsigned long long m;
+    if (nb <= 53) {
+        m = u << (53 - nb);
+    } else {
+        const int r = nb - 53;
+        m = u >> r;
+        const unsigned long long rem = u & ((1ull << r) - 1), half = 1ull << (r - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            ++m;
+            if (m == (1ull << 53)) {
+                m >>= 1;
+                ++ex;
+            }
+        }
+    }
+    if (ex < -1022 || ex > 1023) return ldexp((double)v, E);
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(ex + 1023) << 52) | (m & ((1ull << 52) - 1))));
+}
+
 __device__ __forceinline__ void split_rows_body(const SplitRowsArgs& ra, int j) {
     if (zt_gate_skip(ra.st, ra.gate)) return;
     const double2* __restrict__ X = ra.X;
@@ -288,17 +317,20 @@ __device__ __forceinline__ void split_rows_body(const SplitRowsArgs& ra, int j) 
             bool nz = false;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                long long dr, di;
+                // balanced digit d = ((v + H) mod R) - H, and (v - d) / R = (v + H) >> beta;
+                // digits fit 32 bits, so the conversions stay off the FP64 pipe
+                int dr, di;
                 if (p > 0) {
-                    dr = ((vr[u] + H) & (R - 1)) - H;
-                    di = ((vi[u] + H) & (R - 1)) - H;
-                    vr[u] = (vr[u] - dr) >> beta;
-                    vi[u] = (vi[u] - di) >> beta;
+                    const long long tr = vr[u] + H, ti = vi[u] + H;
+                    dr = ((int)tr & (int)(R - 1)) - (int)H;
+                    di = ((int)ti & (int)(R - 1)) - (int)H;
+                    vr[u] = tr >> beta;
+                    vi[u] = ti >> beta;
                 } else {
-                    dr = vr[u];
-                    di = vi[u];
+                    dr = (int)vr[u];
+                    di = (int)vi[u];
                 }
-                nz |= (dr != 0) | (di != 0);
+                nz |= (dr | di) != 0;
                 const float fr = (float)dr, fi = (float)di;
                 wa[u] = __floats2bfloat162_rn(fr, fi);
                 // B'^T row 2j: interleaved(y); row 2j+1: interleaved(i y) = (-im, re)
@@ -592,6 +624,12 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
         const bool v32 = (a.N & 1) == 0 && ((uintptr_t)a.C & 31) == 0;   // rows start on 32-byte boundaries
         const int ea = row_ok ? a.eA[gi] : 0;
         const int eoff = -(a.s + 1) * a.beta + 2 + a.u;
+        // alpha = +-2^k (the usual +-1) folds into the exponent and the sign
+        const long long abits = __double_as_longlong(a.alpha);
+        const int aef = (int)((abits >> 52) & 0x7FF);
+        const bool apow2 = (abits & 0xFFFFFFFFFFFFFLL) == 0 && aef != 0 && aef != 0x7FF;
+        const int aexp = apow2 ? aef - 1023 : 0;
+        const unsigned long long asign = apow2 ? ((unsigned long long)abits & 0x8000000000000000ull) : 0ull;
         int seg = 0;
         bool ok = true;
         for (int g = 0; g < a.s && ok; ++g) {
@@ -671,11 +709,9 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
                                     if (ea == EXP_NAN || ebv[k] == EXP_NAN) {
                                         out = __longlong_as_double(0x7ff8000000000000LL);
                                     } else {
-                                        const int E = ea + ebv[k] + eoff;
-                                        const double scale = (E >= -1022 && E <= 1023)
-                                                                 ? __longlong_as_double((long long)(E + 1023) << 52)
-                                                                 : ldexp(1.0, E);
-                                        out = (double)v[t + k] * (scale * a.alpha);
+                                        out = fixed_to_double(v[t + k], ea + ebv[k] + eoff + aexp);
+                                        out = __longlong_as_double(__double_as_longlong(out) ^ (long long)asign);
+                                        if (!apow2) out *= a.alpha;
                                     }
                                     v[t + k] = __double_as_longlong(out);
                                 }
