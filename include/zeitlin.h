@@ -55,11 +55,13 @@ typedef struct zt_tuning {
     int exact_groups;    /* SPLIT: leading digit groups summed exactly (default 4)   */
     int final_mode;      /* ZT_FINAL_FRESH (default) or ZT_FINAL_REUSE               */
     int sweeps_per_sync; /* sweeps enqueued between host convergence checks (def. 4) */
-    int cluster_m;       /* SPLIT: CTAs sharing each B'^T tile by TMA multicast (1, 2, 4; def. 2) */
+    int cluster_m;       /* SPLIT: CTAs sharing each B'^T tile by TMA multicast (1, 2, 4; def. 1) */
     int cluster_n;       /* SPLIT: CTAs sharing each X' tile by TMA multicast (1, 2, 4; def. 1) */
     int dense;           /* SPLIT: 1 = multiply every digit pair; 0 (default) = skip digit-pair
                             tiles that are exactly zero (identical results)                  */
-    int tile_order;      /* SPLIT: 0 (default) = tiles near the diagonal first, 1 = row-major */
+    int tile_order;      /* SPLIT launch order of output tiles: 0 (default) / 3 = column blocks of
+                            8 / 16 tile groups, rows walked inside a block; 1 = row-major;
+                            2 = tiles near the diagonal first */
 } zt_tuning;
 
 typedef struct zt_step_stats {

@@ -16,7 +16,7 @@ import os
 
 DEFAULT_CANDIDATES = [
     dict(slices=s, digit_bits=7, exact_groups=eg, cluster_m=cm, cluster_n=1, tile_order=to)
-    for s in (7, 6) for eg in (4, 3) for cm in (2, 4, 1) for to in (0, 1)
+    for s in (7, 6) for eg in (4, 3, 2) for cm in (1, 2) for to in (0, 1, 3)
 ]
 REFERENCE = dict(slices=8, digit_bits=7, exact_groups=8, cluster_m=2, cluster_n=1)
 

@@ -551,7 +551,7 @@ static void fill_tuning_defaults(zt_tuning& t) {
     if (t.digit_bits == 0) t.digit_bits = 7;
     if (t.exact_groups == 0) t.exact_groups = 4;
     if (t.sweeps_per_sync == 0) t.sweeps_per_sync = 4;
-    if (t.cluster_m == 0) t.cluster_m = 2;
+    if (t.cluster_m == 0) t.cluster_m = 1;
     if (t.cluster_n == 0) t.cluster_n = 1;
 }
 
@@ -586,6 +586,22 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     if (p->tun.sweeps_per_sync < 1 || p->tun.sweeps_per_sync > 64) {
         delete p;
         return zt_fail(ZT_EINVAL, "zt_plan_create: sweeps_per_sync outside [1, 64]");
+    }
+    if (precision == ZT_PRECISION_SPLIT) {   // checked before any device work
+        const zt_tuning& t = p->tun;
+        const char* bad = nullptr;
+        auto side = [](int v) { return v == 1 || v == 2 || v == 4; };
+        if (t.slices < 3 || t.slices > 8) bad = "slices outside [3, 8]";
+        else if (t.digit_bits < 6 || t.digit_bits > 8) bad = "digit_bits outside [6, 8]";
+        else if (t.exact_groups < 1 || t.exact_groups > t.slices) bad = "exact_groups outside [1, slices]";
+        else if (t.slices * t.digit_bits > 62) bad = "slices*digit_bits above 62";
+        else if (!side(t.cluster_m) || !side(t.cluster_n) || t.cluster_m * t.cluster_n > 8)
+            bad = "cluster sides must be 1, 2 or 4, at most 8 CTAs";
+        else if (t.tile_order < 0 || t.tile_order > 3) bad = "tile_order outside [0, 3]";
+        if (bad) {
+            delete p;
+            return zt_fail(ZT_EINVAL, "zt_plan_create: %s", bad);
+        }
     }
     int rc = ZT_OK;
     auto fail = [&](int code) {

@@ -45,3 +45,18 @@ def test_argument_validation_on_host():
     assert L.zt_plan_create(8, 0, None, None) == z.ZT_EINVAL
     assert L.zeitlin_stream_solve(None, None, None, None) == z.ZT_EINVAL
     assert L.isomp_step(None, None, 0.01, 1e-12, 50, None, None) == z.ZT_EINVAL
+
+
+@pytest.mark.parametrize("bad", [dict(slices=2), dict(slices=9), dict(digit_bits=5), dict(digit_bits=9),
+                                 dict(slices=4, exact_groups=5), dict(slices=8, digit_bits=8),
+                                 dict(cluster_m=3), dict(cluster_m=4, cluster_n=4), dict(tile_order=4),
+                                 dict(tile_order=-1), dict(sweeps_per_sync=65), dict(final_mode=7)])
+def test_split_tuning_validation_on_host(bad):
+    # rejected before any device work, so this runs without a GPU
+    L = z.load()
+    t = z.Tuning()
+    for k, v in bad.items():
+        setattr(t, k, v)
+    h = ctypes.c_void_p()
+    assert L.zt_plan_create(64, z.PRECISION_SPLIT, ctypes.byref(t), ctypes.byref(h)) == z.ZT_EINVAL
+    assert not h.value
