@@ -197,8 +197,35 @@ def _tuning(args, N):
         return dict(res["tuning"]), {"mode": "auto", "target_rel_err": args.tune_target,
                                      "probe_rel_err": res["rel_err"], "probe_ms": res["ms"]}
     tun = dict(slices=args.slices, digit_bits=args.digit_bits, exact_groups=args.exact_groups,
-               cluster_m=args.cluster_m, cluster_n=args.cluster_n)
+               cluster_m=args.cluster_m, cluster_n=args.cluster_n, tile_order=args.tile_order)
     return tun, {"mode": "fixed"}
+
+
+def run_profile(args):
+    """Kernels only, for profiler captures: --warmup + --steps IsoMP steps of the
+    bench workload with a fixed tuning (or the FP64 form), nothing else."""
+    import torch
+
+    from paper_2206_05466_gb300 import zeitlin as z
+    from paper_2206_05466_gb300.inputs import vorticity_w0
+
+    torch.cuda.set_device(0)
+    N = args.n
+    if args.fp64:
+        plan, tun = z.Plan(N, z.PRECISION_FP64), {}
+    else:
+        tun, _ = _tuning(args, N)
+        plan = z.Plan(N, z.PRECISION_SPLIT, **tun)
+    W = torch.from_numpy(vorticity_w0(N, seed=0)).cuda()
+    iters = []
+    for _ in range(args.warmup + args.steps):
+        iters.append(z.isomp_step(plan, W, H, TOL, MAXIT)["iters"])
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "profile", "N": N, "precision": "fp64" if args.fp64 else "split", "tuning": tun,
+                      "steps": args.warmup + args.steps, "sweeps": iters, "launches": plan.launch_count()}),
+          flush=True)
+    plan.close()
+    return 0
 
 
 def _casimir_drift(W0, W1, ks=(2, 3, 4)):
@@ -500,7 +527,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--mode", default="bench", choices=["bench", "casimir", "ensemble", "serving"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "casimir", "ensemble", "serving", "profile"])
     ap.add_argument("--ens-count", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=20.0)
@@ -512,8 +539,10 @@ def main():
     ap.add_argument("--slices", type=int, default=7)
     ap.add_argument("--digit-bits", type=int, default=7)
     ap.add_argument("--exact-groups", type=int, default=4)
-    ap.add_argument("--cluster-m", type=int, default=2)
+    ap.add_argument("--cluster-m", type=int, default=1)
     ap.add_argument("--cluster-n", type=int, default=1)
+    ap.add_argument("--tile-order", type=int, default=0)
+    ap.add_argument("--fp64", action="store_true", help="profile mode: the FP64 form")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--oracle-steps", type=int, default=2)
     args = ap.parse_args()
@@ -523,6 +552,8 @@ def main():
         return run_reference(args)
     if args.mode == "casimir":
         return run_casimir(args)
+    if args.mode == "profile":
+        return run_profile(args)
     if args.mode in ("ensemble", "serving"):
         import torch
 

@@ -232,6 +232,8 @@ __device__ __forceinline__ long long to_fixed(double x, int e, int sb) {
     return bits < 0 ? -v : v;
 }
 
+__device__ __noinline__ double fixed_to_double_slow(long long v, int E) { return ldexp((double)v, E); }
+
 // v * 2^E rounded to the nearest double (ties to even) with integer operations
 // only (the FP64 pipe is narrow); the same value as (double)v * 2^E.  Results
 // outside the normal range take the FP64 route.
@@ -256,7 +258,7 @@ __device__ __forceinline__ double fixed_to_double(long long v, int E) {
             }
         }
     }
-    if (ex < -1022 || ex > 1023) return ldexp((double)v, E);
+    if (ex < -1022 || ex > 1023) return fixed_to_double_slow(v, E);
     return __longlong_as_double(
         (long long)(sign | ((unsigned long long)(ex + 1023) << 52) | (m & ((1ull << 52) - 1))));
 }
@@ -659,15 +661,21 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
                         if (cb >= ncols) break;
                         const int lim = min(16, ncols - cb);   // even; a multiple of 4 when v32
                         long long v[16];
+                        // separate loops: a select between the two conversions would run the
+                        // 64-bit one (FP64 pipe) for every value
+                        if (fits32) {
 #pragma unroll
-                        for (int t = 0; t < 16; ++t) {
-                            const float f = __uint_as_float(r[16 * hh + t]);
-                            long long x = fits32 ? (long long)__float2int_rn(f) : __float2ll_rn(f);
-                            if (sh >= 0)
-                                x <<= sh;
-                            else
-                                x = (x + (1LL << (-sh - 1))) >> (-sh);
-                            v[t] = x;
+                            for (int t = 0; t < 16; ++t) v[t] = (long long)__float2int_rn(__uint_as_float(r[16 * hh + t]));
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) v[t] = __float2ll_rn(__uint_as_float(r[16 * hh + t]));
+                        }
+                        if (sh >= 0) {
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) v[t] <<= sh;
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) v[t] = (v[t] + (1LL << (-sh - 1))) >> (-sh);
                         }
                         long long* dst = Crow + cb;
                         if (!first) {   // add the accumulator (all loads first)
