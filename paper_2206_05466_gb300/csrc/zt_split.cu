@@ -58,7 +58,9 @@ constexpr int STAGE_BYTES = A_TILE + B_TILE;
 constexpr int NDRAIN = 256;        // drain / epilogue threads: 8 warps, two per TMEM lane quadrant
 constexpr int NTHREADS = 64 + NDRAIN;
 constexpr int MAX_S = 8;
-constexpr uint32_t TMEM_COLS = 512;  // two 128 x 256 FP32 accumulators
+constexpr int NBUF = 2;            // TMEM accumulator buffers per CTA (drain of one overlaps MMAs into the other)
+constexpr int CTAS_PER_SM = 1;     // resident CTAs per SM the launch bounds ask for
+constexpr uint32_t TMEM_COLS = NBUF * BN;   // 128 x 256 FP32 accumulators
 constexpr int MAX_KB = 512;        // K blocks of 64 for N <= 16384
 constexpr size_t SMEM_BYTES =
     1024 /*align slack*/ + (size_t)STAGES * STAGE_BYTES + 256 /*barriers*/ + 2 * MAX_KB /*digit occupancy*/;
@@ -190,6 +192,15 @@ __device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
             smem_u32(bar)),
         "h"(mask)
         : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
@@ -462,7 +473,7 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], cs);   // released by the MMA of every CTA that reads this stage's slices
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NBUF; ++i) {
             mbar_init(&accf[i], 1);
             mbar_init(&acce[i], NDRAIN);
         }
@@ -542,9 +553,10 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
                 for (int kb = 0; kb < nkb && ok; ++kb) {
                     for (int p = fa[kb]; p <= g - fb[kb]; ++p) {
                         if (!open) {   // next accumulation segment: wait for its TMEM buffer to be drained
-                            b = seg & 1;
+                            b = seg % NBUF;
+                            const int use = seg / NBUF;
                             ++seg;
-                            if (!mbar_wait(&acce[b], (((seg - 1) >> 1) & 1) ^ 1, abort_flag)) {
+                            if (!mbar_wait(&acce[b], (use & 1) ^ 1, abort_flag)) {
                                 ok = false;
                                 break;
                             }
@@ -640,35 +652,32 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
             const int nsegs = units == 0 ? 0 : (units - 1) / ulim + 1;
             const int sh = (a.s - 1 - g) * a.beta - a.u;
             for (int q = 0; q < nsegs; ++q) {
-                const int b = seg & 1;
+                const int b = seg % NBUF, use = seg / NBUF;
                 ++seg;
-                if (!mbar_wait(&accf[b], (((seg - 1) >> 1) & 1), abort_flag)) {
+                if (!mbar_wait(&accf[b], use & 1, abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const bool first = seg == 1, last = seg == total;
 #pragma unroll 1
-                for (int ch = 0; ch < BN / 64; ++ch) {
-                    const int col0 = half * (BN / 2) + ch * 32;
-                    uint32_t r[32];
-                    tmem_ld32(tmem + lane_base + (uint32_t)(b * BN + col0), r);
-                    const int cb0 = c0 + col0;
-                    if (!row_ok || cb0 >= ncols) continue;
-#pragma unroll
-                    for (int hh = 0; hh < 2; ++hh) {   // 16 columns at a time (register pressure)
-                        const int cb = cb0 + 16 * hh;
-                        if (cb >= ncols) break;
+                for (int ch = 0; ch < BN / 32; ++ch) {   // 16 columns at a time
+                    const int col0 = half * (BN / 2) + ch * 16;
+                    uint32_t r[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)(b * BN + col0), r);
+                    const int cb = c0 + col0;
+                    if (!row_ok || cb >= ncols) continue;
+                    {
                         const int lim = min(16, ncols - cb);   // even; a multiple of 4 when v32
                         long long v[16];
                         // separate loops: a select between the two conversions would run the
                         // 64-bit one (FP64 pipe) for every value
                         if (fits32) {
 #pragma unroll
-                            for (int t = 0; t < 16; ++t) v[t] = (long long)__float2int_rn(__uint_as_float(r[16 * hh + t]));
+                            for (int t = 0; t < 16; ++t) v[t] = (long long)__float2int_rn(__uint_as_float(r[t]));
                         } else {
 #pragma unroll
-                            for (int t = 0; t < 16; ++t) v[t] = __float2ll_rn(__uint_as_float(r[16 * hh + t]));
+                            for (int t = 0; t < 16; ++t) v[t] = __float2ll_rn(__uint_as_float(r[t]));
                         }
                         if (sh >= 0) {
 #pragma unroll
@@ -768,7 +777,7 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
     if (cs > 1) cluster_sync();
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS, CTAS_PER_SM)
 zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const SplitArgs a) {
     zgemm_split_body(&tmA, &tmB, a, blockIdx.x, false);
@@ -776,7 +785,7 @@ zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 
 // Grouped: instances (each with its own tensor maps in global memory) share one
 // cluster launch; every instance's CTA count is a multiple of the cluster size.
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(NTHREADS, CTAS_PER_SM)
 zgemm_split_grouped(const GemmEntry* tab, const int* offs, int n, int gate) {
     const int inst = zt_group_find(offs, n, blockIdx.x);
     const GemmEntry* e = tab + inst;
