@@ -62,6 +62,8 @@ typedef struct zt_tuning {
     int tile_order;      /* SPLIT launch order of output tiles: 0 (default) / 3 = column blocks of
                             8 / 16 tile groups, rows walked inside a block; 1 = row-major;
                             2 = tiles near the diagonal first */
+    int no_persistent;   /* SPLIT: 0 (default) = persistent product kernel (one CTA per SM working
+                            through the tiles) when clusters are 1x1; 1 = one tile per CTA */
 } zt_tuning;
 
 typedef struct zt_step_stats {

@@ -183,7 +183,9 @@ struct SplitArgs {     // tcgen05 split product (zt_split.cu)
     unsigned long long* units;   // if not NULL: += MMA units (128 x 256 x 64) issued by each CTA
     int cm, cn;        // cluster shape: cm row tiles share B'^T slices, cn column tiles share X' slices
     int ntmg, ntng;    // tile groups (one cluster each) along rows and columns
-    const int* order;  // launch order of tile groups (linear index tig * ntng + tjg), heaviest first
+    const int* order;  // launch order of tile groups (linear index tig * ntng + tjg)
+    int ngroups;       // tile groups of the launch
+    unsigned int* tickets;   // persistent form: tile ticket counter, zero at launch
     double alpha;
     const int* eA;
     const int* eB;

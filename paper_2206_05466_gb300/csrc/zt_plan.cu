@@ -598,6 +598,7 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         else if (!side(t.cluster_m) || !side(t.cluster_n) || t.cluster_m * t.cluster_n > 8)
             bad = "cluster sides must be 1, 2 or 4, at most 8 CTAs";
         else if (t.tile_order < 0 || t.tile_order > 3) bad = "tile_order outside [0, 3]";
+        else if (t.no_persistent != 0 && t.no_persistent != 1) bad = "no_persistent must be 0 or 1";
         if (bad) {
             delete p;
             return zt_fail(ZT_EINVAL, "zt_plan_create: %s", bad);

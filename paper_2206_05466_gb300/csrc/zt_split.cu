@@ -26,13 +26,18 @@
 //     added, shifted by its weight, into an int64 fixed-point accumulator
 //     held in the output buffer itself; the last step scales it back to FP64.
 //
-// Kernel structure (one 128 x 256 output tile per CTA, 192 threads):
+// Kernel structure (128 x 256 output tiles, 352 threads):
 //   warp 0  TMA producer: digit tiles (128 x 64 of X', 256 x 64 of B'^T,
 //           128-byte swizzle) into a 4-stage shared-memory ring;
 //   warp 1  TMEM allocation and the single MMA-issuing thread;
 //   warps 2-9  drain TMEM (double-buffered accumulator) into the int64
 //           accumulator, two warps per TMEM lane quadrant (128 columns
-//           each); the last drain of a tile adds, scales and stores FP64.
+//           each); the last drain of a tile adds, scales and stores FP64;
+//   warp 10 (persistent form) takes tiles from a ticket counter and fills
+//           the tile slots the other roles work through.
+// The persistent form (1x1 clusters) keeps one CTA per SM for the whole
+// launch, so one tile's last drain overlaps the next tile's MMAs; the
+// one-tile-per-CTA form serves thread-block clusters and grouped launches.
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the kernel
 // records a timeout in the step state, lets in-flight work retire and exits.
 #include <cuda.h>
@@ -56,14 +61,12 @@ constexpr int A_TILE = BM * BK * 2;
 constexpr int B_TILE = BN * BK * 2;
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
 constexpr int NDRAIN = 256;        // drain / epilogue threads: 8 warps, two per TMEM lane quadrant
-constexpr int NTHREADS = 64 + NDRAIN;
+constexpr int NTHREADS = 64 + NDRAIN + 32;   // + producer, MMA and scheduler warps
 constexpr int MAX_S = 8;
 constexpr int NBUF = 2;            // TMEM accumulator buffers per CTA (drain of one overlaps MMAs into the other)
 constexpr int CTAS_PER_SM = 1;     // resident CTAs per SM the launch bounds ask for
 constexpr uint32_t TMEM_COLS = NBUF * BN;   // 128 x 256 FP32 accumulators
 constexpr int MAX_KB = 512;        // K blocks of 64 for N <= 16384
-constexpr size_t SMEM_BYTES =
-    1024 /*align slack*/ + (size_t)STAGES * STAGE_BYTES + 256 /*barriers*/ + 2 * MAX_KB /*digit occupancy*/;
 constexpr int EXP_NAN = 0x7fff;    // row exponent marking a non-finite entry
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
 
@@ -85,6 +88,9 @@ struct zt_split_ws {
     int* order_lower = nullptr;
     int n_full = 0, n_lower = 0;
     int skip_zero = 1;                           // skip digit-pair units whose tiles are all zero
+    int persistent = 1;                          // persistent product kernel (1x1 clusters only)
+    int nsm = 0;                                 // SMs of the device
+    unsigned int* tickets = nullptr;             // tile ticket counter of the persistent kernel
     int* occA = nullptr;                         // [ngA][nkb]
     int* occB[2] = {nullptr, nullptr};           // [ngB][nkb]
     CUtensorMap tmA, tmB[2];
@@ -414,357 +420,333 @@ __device__ __forceinline__ int seg_units(int g, int beta, int exact_groups) {
 // ---------------------------------------------------------------------------
 // The tcgen05 product kernel.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const CUtensorMap* tmB_p,
-                                                 const SplitArgs& a, int bid, bool global_maps) {
-    if (zt_gate_skip(a.st, a.gate)) return;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = base;
-    uint8_t* sB = base + STAGES * A_TILE;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_TILE);
-    uint64_t* empty = full + STAGES;
-    uint64_t* accf = empty + STAGES;   // [2]
-    uint64_t* acce = accf + 2;         // [2]
-    uint64_t* drain = acce + 2;        // [1]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    int* gunits = reinterpret_cast<int*>(tmem_slot + 2);     // [MAX_S] active units per digit group
-    uint8_t* fa = reinterpret_cast<uint8_t*>(full) + 256;   // [MAX_KB] first nonzero X' digit per K block
-    uint8_t* fb = fa + MAX_KB;                               // [MAX_KB] first nonzero B'^T digit
-
-    // Tile coordinates.  A cluster of cm x cn CTAs owns a group of cm row
-    // tiles and cn column tiles; CTA rank r sits at (r % cm, r / cm).
-    const int cs = a.cm * a.cn;
-    const int rank = cs > 1 ? (int)cluster_ctarank() : 0;
-    const int grp = bid / cs;
+// Per-tile data shared by the roles: tile-group coordinates, digit occupancy of
+// the group's rows of X' (fa) and B'^T (fb) per K block, active units per digit
+// group and the number of accumulation segments of the tile.
+struct TileSlot {
+    int valid;   // 0: no further tile (persistent kernel)
     int tig, tjg;
+    int total;
+    int gunits[MAX_S];
+    uint8_t fa[MAX_KB];   // the unit (p, q, kb) is all zero unless p >= fa[kb] and q >= fb[kb]
+    uint8_t fb[MAX_KB];
+};
+constexpr int TSLOTS = 2;   // tile slots of the persistent kernel (one being worked, one being filled)
+constexpr size_t SMEM_BYTES = 1024 /*align slack*/ + (size_t)STAGES * STAGE_BYTES + 256 /*barriers*/ +
+                              TSLOTS * sizeof(TileSlot);
+
+struct SmemMap {
+    uint8_t* sA;
+    uint8_t* sB;
+    uint64_t* full;     // [STAGES] operand stage loaded
+    uint64_t* empty;    // [STAGES] operand stage consumed
+    uint64_t* accf;     // [NBUF] accumulator segment complete
+    uint64_t* acce;     // [NBUF] accumulator buffer drained
+    uint64_t* tfull;    // [TSLOTS] tile slot filled
+    uint64_t* tempty;   // [TSLOTS] tile slot released
+    uint64_t* drain;    // all MMAs retired
+    uint32_t* tmem_slot;
+    volatile int* abort_flag;
+    TileSlot* slots;
+};
+
+__device__ __forceinline__ SmemMap smem_map() {
+    extern __shared__ uint8_t smem_raw[];
+    SmemMap m;
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    m.sA = base;
+    m.sB = base + STAGES * A_TILE;
+    m.full = reinterpret_cast<uint64_t*>(m.sB + STAGES * B_TILE);
+    m.empty = m.full + STAGES;
+    m.accf = m.empty + STAGES;
+    m.acce = m.accf + NBUF;
+    m.tfull = m.acce + NBUF;
+    m.tempty = m.tfull + TSLOTS;
+    m.drain = m.tempty + TSLOTS;
+    m.tmem_slot = reinterpret_cast<uint32_t*>(m.drain + 1);
+    m.abort_flag = reinterpret_cast<volatile int*>(m.tmem_slot + 1);
+    m.slots = reinterpret_cast<TileSlot*>(reinterpret_cast<uint8_t*>(m.full) + 256);
+    return m;
+}
+
+// Tile group of a linear launch index; false when the group has no element in
+// the requested (lower) triangle.
+__device__ __forceinline__ bool tile_group(const SplitArgs& a, int grp, int& tig, int& tjg) {
     if (a.order) {   // explicit order (only groups that have work are listed)
         const int gl = a.order[grp];
         tig = gl / a.ntng;
         tjg = gl % a.ntng;
-    } else if (a.lower_only && a.cm == a.cn) {   // groups on or below the diagonal, triangular order
+        return true;
+    }
+    if (a.lower_only && a.cm == a.cn) {   // groups on or below the diagonal, triangular order
         int r = (int)((sqrtf(8.0f * grp + 1.0f) - 1.0f) * 0.5f);
         while (r * (r + 1) / 2 > grp) --r;
         while ((r + 1) * (r + 2) / 2 <= grp) ++r;
         tig = r;
         tjg = grp - r * (r + 1) / 2;
-    } else {
-        tig = grp / a.ntng;
-        tjg = grp % a.ntng;
-        // a group strictly above the diagonal has no lower-triangle element (whole cluster leaves)
-        if (a.lower_only && tjg * a.cn >= (tig + 1) * a.cm) return;
+        return true;
     }
-    const int rm = rank % a.cm, rn = rank / a.cm;
-    const int ti = tig * a.cm + rm, tj = tjg * a.cn + rn;
-    const int i0 = ti * BM, c0 = tj * BN;
-    // each CTA fetches one slice of its X' tile (shared along the cluster row)
-    // and one slice of its B'^T tile (shared along the cluster column)
-    const int a_rows = BM / a.cn, b_rows = BN / a.cm;
-    const int a_off = rn * a_rows, b_off = rm * b_rows;
-    uint16_t mask_a = 0, mask_b = 0;
-    for (int n2 = 0; n2 < a.cn; ++n2) mask_a |= (uint16_t)(1u << (rm + a.cm * n2));
-    for (int m2 = 0; m2 < a.cm; ++m2) mask_b |= (uint16_t)(1u << (m2 + a.cm * rn));
-    const uint16_t mask_all = (uint16_t)((1u << cs) - 1u);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nkb = a.ldk / BK;
+    tig = grp / a.ntng;
+    tjg = grp % a.ntng;
+    return !(a.lower_only && tjg * a.cn >= (tig + 1) * a.cm);
+}
 
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], cs);   // released by the MMA of every CTA that reads this stage's slices
+// One warp fills a tile slot: occupancy, active units per group, segments.
+__device__ __forceinline__ void fill_slot_warp(const SplitArgs& a, TileSlot& ts, int tig, int tjg, int nkb, int lane) {
+    int u[MAX_S];
+#pragma unroll
+    for (int g = 0; g < MAX_S; ++g) u[g] = 0;
+    for (int kb = lane; kb < nkb; kb += 32) {
+        const int fa = a.occA ? a.s - a.occA[(size_t)tig * nkb + kb] : 0;
+        const int fb = a.occB ? a.s - a.occB[(size_t)tjg * nkb + kb] : 0;
+        ts.fa[kb] = (uint8_t)fa;
+        ts.fb[kb] = (uint8_t)fb;
+        const int c = fa + fb;
+#pragma unroll
+        for (int g = 0; g < MAX_S; ++g) u[g] += max(0, g - c + 1);
+    }
+    int total = 0;
+#pragma unroll
+    for (int g = 0; g < MAX_S; ++g) {
+        int v = u[g];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (g < a.s) {
+            if (lane == 0) ts.gunits[g] = v;
+            total += v == 0 ? 0 : (v - 1) / seg_units(g, a.beta, a.exact_groups) + 1;
         }
-        for (int i = 0; i < NBUF; ++i) {
-            mbar_init(&accf[i], 1);
-            mbar_init(&acce[i], NDRAIN);
-        }
-        mbar_init(drain, 1);
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (lane == 0) {
+        ts.tig = tig;
+        ts.tjg = tjg;
+        ts.total = total;
+        ts.valid = 1;
     }
-    // Digit occupancy of this cluster's row group (X') and column group (B'^T):
-    // the unit (p, q, kb) is all zero unless p >= fa[kb] and q >= fb[kb].
-    for (int kb = threadIdx.x; kb < nkb; kb += NTHREADS) {
-        fa[kb] = a.occA ? (uint8_t)(a.s - a.occA[(size_t)tig * nkb + kb]) : 0;
-        fb[kb] = a.occB ? (uint8_t)(a.s - a.occB[(size_t)tjg * nkb + kb]) : 0;
-    }
-    tc_fence_before();
-    if (cs > 1)
-        cluster_sync();   // peers' barriers exist before any multicast lands
-    else
-        __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
+    __threadfence_block();
+    __syncwarp();
+}
 
-    if (warp == 0) {
-        if (lane == 0) {   // ---- TMA producer ----
-            if (global_maps) {   // maps written by the host: visible to the tensormap proxy before use
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmA_p) : "memory");
-                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmB_p) : "memory");
-            }
-            int stage = 0;
-            uint32_t ph = 0;
-            bool ok = true;
-            for (int g = 0; g < a.s && ok; ++g) {
-                {
-                    for (int kb = 0; kb < nkb && ok; ++kb) {
-                        for (int p = fa[kb]; p <= g - fb[kb]; ++p) {
-                            if (!mbar_wait(&empty[stage], ph ^ 1, abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                            mbar_expect_tx(&full[stage], STAGE_BYTES);
-                            uint8_t* dA = sA + stage * A_TILE + a_off * 128;
-                            uint8_t* dB = sB + stage * B_TILE + b_off * 128;
-                            const int ya = p * a.Mpad + i0 + a_off, yb = (g - p) * a.Npad + c0 + b_off;
-                            if (a.cn > 1)
-                                tma_load_2d_mc(dA, tmA_p, &full[stage], kb * BK, ya, mask_a);
-                            else
-                                tma_load_2d(dA, tmA_p, &full[stage], kb * BK, ya);
-                            if (a.cm > 1)
-                                tma_load_2d_mc(dB, tmB_p, &full[stage], kb * BK, yb, mask_b);
-                            else
-                                tma_load_2d(dB, tmB_p, &full[stage], kb * BK, yb);
-                            if (++stage == STAGES) {
-                                stage = 0;
-                                ph ^= 1;
-                            }
-                        }
-                    }
+// ---- TMA producer (one thread): digit tiles of every active unit of the tile ----
+__device__ __forceinline__ bool produce_tile(const SplitArgs& a, const TileSlot& ts, const SmemMap& m,
+                                             const CUtensorMap* tmA_p, const CUtensorMap* tmB_p, int i0, int c0,
+                                             int a_off, int b_off, uint16_t mask_a, uint16_t mask_b, int nkb,
+                                             int& stage, uint32_t& ph) {
+    for (int g = 0; g < a.s; ++g)
+        for (int kb = 0; kb < nkb; ++kb)
+            for (int p = ts.fa[kb]; p <= g - ts.fb[kb]; ++p) {
+                if (!mbar_wait(&m.empty[stage], ph ^ 1, m.abort_flag)) return false;
+                mbar_expect_tx(&m.full[stage], STAGE_BYTES);
+                uint8_t* dA = m.sA + stage * A_TILE + a_off * 128;
+                uint8_t* dB = m.sB + stage * B_TILE + b_off * 128;
+                const int ya = p * a.Mpad + i0 + a_off, yb = (g - p) * a.Npad + c0 + b_off;
+                if (a.cn > 1)
+                    tma_load_2d_mc(dA, tmA_p, &m.full[stage], kb * BK, ya, mask_a);
+                else
+                    tma_load_2d(dA, tmA_p, &m.full[stage], kb * BK, ya);
+                if (a.cm > 1)
+                    tma_load_2d_mc(dB, tmB_p, &m.full[stage], kb * BK, yb, mask_b);
+                else
+                    tma_load_2d(dB, tmB_p, &m.full[stage], kb * BK, yb);
+                if (++stage == STAGES) {
+                    stage = 0;
+                    ph ^= 1;
                 }
             }
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {   // ---- MMA issuer ----
-            int stage = 0, seg = 0;
-            unsigned long long issued = 0;
-            uint32_t ph = 0;
-            bool ok = true;
-            for (int g = 0; g < a.s && ok; ++g) {
-                const int ulim = seg_units(g, a.beta, a.exact_groups);
-                int cnt = 0, b = 0;
-                bool open = false;
-                uint32_t d = 0;
-                for (int kb = 0; kb < nkb && ok; ++kb) {
-                    for (int p = fa[kb]; p <= g - fb[kb]; ++p) {
-                        if (!open) {   // next accumulation segment: wait for its TMEM buffer to be drained
-                            b = seg % NBUF;
-                            const int use = seg / NBUF;
-                            ++seg;
-                            if (!mbar_wait(&acce[b], (use & 1) ^ 1, abort_flag)) {
-                                ok = false;
-                                break;
-                            }
-                            tc_fence_after();
-                            d = tmem + (uint32_t)(b * BN);
-                            open = true;
-                            cnt = 0;
-                        }
-                        if (!mbar_wait(&full[stage], ph, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint64_t ad = sw128_desc(smem_u32(sA + stage * A_TILE));
-                        const uint64_t bd = sw128_desc(smem_u32(sB + stage * B_TILE));
-#pragma unroll
-                        for (int k = 0; k < BK / 16; ++k)
-                            umma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (cnt == 0 && k == 0) ? 0u : 1u);
-                        ++cnt;
-                        ++issued;
-                        if (cs > 1)
-                            umma_commit_mc(&empty[stage], mask_all);
-                        else
-                            umma_commit(&empty[stage]);
-                        if (++stage == STAGES) {
-                            stage = 0;
-                            ph ^= 1;
-                        }
-                        if (cnt == ulim) {   // exactness budget of this segment used up
-                            umma_commit(&accf[b]);
-                            open = false;
-                        }
-                    }
+    return true;
+}
+
+// ---- MMA issuer (one thread): one accumulation segment per exactness budget ----
+// stage/ph/seg continue from tile to tile; seg numbers the accumulator buffers.
+__device__ __forceinline__ bool mma_tile(const SplitArgs& a, const TileSlot& ts, const SmemMap& m, uint32_t tmem,
+                                         int nkb, int cs, uint16_t mask_all, int& stage, uint32_t& ph, int& seg,
+                                         unsigned long long& issued) {
+    for (int g = 0; g < a.s; ++g) {
+        const int ulim = seg_units(g, a.beta, a.exact_groups);
+        int cnt = 0, b = 0;
+        bool open = false;
+        uint32_t d = 0;
+        for (int kb = 0; kb < nkb; ++kb) {
+            for (int p = ts.fa[kb]; p <= g - ts.fb[kb]; ++p) {
+                if (!open) {   // next accumulation segment: wait for its TMEM buffer to be drained
+                    b = seg % NBUF;
+                    const int use = seg / NBUF;
+                    ++seg;
+                    if (!mbar_wait(&m.acce[b], (use & 1) ^ 1, m.abort_flag)) return false;
+                    tc_fence_after();
+                    d = tmem + (uint32_t)(b * BN);
+                    open = true;
+                    cnt = 0;
                 }
-                if (ok && open) umma_commit(&accf[b]);
-            }
-            if (a.units) atomicAdd(a.units, issued);
-            // all MMAs issued by this thread retire before TMEM is released
-            umma_commit(drain);
-            volatile int dummy = 0;
-            if (!mbar_wait(drain, 0, &dummy)) *abort_flag = 1;
-        }
-    } else {   // ---- drain / epilogue: warps 2..9 ----
-        const int wq = warp & 3;                 // TMEM lane quadrant this warp may access
-        const int half = (warp - 2) >> 2;        // column half of the tile this warp drains
-        const int dt = threadIdx.x - 64;         // 0 .. NDRAIN-1
-        const int gi = i0 + wq * 32 + lane;
-        const bool row_ok = gi < a.N;
-        const int ncols = 2 * a.N;
-        const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
-        long long* Crow = reinterpret_cast<long long*>(a.C) + (size_t)gi * ncols;
-        // active units of every digit group on this tile, counted once
-        if (dt < MAX_S) gunits[dt] = 0;
-        drain_bar();
-        {
-            int u[MAX_S];
-#pragma unroll
-            for (int g = 0; g < MAX_S; ++g) u[g] = 0;
-            for (int kb = dt; kb < nkb; kb += NDRAIN) {
-                const int c = fa[kb] + fb[kb];
-#pragma unroll
-                for (int g = 0; g < MAX_S; ++g) u[g] += max(0, g - c + 1);
-            }
-#pragma unroll
-            for (int g = 0; g < MAX_S; ++g) {
-                int v = u[g];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0 && g < a.s && v) atomicAdd(&gunits[g], v);
-            }
-        }
-        drain_bar();
-        int total = 0;
-        for (int g = 0; g < a.s; ++g) {
-            const int ulim = seg_units(g, a.beta, a.exact_groups);
-            total += gunits[g] == 0 ? 0 : (gunits[g] - 1) / ulim + 1;
-        }
-        // FP32 segment sums are integers below 2^31 unless K' and the digits are large
-        const bool fits32 = (double)a.s * (double)ncols * (double)(1LL << (2 * a.beta - 2)) < 2147483647.0;
-        const bool v32 = (a.N & 1) == 0 && ((uintptr_t)a.C & 31) == 0;   // rows start on 32-byte boundaries
-        const int ea = row_ok ? a.eA[gi] : 0;
-        const int eoff = -(a.s + 1) * a.beta + 2 + a.u;
-        // alpha = +-2^k (the usual +-1) folds into the exponent and the sign
-        const long long abits = __double_as_longlong(a.alpha);
-        const int aef = (int)((abits >> 52) & 0x7FF);
-        const bool apow2 = (abits & 0xFFFFFFFFFFFFFLL) == 0 && aef != 0 && aef != 0x7FF;
-        const int aexp = apow2 ? aef - 1023 : 0;
-        const unsigned long long asign = apow2 ? ((unsigned long long)abits & 0x8000000000000000ull) : 0ull;
-        int seg = 0;
-        bool ok = true;
-        for (int g = 0; g < a.s && ok; ++g) {
-            const int ulim = seg_units(g, a.beta, a.exact_groups);
-            const int units = gunits[g];
-            const int nsegs = units == 0 ? 0 : (units - 1) / ulim + 1;
-            const int sh = (a.s - 1 - g) * a.beta - a.u;
-            for (int q = 0; q < nsegs; ++q) {
-                const int b = seg % NBUF, use = seg / NBUF;
-                ++seg;
-                if (!mbar_wait(&accf[b], use & 1, abort_flag)) {
-                    ok = false;
-                    break;
-                }
+                if (!mbar_wait(&m.full[stage], ph, m.abort_flag)) return false;
                 tc_fence_after();
-                const bool first = seg == 1, last = seg == total;
+                const uint64_t ad = sw128_desc(smem_u32(m.sA + stage * A_TILE));
+                const uint64_t bd = sw128_desc(smem_u32(m.sB + stage * B_TILE));
+#pragma unroll
+                for (int k = 0; k < BK / 16; ++k)
+                    umma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (cnt == 0 && k == 0) ? 0u : 1u);
+                ++cnt;
+                ++issued;
+                if (cs > 1)
+                    umma_commit_mc(&m.empty[stage], mask_all);
+                else
+                    umma_commit(&m.empty[stage]);
+                if (++stage == STAGES) {
+                    stage = 0;
+                    ph ^= 1;
+                }
+                if (cnt == ulim) {   // exactness budget of this segment used up
+                    umma_commit(&m.accf[b]);
+                    open = false;
+                }
+            }
+        }
+        if (open) umma_commit(&m.accf[b]);
+    }
+    return true;
+}
+
+// ---- drain / epilogue (the 8 drain warps): every segment of the tile into the
+// int64 accumulator held in C; the tile's last segment adds, scales and stores
+// FP64 in place.  seg continues from tile to tile.
+__device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& ts, const SmemMap& m, uint32_t tmem,
+                                           int i0, int c0, int warp, int lane, int& seg) {
+    const int wq = warp & 3;                 // TMEM lane quadrant this warp may access
+    const int half = (warp - 2) >> 2;        // column half of the tile this warp drains
+    const int gi = i0 + wq * 32 + lane;
+    const bool row_ok = gi < a.N;
+    const int ncols = 2 * a.N;
+    const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
+    long long* Crow = reinterpret_cast<long long*>(a.C) + (size_t)gi * ncols;
+    const int total = ts.total;
+    // FP32 segment sums are integers below 2^31 unless K' and the digits are large
+    const bool fits32 = (double)a.s * (double)ncols * (double)(1LL << (2 * a.beta - 2)) < 2147483647.0;
+    const bool v32 = (a.N & 1) == 0 && ((uintptr_t)a.C & 31) == 0;   // rows start on 32-byte boundaries
+    const int ea = row_ok ? a.eA[gi] : 0;
+    const int eoff = -(a.s + 1) * a.beta + 2 + a.u;
+    // alpha = +-2^k (the usual +-1) folds into the exponent and the sign
+    const long long abits = __double_as_longlong(a.alpha);
+    const int aef = (int)((abits >> 52) & 0x7FF);
+    const bool apow2 = (abits & 0xFFFFFFFFFFFFFLL) == 0 && aef != 0 && aef != 0x7FF;
+    const int aexp = apow2 ? aef - 1023 : 0;
+    const unsigned long long asign = apow2 ? ((unsigned long long)abits & 0x8000000000000000ull) : 0ull;
+    int tseg = 0;   // segments of this tile drained so far
+    for (int g = 0; g < a.s; ++g) {
+        const int ulim = seg_units(g, a.beta, a.exact_groups);
+        const int units = ts.gunits[g];
+        const int nsegs = units == 0 ? 0 : (units - 1) / ulim + 1;
+        const int sh = (a.s - 1 - g) * a.beta - a.u;
+        for (int q = 0; q < nsegs; ++q) {
+            const int b = seg % NBUF, use = seg / NBUF;
+            ++seg;
+            if (!mbar_wait(&m.accf[b], use & 1, m.abort_flag)) return false;
+            tc_fence_after();
+            const bool first = tseg == 0, last = tseg == total - 1;
+            ++tseg;
 #pragma unroll 1
-                for (int ch = 0; ch < BN / 32; ++ch) {   // 16 columns at a time
-                    const int col0 = half * (BN / 2) + ch * 16;
-                    uint32_t r[16];
-                    tmem_ld16(tmem + lane_base + (uint32_t)(b * BN + col0), r);
-                    const int cb = c0 + col0;
-                    if (!row_ok || cb >= ncols) continue;
-                    {
-                        const int lim = min(16, ncols - cb);   // even; a multiple of 4 when v32
-                        long long v[16];
-                        // separate loops: a select between the two conversions would run the
-                        // 64-bit one (FP64 pipe) for every value
-                        if (fits32) {
+            for (int ch = 0; ch < BN / 32; ++ch) {   // 16 columns at a time
+                const int col0 = half * (BN / 2) + ch * 16;
+                uint32_t r[16];
+                tmem_ld16(tmem + lane_base + (uint32_t)(b * BN + col0), r);
+                const int cb = c0 + col0;
+                if (!row_ok || cb >= ncols) continue;
+                const int lim = min(16, ncols - cb);   // even; a multiple of 4 when v32
+                long long v[16];
+                // separate loops: a select between the two conversions would run the
+                // 64-bit one (FP64 pipe) for every value
+                if (fits32) {
 #pragma unroll
-                            for (int t = 0; t < 16; ++t) v[t] = (long long)__float2int_rn(__uint_as_float(r[t]));
-                        } else {
+                    for (int t = 0; t < 16; ++t) v[t] = (long long)__float2int_rn(__uint_as_float(r[t]));
+                } else {
 #pragma unroll
-                            for (int t = 0; t < 16; ++t) v[t] = __float2ll_rn(__uint_as_float(r[t]));
+                    for (int t = 0; t < 16; ++t) v[t] = __float2ll_rn(__uint_as_float(r[t]));
+                }
+                if (sh >= 0) {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) v[t] <<= sh;
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) v[t] = (v[t] + (1LL << (-sh - 1))) >> (-sh);
+                }
+                long long* dst = Crow + cb;
+                if (!first) {   // add the accumulator (all loads first)
+                    long long o[16];
+                    if (v32) {
+#pragma unroll
+                        for (int t = 0; t < 16; t += 4) {
+                            if (t < lim)
+                                asm volatile("ld.global.v4.b64 {%0,%1,%2,%3}, [%4];"
+                                             : "=l"(o[t]), "=l"(o[t + 1]), "=l"(o[t + 2]), "=l"(o[t + 3])
+                                             : "l"(dst + t));
+                            else
+                                o[t] = o[t + 1] = o[t + 2] = o[t + 3] = 0;
                         }
-                        if (sh >= 0) {
+                    } else {
 #pragma unroll
-                            for (int t = 0; t < 16; ++t) v[t] <<= sh;
-                        } else {
-#pragma unroll
-                            for (int t = 0; t < 16; ++t) v[t] = (v[t] + (1LL << (-sh - 1))) >> (-sh);
-                        }
-                        long long* dst = Crow + cb;
-                        if (!first) {   // add the accumulator (all loads first)
-                            long long o[16];
-                            if (v32) {
-#pragma unroll
-                                for (int t = 0; t < 16; t += 4) {
-                                    if (t < lim)
-                                        asm volatile("ld.global.v4.b64 {%0,%1,%2,%3}, [%4];"
-                                                     : "=l"(o[t]), "=l"(o[t + 1]), "=l"(o[t + 2]), "=l"(o[t + 3])
-                                                     : "l"(dst + t));
-                                    else
-                                        o[t] = o[t + 1] = o[t + 2] = o[t + 3] = 0;
-                                }
+                        for (int t = 0; t < 16; t += 2) {
+                            if (t < lim) {
+                                const longlong2 w = *reinterpret_cast<const longlong2*>(dst + t);
+                                o[t] = w.x;
+                                o[t + 1] = w.y;
                             } else {
-#pragma unroll
-                                for (int t = 0; t < 16; t += 2) {
-                                    if (t < lim) {
-                                        const longlong2 w = *reinterpret_cast<const longlong2*>(dst + t);
-                                        o[t] = w.x;
-                                        o[t + 1] = w.y;
-                                    } else {
-                                        o[t] = o[t + 1] = 0;
-                                    }
-                                }
-                            }
-#pragma unroll
-                            for (int t = 0; t < 16; ++t) v[t] += o[t];
-                        }
-                        if (last) {   // int64 fixed point -> FP64, in place
-#pragma unroll
-                            for (int t = 0; t < 16; t += 4) {
-                                if (t >= lim) break;
-                                const int4 eb4 = *reinterpret_cast<const int4*>(a.eB + cb + t);
-                                const int ebv[4] = {eb4.x, eb4.y, eb4.z, eb4.w};
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) {
-                                    double out;
-                                    if (ea == EXP_NAN || ebv[k] == EXP_NAN) {
-                                        out = __longlong_as_double(0x7ff8000000000000LL);
-                                    } else {
-                                        out = fixed_to_double(v[t + k], ea + ebv[k] + eoff + aexp);
-                                        out = __longlong_as_double(__double_as_longlong(out) ^ (long long)asign);
-                                        if (!apow2) out *= a.alpha;
-                                    }
-                                    v[t + k] = __double_as_longlong(out);
-                                }
+                                o[t] = o[t + 1] = 0;
                             }
                         }
-                        if (v32) {
+                    }
 #pragma unroll
-                            for (int t = 0; t < 16; t += 4)
-                                if (t < lim)
-                                    asm volatile("st.global.v4.b64 [%0], {%1,%2,%3,%4};" ::"l"(dst + t), "l"(v[t]),
-                                                 "l"(v[t + 1]), "l"(v[t + 2]), "l"(v[t + 3])
-                                                 : "memory");
-                        } else {
+                    for (int t = 0; t < 16; ++t) v[t] += o[t];
+                }
+                if (last) {   // int64 fixed point -> FP64, in place
 #pragma unroll
-                            for (int t = 0; t < 16; t += 2)
-                                if (t < lim) *reinterpret_cast<longlong2*>(dst + t) = make_longlong2(v[t], v[t + 1]);
+                    for (int t = 0; t < 16; t += 4) {
+                        if (t >= lim) break;
+                        const int4 eb4 = *reinterpret_cast<const int4*>(a.eB + cb + t);
+                        const int ebv[4] = {eb4.x, eb4.y, eb4.z, eb4.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            double out;
+                            if (ea == EXP_NAN || ebv[k] == EXP_NAN) {
+                                out = __longlong_as_double(0x7ff8000000000000LL);
+                            } else {
+                                out = fixed_to_double(v[t + k], ea + ebv[k] + eoff + aexp);
+                                out = __longlong_as_double(__double_as_longlong(out) ^ (long long)asign);
+                                if (!apow2) out *= a.alpha;
+                            }
+                            v[t + k] = __double_as_longlong(out);
                         }
                     }
                 }
-                tc_fence_before();
-                mbar_arrive(&acce[b]);
+                if (v32) {
+#pragma unroll
+                    for (int t = 0; t < 16; t += 4)
+                        if (t < lim)
+                            asm volatile("st.global.v4.b64 [%0], {%1,%2,%3,%4};" ::"l"(dst + t), "l"(v[t]),
+                                         "l"(v[t + 1]), "l"(v[t + 2]), "l"(v[t + 3])
+                                         : "memory");
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 16; t += 2)
+                        if (t < lim) *reinterpret_cast<longlong2*>(dst + t) = make_longlong2(v[t], v[t + 1]);
+                }
             }
-        }
-        if (ok && total == 0 && row_ok) {   // every digit product of the tile is zero
-            const int cbeg = c0 + half * (BN / 2);
-            for (int c = cbeg; c < cbeg + BN / 2 && c < ncols; ++c) {
-                const bool nan = ea == EXP_NAN || a.eB[c] == EXP_NAN;
-                reinterpret_cast<double*>(Crow)[c] = nan ? __longlong_as_double(0x7ff8000000000000LL) : 0.0;
-            }
+            tc_fence_before();
+            mbar_arrive(&m.acce[b]);
         }
     }
+    if (total == 0 && row_ok) {   // every digit product of the tile is zero
+        const int cbeg = c0 + half * (BN / 2);
+        for (int c = cbeg; c < cbeg + BN / 2 && c < ncols; ++c) {
+            const bool nan = ea == EXP_NAN || a.eB[c] == EXP_NAN;
+            reinterpret_cast<double*>(Crow)[c] = nan ? __longlong_as_double(0x7ff8000000000000LL) : 0.0;
+        }
+    }
+    return true;
+}
 
+// Teardown shared by both kernels: on a timeout the CTA records it, gives
+// copies in flight time to land, frees TMEM and leaves.
+__device__ __forceinline__ void split_teardown(const SplitArgs& a, const SmemMap& m, uint32_t tmem, int warp, int cs) {
     __syncthreads();
-    if (*abort_flag) {
+    if (*m.abort_flag) {
         if (threadIdx.x == 0) atomicExch(&a.st->timeout, 1);
-        // give copies still in flight time to land before the CTA exits
         const unsigned long long t0 = gtimer();
         while (gtimer() - t0 < 200000ull) {
         }
@@ -777,10 +759,198 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
     if (cs > 1) cluster_sync();
 }
 
+__device__ __forceinline__ void tmem_alloc_warp(const SmemMap& m) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(m.tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// One output tile (cluster group) per CTA; clusters share operand slices by
+// TMA multicast.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const CUtensorMap* tmB_p,
+                                                 const SplitArgs& a, int bid, bool global_maps) {
+    if (zt_gate_skip(a.st, a.gate)) return;
+    const SmemMap m = smem_map();
+    TileSlot& ts = m.slots[0];
+
+    // A cluster of cm x cn CTAs owns a group of cm row tiles and cn column
+    // tiles; CTA rank r sits at (r % cm, r / cm).
+    const int cs = a.cm * a.cn;
+    const int rank = cs > 1 ? (int)cluster_ctarank() : 0;
+    int tig, tjg;
+    if (!tile_group(a, bid / cs, tig, tjg)) return;   // whole cluster leaves
+    const int rm = rank % a.cm, rn = rank / a.cm;
+    const int ti = tig * a.cm + rm, tj = tjg * a.cn + rn;
+    const int i0 = ti * BM, c0 = tj * BN;
+    // each CTA fetches one slice of its X' tile (shared along the cluster row)
+    // and one slice of its B'^T tile (shared along the cluster column)
+    const int a_off = rn * (BM / a.cn), b_off = rm * (BN / a.cm);
+    uint16_t mask_a = 0, mask_b = 0;
+    for (int n2 = 0; n2 < a.cn; ++n2) mask_a |= (uint16_t)(1u << (rm + a.cm * n2));
+    for (int m2 = 0; m2 < a.cm; ++m2) mask_b |= (uint16_t)(1u << (m2 + a.cm * rn));
+    const uint16_t mask_all = (uint16_t)((1u << cs) - 1u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkb = a.ldk / BK;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&m.full[i], 1);
+            mbar_init(&m.empty[i], cs);   // released by the MMA of every CTA that reads this stage's slices
+        }
+        for (int i = 0; i < NBUF; ++i) {
+            mbar_init(&m.accf[i], 1);
+            mbar_init(&m.acce[i], NDRAIN);
+        }
+        mbar_init(m.drain, 1);
+        *m.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc_warp(m);
+    if (warp == 2) fill_slot_warp(a, ts, tig, tjg, nkb, lane);
+    tc_fence_before();
+    if (cs > 1)
+        cluster_sync();   // peers' barriers exist before any multicast lands
+    else
+        __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *m.tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            if (global_maps) {   // maps written by the host: visible to the tensormap proxy before use
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmA_p) : "memory");
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmB_p) : "memory");
+            }
+            int stage = 0;
+            uint32_t ph = 0;
+            produce_tile(a, ts, m, tmA_p, tmB_p, i0, c0, a_off, b_off, mask_a, mask_b, nkb, stage, ph);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0, seg = 0;
+            uint32_t ph = 0;
+            unsigned long long issued = 0;
+            mma_tile(a, ts, m, tmem, nkb, cs, mask_all, stage, ph, seg, issued);
+            if (a.units) atomicAdd(a.units, issued);
+            // all MMAs issued by this thread retire before TMEM is released
+            umma_commit(m.drain);
+            volatile int dummy = 0;
+            if (!mbar_wait(m.drain, 0, &dummy)) *m.abort_flag = 1;
+        }
+    } else if (warp < 2 + NDRAIN / 32) {
+        int seg = 0;
+        drain_tile(a, ts, m, tmem, i0, c0, warp, lane, seg);
+    }
+    split_teardown(a, m, tmem, warp, cs);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form (1x1 clusters): one CTA per SM works through the launch
+// order, taking tile groups from a ticket counter (zeroed by the host before
+// every launch).  A scheduler warp fills a ring of tile slots ahead of the
+// roles, and the accumulator buffers rotate across tiles, so the last drain
+// and the FP64 epilogue of one tile overlap the first MMAs of the next.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void zgemm_split_persistent_body(const CUtensorMap* tmA_p, const CUtensorMap* tmB_p,
+                                                            const SplitArgs& a) {
+    if (zt_gate_skip(a.st, a.gate)) return;
+    const SmemMap m = smem_map();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nkb = a.ldk / BK;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) {
+            mbar_init(&m.full[i], 1);
+            mbar_init(&m.empty[i], 1);
+        }
+        for (int i = 0; i < NBUF; ++i) {
+            mbar_init(&m.accf[i], 1);
+            mbar_init(&m.acce[i], NDRAIN);
+        }
+        for (int i = 0; i < TSLOTS; ++i) {
+            mbar_init(&m.tfull[i], 1);
+            mbar_init(&m.tempty[i], NDRAIN);   // released by every drain thread after the tile's last drain
+        }
+        mbar_init(m.drain, 1);
+        *m.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc_warp(m);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *m.tmem_slot;
+
+    if (warp == 0) {   // ---- TMA producer ----
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t ph = 0;
+            for (int k = 0;; ++k) {
+                const TileSlot& ts = m.slots[k % TSLOTS];
+                if (!mbar_wait(&m.tfull[k % TSLOTS], (k / TSLOTS) & 1, m.abort_flag) || !ts.valid) break;
+                if (!produce_tile(a, ts, m, tmA_p, tmB_p, ts.tig * BM, ts.tjg * BN, 0, 0, 0, 0, nkb, stage, ph))
+                    break;
+            }
+        }
+    } else if (warp == 1) {   // ---- MMA issuer ----
+        if (lane == 0) {
+            int stage = 0, seg = 0;
+            uint32_t ph = 0;
+            unsigned long long issued = 0;
+            for (int k = 0;; ++k) {
+                const TileSlot& ts = m.slots[k % TSLOTS];
+                if (!mbar_wait(&m.tfull[k % TSLOTS], (k / TSLOTS) & 1, m.abort_flag) || !ts.valid) break;
+                if (!mma_tile(a, ts, m, tmem, nkb, 1, 1, stage, ph, seg, issued)) break;
+            }
+            if (a.units) atomicAdd(a.units, issued);
+            umma_commit(m.drain);
+            volatile int dummy = 0;
+            if (!mbar_wait(m.drain, 0, &dummy)) *m.abort_flag = 1;
+        }
+    } else if (warp < 2 + NDRAIN / 32) {   // ---- drain / epilogue ----
+        int seg = 0;
+        for (int k = 0;; ++k) {
+            const TileSlot& ts = m.slots[k % TSLOTS];
+            if (!mbar_wait(&m.tfull[k % TSLOTS], (k / TSLOTS) & 1, m.abort_flag) || !ts.valid) break;
+            if (!drain_tile(a, ts, m, tmem, ts.tig * BM, ts.tjg * BN, warp, lane, seg)) break;
+            mbar_arrive(&m.tempty[k % TSLOTS]);   // this thread is done with the slot
+        }
+    } else {   // ---- scheduler: tile slots filled ahead of the roles ----
+        for (int k = 0;; ++k) {
+            TileSlot& ts = m.slots[k % TSLOTS];
+            if (!mbar_wait(&m.tempty[k % TSLOTS], ((k / TSLOTS) & 1) ^ 1, m.abort_flag)) break;
+            unsigned int ticket = 0;
+            if (lane == 0) ticket = atomicAdd(a.tickets, 1u);
+            ticket = __shfl_sync(0xffffffffu, ticket, 0);
+            int tig = 0, tjg = 0;
+            if (ticket >= (unsigned)a.ngroups || !tile_group(a, (int)ticket, tig, tjg)) {
+                if (lane == 0) {
+                    ts.valid = 0;
+                    __threadfence_block();
+                    mbar_arrive(&m.tfull[k % TSLOTS]);
+                }
+                break;
+            }
+            fill_slot_warp(a, ts, tig, tjg, nkb, lane);
+            if (lane == 0) mbar_arrive(&m.tfull[k % TSLOTS]);
+        }
+    }
+    split_teardown(a, m, tmem, warp, 1);
+}
+
 __global__ void __launch_bounds__(NTHREADS, CTAS_PER_SM)
 zgemm_split_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const SplitArgs a) {
     zgemm_split_body(&tmA, &tmB, a, blockIdx.x, false);
+}
+
+__global__ void __launch_bounds__(NTHREADS, CTAS_PER_SM)
+zgemm_split_persistent(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                       const SplitArgs a) {
+    zgemm_split_persistent_body(&tmA, &tmB, a);
 }
 
 // Grouped: instances (each with its own tensor maps in global memory) share one
@@ -919,8 +1089,14 @@ int zt_split_create(zt_plan* p) {
         ZT_CU(cudaMemcpyAsync(w->order_lower, ol.data(), ol.size() * sizeof(int), cudaMemcpyHostToDevice, cs));
         ZT_CU(cudaStreamSynchronize(cs));   // host vectors go out of scope
     }
+    w->persistent = (cm == 1 && cn == 1 && !p->tun.no_persistent) ? 1 : 0;
+    ZT_CU(cudaDeviceGetAttribute(&w->nsm, cudaDevAttrMultiProcessorCount, p->device));
+    ZT_CU(ZT_DMALLOC(w->tickets, 16, cs));
+    ZT_CU(cudaMemsetAsync(w->tickets, 0, 16, cs));
     if (zt_attr_needed(ZT_ATTR_SPLIT)) {
         ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        ZT_CU(cudaFuncSetAttribute(zgemm_split_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)SMEM_BYTES));
         ZT_CU(cudaFuncSetAttribute(zgemm_split_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)SMEM_BYTES));
     }
@@ -933,7 +1109,7 @@ size_t zt_split_bytes(int N, const zt_tuning& t) {
                  Npad = (size_t)round_up(2 * N, BN * cn);
     const size_t nkb = ldk / BK, ngA = Mpad / (BM * cm), ngB = Npad / (BN * cn);
     return (size_t)s * Mpad * ldk * 2 + 2 * (size_t)s * Npad * ldk * 2 + Mpad * 4 + 2 * Npad * 4 +
-           ngA * nkb * 4 + 2 * ngB * nkb * 4;
+           ngA * nkb * 4 + 2 * ngB * nkb * 4 + 16;
 }
 
 void zt_split_destroy(zt_plan* p) {
@@ -945,6 +1121,7 @@ void zt_split_destroy(zt_plan* p) {
     zt_dfree(w->occA, ms);
     zt_dfree(w->order_full, ms);
     zt_dfree(w->order_lower, ms);
+    zt_dfree(w->tickets, ms);
     for (int b = 0; b < 2; ++b) {
         zt_dfree(w->dB[b], ms);
         zt_dfree(w->eB[b], ms);
@@ -1040,6 +1217,8 @@ static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int l
     const int cs = w->cm * w->cn;
     a.order = lower_only ? w->order_lower : w->order_full;   // only groups with work, heaviest first
     const int ngroups = lower_only ? w->n_lower : w->n_full;
+    a.ngroups = ngroups;
+    a.tickets = nullptr;
     *ngroups_out = ngroups;
     *ntiles_out = ngroups * cs;
 }
@@ -1114,6 +1293,15 @@ int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower
             zt_timer_end(p, t, s);
             return zt_cuda_check(e, "cudaLaunchKernelEx(zgemm_split_kernel)");
         }
+    } else if (w->persistent) {   // one CTA per SM works through the tile groups
+        e = cudaMemsetAsync(w->tickets, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) {
+            zt_timer_end(p, t, s);
+            return zt_cuda_check(e, "cudaMemsetAsync(tickets)");
+        }
+        a.tickets = w->tickets;
+        const int grid = ngroups < w->nsm ? ngroups : w->nsm;
+        if (grid > 0) zgemm_split_persistent<<<grid, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB[b_slot], a);
     } else {
         zgemm_split_kernel<<<ngroups, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB[b_slot], a);
     }
@@ -1254,6 +1442,7 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
     a.exact_groups = NA_EG;
     a.ntn = NA_NPAD / BN;
     a.lower_only = 0;
+    a.tickets = nullptr;
     a.cm = 1;
     a.cn = 1;
     a.ntmg = NA_MPAD / BM;
@@ -1262,6 +1451,7 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
     a.occB = nullptr;
     a.units = nullptr;
     a.order = nullptr;
+    a.ngroups = (NA_MPAD / BM) * (NA_NPAD / BN);
     a.alpha = -1.0;
     a.eA = eA;
     a.eB = eB;

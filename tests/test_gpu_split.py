@@ -188,3 +188,24 @@ def test_banded_product_has_zero_far_tiles():
     far = np.abs(i[:, None] - i[None, :]) > 20
     assert np.all(got[far] == 0)
     assert _rel(got, X @ Y) < 1e-12
+
+
+@pytest.mark.parametrize("N", [200, 1024])
+def test_persistent_kernel_equals_one_tile_per_cta(N):
+    # The persistent product kernel (one CTA per SM taking tiles from a ticket
+    # counter) runs each tile's arithmetic unchanged: bitwise equal results,
+    # for the full product and, through IsoMP steps, the lower-triangle one.
+    W = vorticity_w0(N, seed=8)
+    P = oracle.stream_solve(W)
+    persistent = _gemm(_split_plan(N), P, W)
+    one_tile = _gemm(_split_plan(N, no_persistent=1), P, W)
+    assert np.array_equal(persistent, one_tile)
+    outs = []
+    for flag in (0, 1):
+        plan = z.Plan(N, z.PRECISION_SPLIT, no_persistent=flag)
+        Wd = torch.from_numpy(W.copy()).cuda()
+        for _ in range(2):
+            z.isomp_step(plan, Wd, 0.01)
+        outs.append(Wd.cpu().numpy())
+        plan.close()
+    assert np.array_equal(outs[0], outs[1])
