@@ -56,7 +56,7 @@ namespace {
 constexpr int BM = 128;            // tile rows (X' rows)
 constexpr int BN = 256;            // tile cols (B'^T rows = real output columns)
 constexpr int BK = 64;             // K per stage: 64 BF16 = 128 bytes per row
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int A_TILE = BM * BK * 2;
 constexpr int B_TILE = BN * BK * 2;
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
@@ -199,6 +199,23 @@ __device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
         "h"(mask)
         : "memory");
 }
+// Asynchronous bulk reduce-add of `bytes` (a multiple of 16) of int64 from
+// shared to global memory; the L2 performs the additions.
+__device__ __forceinline__ void bulk_reduce_add_s64(long long* gdst, uint32_t ssrc, int bytes) {
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(gdst), "r"(ssrc),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -432,8 +449,12 @@ struct TileSlot {
     uint8_t fb[MAX_KB];
 };
 constexpr int TSLOTS = 2;   // tile slots of the persistent kernel (one being worked, one being filled)
+// Drain staging: per drain thread two 128-byte slots (16 int64) for the bulk
+// reduce-adds of intermediate segments; a 272-byte stride keeps the 16-byte
+// shared stores of a quarter-warp on distinct banks.
+constexpr int STG_STRIDE = 272;
 constexpr size_t SMEM_BYTES = 1024 /*align slack*/ + (size_t)STAGES * STAGE_BYTES + 256 /*barriers*/ +
-                              TSLOTS * sizeof(TileSlot);
+                              TSLOTS * sizeof(TileSlot) + (size_t)NDRAIN * STG_STRIDE;
 
 struct SmemMap {
     uint8_t* sA;
@@ -448,6 +469,7 @@ struct SmemMap {
     uint32_t* tmem_slot;
     volatile int* abort_flag;
     TileSlot* slots;
+    uint8_t* stg;       // [NDRAIN][STG_STRIDE] drain staging
 };
 
 __device__ __forceinline__ SmemMap smem_map() {
@@ -466,6 +488,7 @@ __device__ __forceinline__ SmemMap smem_map() {
     m.tmem_slot = reinterpret_cast<uint32_t*>(m.drain + 1);
     m.abort_flag = reinterpret_cast<volatile int*>(m.tmem_slot + 1);
     m.slots = reinterpret_cast<TileSlot*>(reinterpret_cast<uint8_t*>(m.full) + 256);
+    m.stg = reinterpret_cast<uint8_t*>(m.slots + TSLOTS);
     return m;
 }
 
@@ -628,6 +651,9 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
     const bool apow2 = (abits & 0xFFFFFFFFFFFFFLL) == 0 && aef != 0 && aef != 0x7FF;
     const int aexp = apow2 ? aef - 1023 : 0;
     const unsigned long long asign = apow2 ? ((unsigned long long)abits & 0x8000000000000000ull) : 0ull;
+    // staging slots of this thread for the bulk reduce-adds of intermediate segments
+    uint8_t* stg = m.stg + (size_t)(threadIdx.x - 64) * STG_STRIDE;
+    int nstg = 0;   // bulk operations issued by this thread in this tile
     int tseg = 0;   // segments of this tile drained so far
     for (int g = 0; g < a.s; ++g) {
         const int ulim = seg_units(g, a.beta, a.exact_groups);
@@ -637,10 +663,17 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
         for (int q = 0; q < nsegs; ++q) {
             const int b = seg % NBUF, use = seg / NBUF;
             ++seg;
-            if (!mbar_wait(&m.accf[b], use & 1, m.abort_flag)) return false;
+            if (!mbar_wait(&m.accf[b], use & 1, m.abort_flag)) {
+                if (nstg) bulk_wait_all();
+                return false;
+            }
             tc_fence_after();
             const bool first = tseg == 0, last = tseg == total - 1;
             ++tseg;
+            if (last && nstg) {   // every reduce-add of this tile has landed and is visible
+                bulk_wait_all();
+                fence_proxy_async_global();
+            }
 #pragma unroll 1
             for (int ch = 0; ch < BN / 32; ++ch) {   // 16 columns at a time
                 const int col0 = half * (BN / 2) + ch * 16;
@@ -667,6 +700,17 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
                     for (int t = 0; t < 16; ++t) v[t] = (v[t] + (1LL << (-sh - 1))) >> (-sh);
                 }
                 long long* dst = Crow + cb;
+                if (!first && !last) {   // intermediate segment: reduce-add through L2, asynchronously
+                    uint8_t* slot = stg + (nstg & 1) * 128;
+                    if (nstg >= 2) bulk_wait_read_1();   // the slot's previous copy has been read
+#pragma unroll
+                    for (int t = 0; t < 16; t += 2)
+                        if (t < lim) *reinterpret_cast<longlong2*>(slot + t * 8) = make_longlong2(v[t], v[t + 1]);
+                    fence_proxy_async_shared();
+                    bulk_reduce_add_s64(dst, smem_u32(slot), lim * 8);
+                    ++nstg;
+                    continue;
+                }
                 if (!first) {   // add the accumulator (all loads first)
                     long long o[16];
                     if (v32) {
@@ -727,10 +771,12 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
                         if (t < lim) *reinterpret_cast<longlong2*>(dst + t) = make_longlong2(v[t], v[t + 1]);
                 }
             }
+            if (first && total > 2) fence_proxy_async_global();   // plain stores before later reduce-adds
             tc_fence_before();
             mbar_arrive(&m.acce[b]);
         }
     }
+    if (nstg) bulk_wait_all();   // staging reads done before the slots are reused or the CTA leaves
     if (total == 0 && row_ok) {   // every digit product of the tile is zero
         const int cbeg = c0 + half * (BN / 2);
         for (int c = cbeg; c < cbeg + BN / 2 && c < ncols; ++c) {
