@@ -31,10 +31,11 @@ H = 0.005
 TOL = 1e-12
 MAXIT = 50
 
-# DRAM traffic of zgemm_split_kernel per launch, from an ncu capture
+# DRAM traffic of the split product kernel per launch (mean over one IsoMP step), from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
 # source it was taken on (sha256 of csrc/zt_split.cu), null otherwise.
-TRAFFIC = {"sha256": None, "bytes_per_launch": None}
+TRAFFIC = {"sha256": "81df2b00899a389e362725178fdf87e3cfa9b100da1357f2aaf88af6b7a42bb9",
+           "bytes_per_launch": 5852482848}
 
 
 def _peaks():
@@ -496,7 +497,7 @@ def run_gpu(args):
         "gpu_launches": gpu_launches,
         "e2e": e2e,
         "fp64_form": fp64,
-        "roofline": {"bound": "tensor", "kernel": "zgemm_split_kernel", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "tensor", "kernel": "zgemm_split_persistent", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "peak_source": f"{peaks['source']} bf16 sustained",
                      "work": "BF16 digit-pair MMA units issued (2 x 128 x 256 x 64 flops each, counted on the "
