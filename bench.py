@@ -120,14 +120,21 @@ def _dist():
 
 
 def _barrier_max(value: float, ws: int):
+    """Maximum of a per-rank value over all ranks (the slowest rank's time)."""
     if ws <= 1:
         return value
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _job_rate(units_per_rank: int, seconds_max: float, ws: int) -> float:
+    """Whole-job throughput of replicas: units every rank processed over the slowest rank's time."""
+    return ws * units_per_rank / seconds_max
 
 
 def _barrier(ws):
@@ -401,7 +408,7 @@ def run_gpu(args):
     upd = plan.kernel_time(z.KERNEL_UPDATE)
     plan.set_timing(False)
     t_max = _barrier_max(t_ms, ws)
-    value = ws * args.steps / (t_max / 1e3)
+    value = _job_rate(args.steps, t_max / 1e3, ws)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed ----
     _log('e2e')
@@ -418,7 +425,7 @@ def run_gpu(args):
         Wout.copy_(Wd2, non_blocking=True)
         torch.cuda.synchronize()
     t_e2e = _barrier_max(time.perf_counter() - t0, ws)
-    e2e = {"value": ws * e2e_steps / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": int(Wh.numel() * 16),
+    e2e = {"value": _job_rate(e2e_steps, t_e2e, ws), "unit": "steps/s", "h2d_bytes_per_step": int(Wh.numel() * 16),
            "d2h_bytes_per_step": int(Wout.numel() * 16), "steps": e2e_steps}
 
     # ---- plain FP64 form on the same GPU (same workload) ----
