@@ -36,7 +36,7 @@
 
 namespace {
 constexpr int SD = 16;             // diagonals per tile
-constexpr int SL = 64;             // positions per segment
+constexpr int SL = 32;             // positions per segment (32 measured best: more tiles in flight, short carries)
 constexpr int SROWS = SL + SD;     // staged rows per tile
 constexpr int STH = 64;            // threads per CTA: 2 per diagonal (re, im) compute, all stage
 constexpr int CH = 8;              // positions per register chunk
