@@ -58,6 +58,28 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs) * 1e3, q)) if len(xs) else None
 
 
+def next_admission(queues, resident, used, budget, stepped, ema, target, estimate):
+    """The class whose head job is admitted next, or None (the admission policy).
+
+    queues: class -> deque of waiting jobs (FIFO per class); classes are tried in
+    the order of their head job's arrival.  resident: class -> number of resident
+    jobs.  A head job fits when its plan footprint estimate(N, precision) fits the
+    remaining budget, or nothing at all is resident.  A class with resident jobs
+    admits another only after a completed step with its current set (stepped)
+    and while its step-time average ema[class] is below target (seconds; None:
+    footprint only).
+    """
+    anything = sum(resident.values()) > 0
+    for cls in sorted((c for c in queues if queues[c]), key=lambda c: queues[c][0].arrival):
+        head = queues[cls][0]
+        if used + estimate(head.N, head.precision) > budget and anything:
+            continue
+        if resident.get(cls) and target is not None and not (stepped.get(cls) and ema.get(cls, 0.0) < target):
+            continue
+        return cls
+    return None
+
+
 class Server:
     def __init__(self, budget_bytes: int, tol: float = 1e-12, maxit: int = 50, graph: bool = False,
                  target_step_ms: float | None = 100.0):
@@ -183,18 +205,11 @@ class Server:
                     break
                 job = None
                 with lock:
-                    resident = sum(len(c) for c in classes.values())
-                    for cls in sorted((c for c in queues if queues[c]), key=lambda c: queues[c][0].arrival):
-                        head = queues[cls][0]
-                        need = z.plan_estimate_bytes(head.N, head.precision)
-                        if st["used"] + need > self.budget and resident:
-                            continue
-                        if classes.get(cls) and self.target is not None and not (
-                                stepped.get(cls) and ema.get(cls, 0.0) < self.target):
-                            continue
+                    cls = next_admission(queues, {c: len(v) for c, v in classes.items()}, st["used"], self.budget,
+                                         stepped, ema, self.target, z.plan_estimate_bytes)
+                    if cls is not None:
                         job = queues[cls].popleft()
                         stepped[cls] = False
-                        break
                 if job is None:
                     break
                 ta = clock()
