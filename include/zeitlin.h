@@ -138,6 +138,15 @@ ZT_API int isomp_run(zt_plan* plan, double* W, double h, long nsteps, double tol
  * ZT_ECUDA, ZT_ETIMEOUT. */
 ZT_API int zt_zgemm_skew(zt_plan* plan, const double* X, const double* Y, double* C, void* stream);
 
+/* Discrete Casimirs C_k = tr(W^k), k = 2..5 (Sec. 2, Eq. 7), computed on the
+ * device with the plan's products (W^2 = W W and W^4 = W^2 W^2, split or FP64
+ * as the plan) and FP64 conjugate dot products summed in a fixed order.
+ * W: device, N x N complex128 row-major, skew-Hermitian (the identities used
+ * rely on it).  C: HOST array of 8 doubles, (Re, Im) of C2, C3, C4, C5.  Uses
+ * the plan's step workspace; waits for the stream before returning.  Status
+ * as for the other calls (ZT_ETIMEOUT if a bounded device wait ran out). */
+ZT_API int zeitlin_casimirs(zt_plan* plan, const double* W, double* C, void* stream);
+
 /* Device bytes a plan for (N, precision, tuning) allocates (for admission by
  * memory footprint); -1 for an invalid N.  `opt` may be NULL. */
 ZT_API long long zt_plan_estimate_bytes(int N, int precision, const zt_tuning* opt);

@@ -86,6 +86,7 @@ struct zt_plan {
     double2* A = nullptr;
     double2* B = nullptr;
     double* partials = nullptr;
+    double* cas_part = nullptr;   // Casimir partial sums [CTAs + 1][8]
     int npartials = 0;
     // segmented stream solve: factors and their products within a segment,
     // diagonal-major (diagonal m at dof[m], padded to 8 entries), constant

@@ -14,6 +14,8 @@
 // ---------------------------------------------------------------------------
 static thread_local char g_err[512] = "";
 
+constexpr int CAS_CTAS = 304, CAS_TH = 256;   // Casimir reduction: CTAs (2 per SM) and threads
+
 int zt_fail(int code, const char* fmt, ...) {
     va_list ap;
     va_start(ap, fmt);
@@ -533,6 +535,7 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     zt_dfree(p->A, ms);
     zt_dfree(p->B, ms);
     zt_dfree(p->partials, ms);
+    zt_dfree(p->cas_part, ms);
     zt_dfree(p->state, ms);
     zt_dfree(p->d_units, ms);
     zt_host_states_release(p->h_state, 1);   // no copy into it is in flight: steps end synchronised
@@ -562,7 +565,8 @@ extern "C" long long zt_plan_estimate_bytes(int N, int precision, const zt_tunin
     fill_tuning_defaults(t);
     const size_t nn = (size_t)N * N, ntri = (size_t)N * (N + 1) / 2;
     const size_t nt = (N + 31) / 32;
-    size_t b = 2 * ntri * 8 + 5 * nn * 16 + nt * (nt + 1) / 2 * 8 + zt_solve_bytes(N) + 1024;
+    size_t b = 2 * ntri * 8 + 5 * nn * 16 + nt * (nt + 1) / 2 * 8 + zt_solve_bytes(N) + 1024 +
+               ((size_t)CAS_CTAS + 1) * 8 * sizeof(double);
     if (precision == ZT_PRECISION_SPLIT) b += zt_split_bytes(N, t);
     return (long long)b;
 }
@@ -632,6 +636,7 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     const int nt = (N + UT - 1) / UT;
     p->npartials = nt * (nt + 1) / 2;
     ZT_TRY(ZT_DMALLOC(p->partials, (size_t)p->npartials * sizeof(double), cs));
+    ZT_TRY(ZT_DMALLOC(p->cas_part, ((size_t)CAS_CTAS + 1) * 8 * sizeof(double), cs));
     ZT_TRY(ZT_DMALLOC(p->state, sizeof(zt_dev_state), cs));
     ZT_TRY(ZT_DMALLOC(p->d_units, sizeof(unsigned long long), cs));
     tr.mark("allocations");
@@ -728,6 +733,73 @@ extern "C" int zt_zgemm_skew(zt_plan* p, const double* X, const double* Y, doubl
     rc = zgemm(p, (const double2*)X, (const double2*)Y, (double2*)C, -1.0, 0, s, ZT_GATE_NONE);
     zt_note_use(p, s);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Casimirs C_k = tr(W^k), k = 2..5 (Sec. 2, Eq. 7), from W^2 = W W and
+// W^4 = W^2 W^2 (the plan's products) and conjugate dot products: W is
+// skew-Hermitian and W^2, W^4 are Hermitian, so tr(X Y) = sum_ij X_ij Y_ji
+// = -sum_ij X_ij conj(W_ij) for Y = W and +sum_ij X_ij conj(Y_ij) for Y = W^2:
+//   C2 = -sum |W_ij|^2,  C3 = -sum (W^2)_ij conj(W_ij),
+//   C4 = sum |(W^2)_ij|^2,  C5 = -sum (W^4)_ij conj(W_ij).
+// FP64 sums in a fixed order (per-CTA partials, then one pass).
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(CAS_TH) casimir_partials(const double2* __restrict__ W,
+                                                           const double2* __restrict__ W2,
+                                                           const double2* __restrict__ W4, size_t n,
+                                                           double* __restrict__ part) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (size_t e = (size_t)blockIdx.x * CAS_TH + threadIdx.x; e < n; e += (size_t)gridDim.x * CAS_TH) {
+        const double2 w = W[e], a = W2[e], b = W4[e];
+        acc[0] -= w.x * w.x + w.y * w.y;
+        acc[2] -= a.x * w.x + a.y * w.y;
+        acc[3] -= a.y * w.x - a.x * w.y;
+        acc[4] += a.x * a.x + a.y * a.y;
+        acc[6] -= b.x * w.x + b.y * w.y;
+        acc[7] -= b.y * w.x - b.x * w.y;
+    }
+    __shared__ double red[CAS_TH];
+    for (int j = 0; j < 8; ++j) {
+        red[threadIdx.x] = acc[j];
+        __syncthreads();
+        for (int w = CAS_TH / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(size_t)blockIdx.x * 8 + j] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void casimir_final(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+    const int j = threadIdx.x;
+    if (j >= 8) return;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[(size_t)b * 8 + j];
+    out[j] = s;
+}
+
+extern "C" int zeitlin_casimirs(zt_plan* p, const double* W, double* C, void* stream) {
+    if (!p) return zt_fail(ZT_EINVAL, "plan is NULL");
+    if (!C) return zt_fail(ZT_EINVAL, "C is NULL");
+    int rc;
+    if ((rc = check_ptr(W, "W"))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    ZT_CU(cudaMemsetAsync(p->state, 0, sizeof(zt_dev_state), s));
+    if ((rc = zgemm(p, (const double2*)W, (const double2*)W, p->A, -1.0, 0, s, ZT_GATE_NONE))) return rc;   // W W
+    if ((rc = zgemm(p, p->A, p->A, p->B, 1.0, 0, s, ZT_GATE_NONE))) return rc;   // W^2 W^2 (W^2 Hermitian)
+    const size_t n = (size_t)p->N * p->N;
+    casimir_partials<<<CAS_CTAS, CAS_TH, 0, s>>>((const double2*)W, p->A, p->B, n, p->cas_part);
+    casimir_final<<<1, 32, 0, s>>>(p->cas_part, CAS_CTAS, p->cas_part + (size_t)CAS_CTAS * 8);
+    p->launches += 2;
+    ZT_CU(cudaGetLastError());
+    ZT_CU(cudaMemcpyAsync(p->h_state, p->state, sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
+    ZT_CU(cudaMemcpyAsync(C, p->cas_part + (size_t)CAS_CTAS * 8, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ZT_CU(cudaStreamSynchronize(s));
+    zt_note_use(p, s);
+    if (p->h_state->timeout) return zt_fail(ZT_ETIMEOUT, "zeitlin_casimirs: bounded device wait ran out");
+    return ZT_OK;
 }
 
 // One fixed-point sweep (Eq. isomp_iter): Pt = solve(Wt), A = Pt Wt,

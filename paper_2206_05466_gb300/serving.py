@@ -212,6 +212,7 @@ class Server:
                         stepped[cls] = False
                 if job is None:
                     break
+                need = z.plan_estimate_bytes(job.N, job.precision)
                 ta = clock()
                 plan = z.Plan(job.N, job.precision)
                 tb = clock()

@@ -95,6 +95,8 @@ def load(build_if_missing: bool = True):
     L.isomp_run.restype = i
     L.zt_zgemm_skew.argtypes = [vp, vp, vp, vp, vp]
     L.zt_zgemm_skew.restype = i
+    L.zeitlin_casimirs.argtypes = [vp, vp, ctypes.POINTER(d), vp]
+    L.zeitlin_casimirs.restype = i
     L.zt_plan_launch_count.argtypes = [vp]
     L.zt_plan_launch_count.restype = l
     L.zt_plan_set_timing.argtypes = [vp, i]
@@ -215,6 +217,13 @@ def isomp_run(plan: Plan, W, h: float, nsteps: int, tol: float = 1e-12, maxit: i
                                  ctypes.byref(st), _stream(stream)), allow)
     return {"status": rc, "steps": st.steps, "total_iters": st.total_iters, "max_iters": st.max_iters,
             "all_converged": bool(st.all_converged), "max_residual": st.max_residual}
+
+
+def zeitlin_casimirs(plan: Plan, W, stream=None) -> dict:
+    """Casimirs {k: tr(W^k)} for k = 2..5, computed on the device (waits for the stream)."""
+    out = (ctypes.c_double * 8)()
+    _check(load().zeitlin_casimirs(plan.handle, _ptr(W, plan.N), out, _stream(stream)))
+    return {k: complex(out[2 * (k - 2)], out[2 * (k - 2) + 1]) for k in (2, 3, 4, 5)}
 
 
 def zt_zgemm_skew(plan: Plan, X, Y, C, stream=None):
