@@ -253,6 +253,8 @@ def run_casimir(args):
     """Long run: Casimir and spectrum drift after --steps steps, split and (optionally) FP64 form."""
     import torch
 
+    import numpy as np
+
     from paper_2206_05466_gb300 import zeitlin as z
     from paper_2206_05466_gb300.inputs import vorticity_w0
 
@@ -268,13 +270,21 @@ def run_casimir(args):
         else:
             plan = z.Plan(N, prec)
         W = torch.from_numpy(W0).cuda()
+        c0 = z.zeitlin_casimirs(plan, W)   # on the device, the plan's products
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = z.isomp_run(plan, W, H, steps, TOL, MAXIT)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        tc = time.perf_counter()
+        c1 = z.zeitlin_casimirs(plan, W)
+        t_cas = time.perf_counter() - tc
         W1 = W.cpu().numpy()
-        res[name] = {"steps_per_s": steps / dt, "run_stats": r, "drift": _casimir_drift(W0, W1),
+        drift = _casimir_drift(W0, W1)
+        mu0 = np.abs(np.linalg.eigvalsh(-1j * W0))
+        dev = {f"C{k}": float(abs(c1[k] - c0[k]) / np.sum(mu0 ** k)) for k in (2, 3, 4, 5)}
+        res[name] = {"steps_per_s": steps / dt, "run_stats": r, "drift": drift,
+                     "device_casimir_drift": dev, "device_casimirs_ms": t_cas * 1e3,
                      "trace_abs": float(abs(W1.trace())), "skew_err": float(abs(W1 + W1.conj().T).max())}
         plan.close()
     print(json.dumps(res), flush=True)
