@@ -15,6 +15,9 @@ sphere", that it follows):
                        isomp and isomp_iter, Sec. 3.1
   isomp_run         -- repeated steps
   casimirs          -- C_k = tr(W^k), Sec. 2 Eq. W_pow
+  basis (module)    -- quantised spherical-harmonic basis T^_lm by Wigner 3j
+                       symbols and by eigenvectors of the blocks, W from
+                       omega_lm and back, Sec. 3.2 Eqs. W0, Tlm, lap_prop
 
 Every function is pinned by tests/test_oracle_*.py against facts that do not
 come from this package (closed-form spectrum, the textbook spin-Casimir
