@@ -87,6 +87,22 @@ def SIGN_RULE(N: int, l: int, m: int) -> int:
     return -1 if m % 2 else 1
 
 
+def end_recurrence_sign(d, e, lam, sign_last, j):
+    """Sign at position j of the solution of (T - lam I) y = 0 (T tridiagonal: diagonal d,
+    off-diagonal e, all e < 0) with y[n-1] = sign_last, by the backward three-term
+    recurrence (rescaled against overflow)."""
+    n = len(d)
+    y1, y0 = float(sign_last), 0.0   # y[i], y[i+1]
+    for i in range(n - 1, j, -1):
+        # row i: e[i-1] y[i-1] + (d[i] - lam) y[i] + e[i] y[i+1] = 0
+        nxt = -((d[i] - lam) * y1 + (e[i] * y0 if i + 1 < n else 0.0)) / e[i - 1]
+        y0, y1 = y1, nxt
+        big = max(abs(y0), abs(y1))
+        if big > 1e100:
+            y0, y1 = y0 / big, y1 / big
+    return float(np.sign(y1))
+
+
 def that_lm_eig(N: int, l: int, m: int) -> np.ndarray:
     """T^_lm from the eigenvector of the block -Delta^m for the eigenvalue l(l+1), m >= 0."""
     assert 0 <= m <= l < N
@@ -98,7 +114,14 @@ def that_lm_eig(N: int, l: int, m: int) -> np.ndarray:
         lam, vec = scipy.linalg.eigh_tridiagonal(d, e)
     k = int(np.argmin(np.abs(lam - l * (l + 1))))
     v = vec[:, k] / np.linalg.norm(vec[:, k])
-    if np.sign(v[n - 1]) != SIGN_RULE(N, l, m):
+    # The end entries can be far below the eigensolver's absolute accuracy (and
+    # interior entries can vanish: the blocks are persymmetric), so the sign is
+    # fixed at the largest entry: the three-term recurrence of (-Delta^m -
+    # l(l+1) I) y = 0 run backwards from y[n-1] = (-1)^m (the sign the
+    # stretched 3j symbol gives the last entry) grows from that end towards
+    # the bulk, and its sign at the largest entry of v is that of T^_lm there.
+    jmax = int(np.argmax(np.abs(v)))
+    if end_recurrence_sign(d, e, l * (l + 1), SIGN_RULE(N, l, m), jmax) != np.sign(v[jmax]):
         v = -v
     out = np.zeros((N, N))
     out[np.arange(m, N), np.arange(0, n)] = v

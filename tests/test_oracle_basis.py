@@ -91,3 +91,10 @@ def test_w_from_omega_is_in_su_n_and_round_trips(N, lmax):
     assert abs(np.trace(W)) < 1e-13
     back = basis.omega_from_w(N, W, lmax)
     assert np.abs(back - om).max() < 1e-13
+
+
+@pytest.mark.parametrize("N,pairs", [(64, [(50, 40), (63, 63), (40, 1), (63, 0), (30, 29), (17, 9)]),
+                                     (129, [(128, 100), (90, 90), (20, 3), (127, 64)])])
+def test_eigenvector_route_at_larger_n_where_the_ends_are_tiny(N, pairs):
+    for l, m in pairs:
+        assert np.abs(basis.that_lm(N, l, m) - basis.that_lm_eig(N, l, m)).max() < 1e-13, (l, m)
