@@ -147,6 +147,28 @@ ZT_API int zt_zgemm_skew(zt_plan* plan, const double* X, const double* Y, double
  * as for the other calls (ZT_ETIMEOUT if a bounded device wait ran out). */
 ZT_API int zeitlin_casimirs(zt_plan* plan, const double* W, double* C, void* stream);
 
+/* ---- Quantised spherical-harmonic basis (Sec. 3.2, Eqs. W0, Tlm, lap_prop) ----
+ * T^_lm (0 <= m <= l) lies on the m-th lower diagonal; its entries there are
+ * the unit eigenvector of the block -Delta^m for the eigenvalue l(l+1), with
+ * the sign of Eq. Tlm (last entry of the diagonal has the sign (-1)^m), and
+ * T^_{l,-m} = (-1)^m T^_lm^T.  A basis holds T^_lm for l <= lmax on the plan's
+ * device (about (lmax+1)(lmax+2)/2 * N doubles, twice during creation); the
+ * plan is read only by zt_basis_create, so either may be destroyed first.
+ * zt_basis_destroy waits for the launches that read the basis.  Coefficients
+ * omega_lm are complex128 in a flat device array of (lmax+1)^2 entries at
+ * l*l + l + m. */
+typedef struct zt_basis zt_basis;
+ZT_API int zt_basis_create(zt_plan* plan, int lmax, zt_basis** out);   /* computes the basis (waits) */
+ZT_API void zt_basis_destroy(zt_basis* basis);
+/* Copies the N - m diagonal entries of T^_lm (0 <= m <= l <= lmax) to a HOST array. */
+ZT_API int zt_basis_vector(zt_basis* basis, int l, int m, double* out);
+/* W = sum_{l <= lmax, |m| <= l} i omega_lm T^_lm (Eq. W0); W: device N x N complex128,
+ * overwritten (zero outside the band |m| <= lmax).  Asynchronous on the stream. */
+ZT_API int zeitlin_w_from_omega(zt_basis* basis, const double* omega, double* W, void* stream);
+/* omega_lm = -i tr(T^_lm^H W) for l <= lmax (the inverse of the above on the span of
+ * the basis).  Asynchronous on the stream. */
+ZT_API int zeitlin_omega_from_w(zt_basis* basis, const double* W, double* omega, void* stream);
+
 /* Device bytes a plan for (N, precision, tuning) allocates (for admission by
  * memory footprint); -1 for an invalid N.  `opt` may be NULL. */
 ZT_API long long zt_plan_estimate_bytes(int N, int precision, const zt_tuning* opt);

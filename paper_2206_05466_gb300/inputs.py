@@ -78,3 +78,23 @@ def serving_jobs(duration_s: float, rate_per_s: float = 50.0,
         nsteps = int(rng.integers(steps_range[0], steps_range[1] + 1))
         jobs.append((t, N, nsteps, len(jobs)))
     return jobs
+
+
+def paper_omega(lmax: int = 20, lmin: int = 2, seed: int = 0):
+    """Seeded spherical-harmonic coefficients of the paper's initial condition
+    (Sec. 4: random omega_lm for 2 <= l <= 20): complex Gaussian omega_lm for
+    m > 0 and real Gaussian omega_l0, with omega_{l,-m} = (-1)^m conj(omega_lm)
+    (so that the vorticity is real / the matrix skew-Hermitian), stored flat at
+    l*l + l + m over l <= lmax.  Random numbers only; the assembly of W from
+    them is the library's (zeitlin_w_from_omega)."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    om = np.zeros((lmax + 1) ** 2, dtype=np.complex128)
+    for l in range(lmin, lmax + 1):
+        om[l * l + l] = rng.standard_normal()
+        for m in range(1, l + 1):
+            z = rng.standard_normal() + 1j * rng.standard_normal()
+            om[l * l + l + m] = z
+            om[l * l + l - m] = (-1) ** m * np.conj(z)
+    return om

@@ -97,6 +97,16 @@ def load(build_if_missing: bool = True):
     L.zt_zgemm_skew.restype = i
     L.zeitlin_casimirs.argtypes = [vp, vp, ctypes.POINTER(d), vp]
     L.zeitlin_casimirs.restype = i
+    L.zt_basis_create.argtypes = [vp, i, ctypes.POINTER(vp)]
+    L.zt_basis_create.restype = i
+    L.zt_basis_destroy.argtypes = [vp]
+    L.zt_basis_destroy.restype = None
+    L.zt_basis_vector.argtypes = [vp, i, i, ctypes.POINTER(d)]
+    L.zt_basis_vector.restype = i
+    L.zeitlin_w_from_omega.argtypes = [vp, vp, vp, vp]
+    L.zeitlin_w_from_omega.restype = i
+    L.zeitlin_omega_from_w.argtypes = [vp, vp, vp, vp]
+    L.zeitlin_omega_from_w.restype = i
     L.zt_plan_launch_count.argtypes = [vp]
     L.zt_plan_launch_count.restype = l
     L.zt_plan_set_timing.argtypes = [vp, i]
@@ -224,6 +234,66 @@ def zeitlin_casimirs(plan: Plan, W, stream=None) -> dict:
     out = (ctypes.c_double * 8)()
     _check(load().zeitlin_casimirs(plan.handle, _ptr(W, plan.N), out, _stream(stream)))
     return {k: complex(out[2 * (k - 2)], out[2 * (k - 2) + 1]) for k in (2, 3, 4, 5)}
+
+
+class Basis:
+    """Quantised spherical-harmonic basis T^_lm, l <= lmax, on the plan's device."""
+
+    def __init__(self, plan: Plan, lmax: int):
+        self.plan = plan
+        self.N = plan.N
+        self.lmax = int(lmax)
+        h = ctypes.c_void_p()
+        _check(load().zt_basis_create(plan.handle, self.lmax, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().zt_basis_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vector(self, l: int, m: int):
+        """The N - m diagonal entries of T^_lm (0 <= m <= l <= lmax), as a NumPy array."""
+        import numpy as np
+
+        out = np.empty(self.N - m, dtype=np.float64)
+        _check(load().zt_basis_vector(self._h, int(l), int(m),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+
+def _ptr_flat(t, n):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda:
+        raise TypeError("expected a complex128 CUDA tensor")
+    if t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"expected a contiguous tensor of {n} entries, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def zeitlin_w_from_omega(basis: Basis, omega, W, stream=None):
+    """W = sum i omega_lm T^_lm; omega: (lmax+1)^2 complex128 entries at l*l + l + m."""
+    _check(load().zeitlin_w_from_omega(basis.handle, _ptr_flat(omega, (basis.lmax + 1) ** 2), _ptr(W, basis.N),
+                                       _stream(stream)))
+    return W
+
+
+def zeitlin_omega_from_w(basis: Basis, W, omega, stream=None):
+    """omega_lm = -i tr(T^_lm^H W) for l <= lmax."""
+    _check(load().zeitlin_omega_from_w(basis.handle, _ptr(W, basis.N), _ptr_flat(omega, (basis.lmax + 1) ** 2),
+                                       _stream(stream)))
+    return omega
 
 
 def zt_zgemm_skew(plan: Plan, X, Y, C, stream=None):
