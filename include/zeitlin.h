@@ -82,7 +82,7 @@ typedef struct zt_run_stats {
 
 /* Create a plan for size N (1 <= N <= 16384) and precision ZT_PRECISION_*.
  * Precomputes, once, the tridiagonal blocks of Delta_N (Sec. 3.2, Eq.
- * delta_tria) and their LDL^T factors (the factorisation behind the HPD
+ * 13) and their LDL^T factors (the factorisation behind the HPD
  * tridiagonal solve of Sec. 3.3), and allocates the step workspace (about
  * 6 N^2 complex values, plus the digit slices for ZT_PRECISION_SPLIT).
  * `opt` may be NULL.  On success *out receives the plan.  Errors: ZT_EINVAL,
@@ -98,7 +98,7 @@ ZT_API const char* zt_last_error(void);
 
 /* W = Delta_N P (Sec. 3.2-3.3): the discrete Laplacian applied diagonal by
  * diagonal, each diagonal m (sub- and super-) through the tridiagonal block
- * -T_m of Eq. delta_tria.  P is any complex N x N matrix; W must not alias P.
+ * -T_m of Eq. 13.  P is any complex N x N matrix; W must not alias P.
  * O(N^2).  Errors: ZT_EINVAL, ZT_ECUDA. */
 ZT_API int zeitlin_laplacian_apply(zt_plan* plan, const double* P, double* W, void* stream);
 
@@ -147,10 +147,10 @@ ZT_API int zt_zgemm_skew(zt_plan* plan, const double* X, const double* Y, double
  * as for the other calls (ZT_ETIMEOUT if a bounded device wait ran out). */
 ZT_API int zeitlin_casimirs(zt_plan* plan, const double* W, double* C, void* stream);
 
-/* ---- Quantised spherical-harmonic basis (Sec. 3.2, Eqs. W0, Tlm, lap_prop) ----
+/* ---- Quantised spherical-harmonic basis (Sec. 3.2, Eqs. 10-12) ----
  * T^_lm (0 <= m <= l) lies on the m-th lower diagonal; its entries there are
  * the unit eigenvector of the block -Delta^m for the eigenvalue l(l+1), with
- * the sign of Eq. Tlm (last entry of the diagonal has the sign (-1)^m), and
+ * the sign of Eq. 11 (last entry of the diagonal has the sign (-1)^m), and
  * T^_{l,-m} = (-1)^m T^_lm^T.  A basis holds T^_lm for l <= lmax on the plan's
  * device (about (lmax+1)(lmax+2)/2 * N doubles, twice during creation); the
  * plan is read only by zt_basis_create, so either may be destroyed first.
@@ -162,7 +162,7 @@ ZT_API int zt_basis_create(zt_plan* plan, int lmax, zt_basis** out);   /* comput
 ZT_API void zt_basis_destroy(zt_basis* basis);
 /* Copies the N - m diagonal entries of T^_lm (0 <= m <= l <= lmax) to a HOST array. */
 ZT_API int zt_basis_vector(zt_basis* basis, int l, int m, double* out);
-/* W = sum_{l <= lmax, |m| <= l} i omega_lm T^_lm (Eq. W0); W: device N x N complex128,
+/* W = sum_{l <= lmax, |m| <= l} i omega_lm T^_lm (Eq. 10); W: device N x N complex128,
  * overwritten (zero outside the band |m| <= lmax).  Asynchronous on the stream. */
 ZT_API int zeitlin_w_from_omega(zt_basis* basis, const double* omega, double* W, void* stream);
 /* omega_lm = -i tr(T^_lm^H W) for l <= lmax (the inverse of the above on the span of

@@ -8,7 +8,7 @@ it shares no code with that path.
 Contents (each function cites the passage of Cifani, Viviani & Modin,
 "An efficient geometric method for incompressible hydrodynamics on the
 sphere", that it follows):
-  laplacian_block   -- tridiagonal block of diagonal m, Sec. 3.2 Eq. delta_tria
+  laplacian_block   -- tridiagonal block of diagonal m, Sec. 3.2 Eq. 13
   laplacian_apply   -- W = Delta_N P, block by block, Sec. 3.2-3.3
   stream_solve      -- P = Delta_N^{-1} W, Sec. 3.3 Eq. sub_tria_W
   isomp_step        -- one IsoMP step by fixed-point sweeps, Sec. 2 Eqs.
@@ -17,7 +17,7 @@ sphere", that it follows):
   casimirs          -- C_k = tr(W^k), Sec. 2 Eq. W_pow
   basis (module)    -- quantised spherical-harmonic basis T^_lm by Wigner 3j
                        symbols and by eigenvectors of the blocks, W from
-                       omega_lm and back, Sec. 3.2 Eqs. W0, Tlm, lap_prop
+                       omega_lm and back, Sec. 3.2 Eqs. 10-12
 
 Every function is pinned by tests/test_oracle_*.py against facts that do not
 come from this package (closed-form spectrum, the textbook spin-Casimir

@@ -1,19 +1,19 @@
-"""Oracle for the quantised spherical-harmonic basis (Sec. 3.2, Eqs. 15-16).
+"""Oracle for the quantised spherical-harmonic basis (Sec. 3.2, Eqs. 10-12).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/, never by the product path.
 
 * `wigner3j`: Wigner 3j symbols by Racah's closed formula, in exact integer
   and rational arithmetic (arguments doubled, so half-integers are exact);
   the square root is taken once at the end.
-* `that_lm`: the complex basis matrix T^_lm of Eq. 15,
+* `that_lm`: the complex basis matrix T^_lm of Eq. 11,
       (T^_lm)[i, j] = (-1)^(s - i) sqrt(2l+1) (s l s; -i m j),  s = (N-1)/2,
   with i, j in {-s, ..., s} and matrix row/column r = i + s, c = j + s (so
   T^_lm with m > 0 lies on the lower m-th diagonal, r - c = m).  The bracket
-  [(N-1)/2] of Eq. 15 is read as s itself: s - i is an integer for every i.
+  [(N-1)/2] of Eq. 11 is read as s itself: s - i is an integer for every i.
 * `that_lm_eig`: the same matrix from the eigenvector of the tridiagonal
-  block -Delta^m with eigenvalue l(l+1) (Eq. 13, 16; SciPy's banded symmetric
+  block -Delta^m with eigenvalue l(l+1) (Eqs. 12-13; SciPy's banded symmetric
   eigensolver), unit 2-norm, sign fixed by `SIGN_RULE`.
-* `w_from_omega`, `omega_from_w`: Eq. 17 (W = sum i omega_lm T^_lm) and its
+* `w_from_omega`, `omega_from_w`: Eq. 10 (W = sum i omega_lm T^_lm) and its
   inverse by orthonormality, omega_lm = -i tr(T^_lm^H W).
 """
 from __future__ import annotations
@@ -61,7 +61,7 @@ def wigner3j(j1: float, j2: float, j3: float, m1: float, m2: float, m3: float) -
 
 
 def that_lm(N: int, l: int, m: int) -> np.ndarray:
-    """T^_lm of Eq. 15 (real entries, N x N)."""
+    """T^_lm of Eq. 11 (real entries, N x N)."""
     s = (N - 1) / 2
     T = np.zeros((N, N))
     for r in range(N):
@@ -77,7 +77,7 @@ def that_lm(N: int, l: int, m: int) -> np.ndarray:
 def SIGN_RULE(N: int, l: int, m: int) -> int:
     """Sign of the last entry (position N - m - 1) of the m-th diagonal of T^_lm, m >= 0.
 
-    There i = s and j = s - m, so Eq. 15 reads sqrt(2l+1) (s l s; -s m s-m)
+    There i = s and j = s - m, so Eq. 11 reads sqrt(2l+1) (s l s; -s m s-m)
     times (-1)^(s-i) = 1.  Reflecting all m's, (j1 j2 j3; m1 m2 m3) =
     (-1)^(j1+j2+j3) (j1 j2 j3; -m1 -m2 -m3), gives (-1)^(2s+l) (s l s; s -m m-s),
     whose first column is stretched (m1 = j1): Racah's sum has the single
@@ -134,7 +134,7 @@ def omega_index(l: int, m: int) -> int:
 
 
 def w_from_omega(N: int, omega: np.ndarray, lmax: int) -> np.ndarray:
-    """W = sum_{l <= lmax} sum_m i omega_lm T^_lm (Eq. 17), T^_{l,-m} = (-1)^m T^_lm^T for m > 0."""
+    """W = sum_{l <= lmax} sum_m i omega_lm T^_lm (Eq. 10), T^_{l,-m} = (-1)^m T^_lm^T for m > 0."""
     W = np.zeros((N, N), dtype=np.complex128)
     for l in range(lmax + 1):
         for m in range(0, l + 1):

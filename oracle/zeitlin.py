@@ -5,8 +5,8 @@ P stream matrix, h time step, W_n the state at time level n, Wt the implicit
 midpoint matrix (W-tilde), Pt = Delta_N^{-1} Wt, k the fixed-point sweep.
 
 Readings of the paper taken here (the CUDA path takes the same ones):
-  * Sign of the blocks.  Eq. delta_tria prints a positive semidefinite
-    tridiagonal matrix, while Eq. lap_prop gives Delta_N the eigenvalues
+  * Sign of the blocks.  Eq. 13 prints a positive semidefinite
+    tridiagonal matrix, while Eq. 12 gives Delta_N the eigenvalues
     -l(l+1).  The printed matrix is taken as T_m = -Delta^m: the block of
     Delta_N on diagonal m is -T_m.
   * Diagonal indexing.  Diagonal m (0 <= m <= N-1) of a matrix A is the
@@ -44,13 +44,13 @@ __all__ = [
 
 
 def laplacian_block(N: int, m: int):
-    """Tridiagonal block T_m = -Delta^m of diagonal m (Sec. 3.2, Eq. delta_tria).
+    """Tridiagonal block T_m = -Delta^m of diagonal m (Sec. 3.2, Eq. 13).
 
     Returns (a, b): a[i] the diagonal entries, i = 0..N-m-1, and b[i] the
     symmetric off-diagonal entries T_m[i, i+1] = T_m[i+1, i], i = 0..N-m-2:
         a[i] = 2 (s (2i + 1 + m) - i (i + m)),             s = (N - 1)/2
         b[i] = -sqrt((i + m + 1)(N - 1 - i - m)) * sqrt((i + 1)(N - 1 - i)).
-    The delta_{i-1} term of Eq. delta_tria is the same expression with i
+    The delta_{i-1} term of Eq. 13 is the same expression with i
     shifted by one, so the block is symmetric.
     """
     if not (0 <= m <= N - 1):

@@ -1,9 +1,9 @@
-// Quantised spherical-harmonic basis (Sec. 3.2, Eqs. W0, Tlm, lap_prop).
+// Quantised spherical-harmonic basis (Sec. 3.2, Eqs. 10-12).
 //
 // T^_lm with m >= 0 lies on the m-th (lower) diagonal of an N x N matrix:
 // its entries there form the unit eigenvector of the tridiagonal block
-// -Delta^m (Eq. delta_tria) for the eigenvalue l(l+1), l = m .. N-1
-// (Eq. lap_prop), and T^_{l,-m} = (-1)^m T^_lm^T.  The sign follows Eq. Tlm:
+// -Delta^m (Eq. 13) for the eigenvalue l(l+1), l = m .. N-1
+// (Eq. 12), and T^_{l,-m} = (-1)^m T^_lm^T.  The sign follows Eq. 11:
 // the last entry of the diagonal carries (-1)^m (its Wigner 3j symbol has a
 // stretched column).
 //
@@ -18,7 +18,7 @@
 // which grows from that end into the bulk (the end entries themselves can be
 // below double precision).
 //
-// W = sum_lm i omega_lm T^_lm (Eq. W0) is banded (|m| <= lmax): one thread per
+// W = sum_lm i omega_lm T^_lm (Eq. 10) is banded (|m| <= lmax): one thread per
 // band element sums over l.  omega_lm = -i tr(T^_lm^T W) (orthonormal basis):
 // one warp per (l, m) reduces along its diagonal in a fixed order.
 #include <cmath>

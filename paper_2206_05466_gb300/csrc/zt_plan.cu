@@ -219,7 +219,7 @@ extern "C" int zt_plan_kernel_time(zt_plan* p, int kind, long* launches, double*
 }
 
 // ---------------------------------------------------------------------------
-// Constant per-diagonal data (Sec. 3.2, Eq. delta_tria) and LDL^T factors,
+// Constant per-diagonal data (Sec. 3.2, Eq. 13) and LDL^T factors,
 // computed once per plan on the host (the recurrence is sequential along each
 // diagonal; on the device it would compete for the FP64 pipe with running
 // work).  Entries go to packed lower-triangular arrays at (r, c) = (i + m, i).

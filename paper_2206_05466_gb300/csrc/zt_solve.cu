@@ -1,7 +1,7 @@
 // Stream solve P = Delta_N^{-1} W (Sec. 3.3, Eq. sub_tria_W), segmented.
 //
 // Diagonal m (0 <= m < N) of the lower triangle holds the N-m unknowns of the
-// tridiagonal system T_m x = -w (T_m = -Delta^m, Eq. delta_tria), solved with
+// tridiagonal system T_m x = -w (T_m = -Delta^m, Eq. 13), solved with
 // the plan's LDL^T factors:
 //     forward   z_i = w_i - l_i z_{i-1}                 (l_0 = 0)
 //     backward  x_i = nd_i z_i - l_{i+1} x_{i+1}         (nd_i = -1/d_i)

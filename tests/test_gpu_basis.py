@@ -1,4 +1,4 @@
-"""Quantised basis on the device against the oracle (Sec. 3.2, Eqs. W0, Tlm, lap_prop)."""
+"""Quantised basis on the device against the oracle (Sec. 3.2, Eqs. 10-12)."""
 import numpy as np
 import pytest
 

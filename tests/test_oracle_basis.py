@@ -1,4 +1,4 @@
-"""Pins of the quantised-basis oracle (Sec. 3.2, Eqs. W0, Tlm, lap_prop).
+"""Pins of the quantised-basis oracle (Sec. 3.2, Eqs. 10-12).
 
 Facts that do not come from the oracle: tabulated Wigner 3j values and their
 orthogonality relation, the Laplacian eigen-relation (with the Laplacian

@@ -1,7 +1,7 @@
 """Pins of the oracle's Laplacian blocks and stream solve (CPU only).
 
 The pins come from outside the oracle: the closed-form spectrum of Eq.
-lap_prop, hand-worked blocks of Eq. delta_tria, and the textbook spin-Casimir
+12, hand-worked blocks of Eq. 13, and the textbook spin-Casimir
 construction of Hoppe's Laplacian (tests/_spin.py), inverted densely.
 """
 import os
@@ -42,7 +42,7 @@ def test_blocks_match_hand_worked_golden():
 
 @pytest.mark.parametrize("N", [2, 3, 4, 5, 8, 13, 32])
 def test_block_spectrum_is_l_l_plus_1(N):
-    # Eq. lap_prop restricted to diagonal m: eigenvalues l(l+1), l = m..N-1.
+    # Eq. 12 restricted to diagonal m: eigenvalues l(l+1), l = m..N-1.
     for m in range(N):
         a, b = oracle.laplacian_block(N, m)
         T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
@@ -102,7 +102,7 @@ def test_stream_solve_roundtrip_and_structure(N):
 
 
 def test_stream_solve_eigenmodes():
-    # W in the l-eigenspace of Delta_N gives P = -W / (l(l+1)) (Eq. lap_prop).
+    # W in the l-eigenspace of Delta_N gives P = -W / (l(l+1)) (Eq. 12).
     N = 11
     S1, S2, S3 = _spin.spin_matrices(N)
     s = (N - 1) / 2
