@@ -102,7 +102,7 @@ ZT_API const char* zt_last_error(void);
  * O(N^2).  Errors: ZT_EINVAL, ZT_ECUDA. */
 ZT_API int zeitlin_laplacian_apply(zt_plan* plan, const double* P, double* W, void* stream);
 
-/* P = Delta_N^{-1} W for W in su(N) (Sec. 3.3, Eq. sub_tria_W): one
+/* P = Delta_N^{-1} W for W in su(N) (Sec. 3.3, Eq. 14): one
  * tridiagonal system per sub-diagonal m = 0..N-1, solved with the
  * precomputed factors; the l = 0 mode of the singular m = 0 block is
  * projected out (mean of the right-hand side and of the solution removed).
@@ -112,7 +112,7 @@ ZT_API int zeitlin_laplacian_apply(zt_plan* plan, const double* P, double* W, vo
 ZT_API int zeitlin_stream_solve(zt_plan* plan, const double* W, double* P, void* stream);
 
 /* One IsoMP step in place, W = W_n on entry, W_{n+1} on return (Sec. 2,
- * Eqs. isomp and isomp_iter; products as in Sec. 3.1).  Fixed-point sweeps
+ * Eqs. 8 and 9; products as in Sec. 3.1).  Fixed-point sweeps
  *   Pt = Delta_N^{-1} Wt,  A = Pt Wt,  B = A Pt,
  *   Wt <- W_n + h/2 (A - A^H) + h^2/4 B,   r = ||Wt_new - Wt_old||_F
  * from Wt = W_n until r < tol or maxit sweeps, then

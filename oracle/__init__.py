@@ -10,14 +10,15 @@ Contents (each function cites the passage of Cifani, Viviani & Modin,
 sphere", that it follows):
   laplacian_block   -- tridiagonal block of diagonal m, Sec. 3.2 Eq. 13
   laplacian_apply   -- W = Delta_N P, block by block, Sec. 3.2-3.3
-  stream_solve      -- P = Delta_N^{-1} W, Sec. 3.3 Eq. sub_tria_W
+  stream_solve      -- P = Delta_N^{-1} W, Sec. 3.3 Eq. 14
   isomp_step        -- one IsoMP step by fixed-point sweeps, Sec. 2 Eqs.
-                       isomp and isomp_iter, Sec. 3.1
+                       8 and 9, Sec. 3.1
   isomp_run         -- repeated steps
-  casimirs          -- C_k = tr(W^k), Sec. 2 Eq. W_pow
+  casimirs          -- C_k = tr(W^k), Sec. 2 Eq. 7
   basis (module)    -- quantised spherical-harmonic basis T^_lm by Wigner 3j
                        symbols and by eigenvectors of the blocks, W from
                        omega_lm and back, Sec. 3.2 Eqs. 10-12
+  spectrum (module) -- kinetic-energy spectrum E_l over the basis, Sec. 4
 
 Every function is pinned by tests/test_oracle_*.py against facts that do not
 come from this package (closed-form spectrum, the textbook spin-Casimir

@@ -16,12 +16,12 @@ Readings of the paper taken here (the CUDA path takes the same ones):
     l = 0 mode).  The l = 0 mode is projected out: the right-hand side has its
     mean removed, the leading N-1 equations are solved with x[N-1] = 0, and
     the mean of x is removed.  This equals -T_0^+ W_0 and gives tr P = 0.
-  * Third term of Eq. isomp_iter.  Read as Pt Wt Pt, the term obtained by
-    expanding the first line of Eq. isomp.
+  * Third term of Eq. 9.  Read as Pt Wt Pt, the term obtained by
+    expanding the first line of Eq. 8.
   * Stop rule.  Absolute Frobenius norm of Wt^{k+1} - Wt^k below tol, or
     maxit sweeps; Wt^0 = W_n.
   * Assembly of W_{n+1} ("fresh", default).  Pt, A = Pt Wt and B = A Pt are
-    recomputed from the last iterate before the second line of Eq. isomp is
+    recomputed from the last iterate before the second line of Eq. 8 is
     applied (Sec. 3.1 counts two products for W_{n+1} as well).  "reuse"
     instead takes A and B of the last sweep.
 """
@@ -76,7 +76,7 @@ def _tridiag_matvec(a, b, v):
 def laplacian_apply(P: np.ndarray) -> np.ndarray:
     """W = Delta_N P for any complex N x N matrix P (Sec. 3.2-3.3).
 
-    Delta_N acts on each diagonal separately (Eq. sub_tria_W): on the
+    Delta_N acts on each diagonal separately (Eq. 14): on the
     sub-diagonal m and on the super-diagonal -m it is the block -T_m.
     """
     P = np.asarray(P, dtype=np.complex128)
@@ -103,7 +103,7 @@ def _solve_spd_tridiag(a, b, rhs):
 
 
 def stream_solve(W: np.ndarray) -> np.ndarray:
-    """P = Delta_N^{-1} W for W in su(N) (Sec. 3.3, Eq. sub_tria_W).
+    """P = Delta_N^{-1} W for W in su(N) (Sec. 3.3, Eq. 14).
 
     For each diagonal m = 0..N-1 the lower diagonal P_m solves
     Delta^m P_m = W_m, i.e. P_m = -T_m^{-1} W_m; the l = 0 mode of the
@@ -143,13 +143,13 @@ class StepInfo:
 
 def isomp_step(Wn: np.ndarray, h: float, tol: float = 1e-12, maxit: int = 50,
                final: str = "fresh"):
-    """One isospectral-midpoint step W_n -> W_{n+1} (Sec. 2, Eqs. isomp, isomp_iter).
+    """One isospectral-midpoint step W_n -> W_{n+1} (Sec. 2, Eqs. 8, 9).
 
-    Fixed point (Eq. isomp_iter), with the two products of Sec. 3.1:
+    Fixed point (Eq. 9), with the two products of Sec. 3.1:
         Pt = Delta_N^{-1} Wt^k,  A = Pt Wt^k,  B = A Pt,
         Wt^{k+1} = W_n + h/2 (A - A^H) + h^2/4 B
     (Wt^k Pt = A^H because Pt and Wt are skew-Hermitian).  Then the second
-    line of Eq. isomp, W_{n+1} = Wt + h/2 (A - A^H) - h^2/4 B.
+    line of Eq. 8, W_{n+1} = Wt + h/2 (A - A^H) - h^2/4 B.
     Returns (W_{n+1}, StepInfo).
     """
     if final not in ("fresh", "reuse"):
@@ -197,7 +197,7 @@ def isomp_run(W0: np.ndarray, h: float, nsteps: int, tol: float = 1e-12,
 
 
 def casimirs(W: np.ndarray, ks=(2, 3, 4)):
-    """Discrete Casimirs C_k(W) = tr(W^k) (Sec. 2, Eq. W_pow)."""
+    """Discrete Casimirs C_k(W) = tr(W^k) (Sec. 2, Eq. 7)."""
     W = np.asarray(W, dtype=np.complex128)
     out = {}
     M = np.eye(W.shape[0], dtype=np.complex128)

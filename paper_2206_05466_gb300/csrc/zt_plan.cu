@@ -309,8 +309,8 @@ int zt_launch_laplacian(zt_plan* p, const double2* P, double2* W, cudaStream_t s
 
 
 // ---------------------------------------------------------------------------
-// Fixed-point update (Eq. isomp_iter with the products of Sec. 3.1) and the
-// assembly of W_{n+1} (second line of Eq. isomp):
+// Fixed-point update (Eq. 9 with the products of Sec. 3.1) and the
+// assembly of W_{n+1} (second line of Eq. 8):
 //   out = base + h/2 (A - A^H) + c2 B,     c2 = +h^2/4 (sweep), -h^2/4 (final)
 // computed on the lower triangle and mirrored (out stays skew-Hermitian; the
 // diagonal keeps its imaginary part only).  With `partials`, each CTA also
@@ -802,7 +802,7 @@ extern "C" int zeitlin_casimirs(zt_plan* p, const double* W, double* C, void* st
     return ZT_OK;
 }
 
-// One fixed-point sweep (Eq. isomp_iter): Pt = solve(Wt), A = Pt Wt,
+// One fixed-point sweep (Eq. 9): Pt = solve(Wt), A = Pt Wt,
 // B = A Pt, Wt <- W_n + h/2 (A - A^H) + h^2/4 B, residual, stop decision.
 // Pt = solve(Wt), A = Pt Wt, B = A Pt (lower half).  In split form Pt is
 // split once into both operand forms.
@@ -830,7 +830,7 @@ static int enqueue_sweep(zt_plan* p, int k, double h, cudaStream_t s) {
     return launch_check(p, "converge_kernel");
 }
 
-// Second line of Eq. isomp; runs only once the sweeps are done.
+// Second line of Eq. 8; runs only once the sweeps are done.
 static int enqueue_final(zt_plan* p, int tag, double2* W, double h, cudaStream_t s) {
     int rc;
     p->cur_sweep = tag;

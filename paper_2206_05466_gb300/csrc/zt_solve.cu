@@ -1,4 +1,4 @@
-// Stream solve P = Delta_N^{-1} W (Sec. 3.3, Eq. sub_tria_W), segmented.
+// Stream solve P = Delta_N^{-1} W (Sec. 3.3, Eq. 14), segmented.
 //
 // Diagonal m (0 <= m < N) of the lower triangle holds the N-m unknowns of the
 // tridiagonal system T_m x = -w (T_m = -Delta^m, Eq. 13), solved with

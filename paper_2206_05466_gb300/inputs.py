@@ -7,8 +7,8 @@ The paper's own initial condition (random spherical-harmonic coefficients
 omega_lm for 2 <= l <= 20, Sec. 4) needs the quantised basis of Sec. 3.2. The
 stand-in used everywhere in this project is a seeded vorticity matrix with the
 same structure the method relies on: W0 is traceless and skew-Hermitian
-(W0 in su(N), Eq. Euler_vort_mat) and normalised in the spectral norm, as the
-paper states its initial vorticity always is (Sec. 2, after Eq. isomp_iter).
+(W0 in su(N), Eq. 6) and normalised in the spectral norm, as the
+paper states its initial vorticity always is (Sec. 2, after Eq. 9).
 
 Recipe (fixed, in this order):
   1. g = a + i b, a and b (N x N) standard normal draws from

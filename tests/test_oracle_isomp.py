@@ -2,11 +2,11 @@
 
 The step is an iteration, so it is pinned by what the paper and the algebra
 fix rather than by stored trajectories:
-  * both lines of Eq. isomp, re-evaluated with explicit products and a
+  * both lines of Eq. 8, re-evaluated with explicit products and a
     stream matrix from the dense spin-Casimir pseudo-inverse;
   * steady states (W inside one l-eigenspace, and every W at N = 2);
   * second-order agreement with an independent RK4 integration of
-    Eq. Euler_vort_mat (this fixes the direction of time);
+    Eq. 6 (this fixes the direction of time);
   * reversibility, isospectrality and Casimir conservation (Sec. 2);
   * preservation of su(N).
 A few tests plant a mistake in a copy of the step and check that the pins
@@ -22,7 +22,7 @@ from tests import _spin
 
 
 def _isomp_lines(Wn, Wnp1, Wt, N, h):
-    """Residuals of both lines of Eq. isomp with an independent stream matrix."""
+    """Residuals of both lines of Eq. 8 with an independent stream matrix."""
     Pt = (_spin.dense_pseudo_inverse(N) @ Wt.reshape(-1)).reshape(N, N)
     I = np.eye(N)
     first = (I - h / 2 * Pt) @ Wt @ (I + h / 2 * Pt)
@@ -40,7 +40,7 @@ def test_both_lines_of_isomp_hold(N, h):
 
 
 def _step_dropped_h2(Wn, h, tol=1e-14, maxit=100):
-    # planted mistake: the h^2/4 term of Eq. isomp_iter is dropped
+    # planted mistake: the h^2/4 term of Eq. 9 is dropped
     Wt = Wn.copy()
     for _ in range(maxit):
         Pt = oz.stream_solve(Wt)
@@ -88,7 +88,7 @@ def test_steady_states():
 
 
 def _rk4_reference(W0, t, nsub):
-    """Independent integration of dW/dt = [P, W], Delta_N P = W (Eq. Euler_vort_mat)."""
+    """Independent integration of dW/dt = [P, W], Delta_N P = W (Eq. 6)."""
     N = W0.shape[0]
     Linv = _spin.dense_pseudo_inverse(N)
 
