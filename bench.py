@@ -250,7 +250,8 @@ def _casimir_drift(W0, W1, ks=(2, 3, 4)):
 
 
 def run_casimir(args):
-    """Long run: Casimir and spectrum drift after --steps steps, split and (optionally) FP64 form."""
+    """Long run: Casimir, eigenvalue and energy drift after --steps steps, split and (optionally) FP64
+    form, with the on-device Casimirs and kinetic-energy spectrum timed."""
     import torch
 
     import numpy as np
@@ -271,6 +272,7 @@ def run_casimir(args):
             plan = z.Plan(N, prec)
         W = torch.from_numpy(W0).cuda()
         c0 = z.zeitlin_casimirs(plan, W)   # on the device, the plan's products
+        E0 = z.zeitlin_energy_spectrum(plan, W).cpu().numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = z.isomp_run(plan, W, H, steps, TOL, MAXIT)
@@ -279,12 +281,23 @@ def run_casimir(args):
         tc = time.perf_counter()
         c1 = z.zeitlin_casimirs(plan, W)
         t_cas = time.perf_counter() - tc
+        st = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(st)
+        E1 = z.zeitlin_energy_spectrum(plan, W)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        t_spec = ev0.elapsed_time(ev1)
+        E1 = E1.cpu().numpy()
         W1 = W.cpu().numpy()
         drift = _casimir_drift(W0, W1)
         mu0 = np.abs(np.linalg.eigvalsh(-1j * W0))
         dev = {f"C{k}": float(abs(c1[k] - c0[k]) / np.sum(mu0 ** k)) for k in (2, 3, 4, 5)}
         res[name] = {"steps_per_s": steps / dt, "run_stats": r, "drift": drift,
                      "device_casimir_drift": dev, "device_casimirs_ms": t_cas * 1e3,
+                     "device_spectrum_ms": t_spec,
+                     "energy_rel_drift": float(abs(E1.sum() - E0.sum()) / E0.sum()),
+                     "spectrum_l_peak": [int(np.argmax(E0)), int(np.argmax(E1))],
                      "trace_abs": float(abs(W1.trace())), "skew_err": float(abs(W1 + W1.conj().T).max())}
         plan.close()
     print(json.dumps(res), flush=True)

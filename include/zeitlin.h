@@ -147,6 +147,15 @@ ZT_API int zt_zgemm_skew(zt_plan* plan, const double* X, const double* Y, double
  * as for the other calls (ZT_ETIMEOUT if a bounded device wait ran out). */
 ZT_API int zeitlin_casimirs(zt_plan* plan, const double* W, double* C, void* stream);
 
+/* Kinetic-energy spectrum (Sec. 4; basis of Sec. 3.2): E_l = sum_{|m| <= l}
+ * |omega_lm|^2 / (2 l (l+1)) for l = 1 .. N-1 and E_0 = 0, with omega_lm the
+ * coefficients of W in the quantised basis (Eq. 10) over every l <= N-1; the
+ * E_l sum to the Hamiltonian (1/2) tr(P W), P = Delta_N^{-1} W.  W: device
+ * N x N complex128; E: DEVICE array of N doubles.  Asynchronous on the
+ * stream; uses the plan's step workspace (not concurrently with a step of the
+ * same plan).  About N^3/6 FP64 recurrence steps (no eigenvector is stored). */
+ZT_API int zeitlin_energy_spectrum(zt_plan* plan, const double* W, double* E, void* stream);
+
 /* ---- Quantised spherical-harmonic basis (Sec. 3.2, Eqs. 10-12) ----
  * T^_lm (0 <= m <= l) lies on the m-th lower diagonal; its entries there are
  * the unit eigenvector of the block -Delta^m for the eigenvalue l(l+1), with

@@ -107,6 +107,8 @@ def load(build_if_missing: bool = True):
     L.zeitlin_w_from_omega.restype = i
     L.zeitlin_omega_from_w.argtypes = [vp, vp, vp, vp]
     L.zeitlin_omega_from_w.restype = i
+    L.zeitlin_energy_spectrum.argtypes = [vp, vp, vp, vp]
+    L.zeitlin_energy_spectrum.restype = i
     L.zt_plan_launch_count.argtypes = [vp]
     L.zt_plan_launch_count.restype = l
     L.zt_plan_set_timing.argtypes = [vp, i]
@@ -294,6 +296,20 @@ def zeitlin_omega_from_w(basis: Basis, W, omega, stream=None):
     _check(load().zeitlin_omega_from_w(basis.handle, _ptr(W, basis.N), _ptr_flat(omega, (basis.lmax + 1) ** 2),
                                        _stream(stream)))
     return omega
+
+
+def zeitlin_energy_spectrum(plan: Plan, W, E=None, stream=None):
+    """E_l = sum_m |omega_lm|^2 / (2 l(l+1)), l = 0..N-1 (E_0 = 0), as a float64 CUDA tensor."""
+    import torch
+
+    if E is None:
+        E = torch.empty(plan.N, dtype=torch.float64, device=W.device)
+    if not isinstance(E, torch.Tensor) or E.dtype != torch.float64 or not E.is_cuda or E.numel() != plan.N \
+            or not E.is_contiguous():
+        raise ValueError(f"E must be a contiguous float64 CUDA tensor of {plan.N} entries")
+    _check(load().zeitlin_energy_spectrum(plan.handle, _ptr(W, plan.N), ctypes.c_void_p(E.data_ptr()),
+                                          _stream(stream)))
+    return E
 
 
 def zt_zgemm_skew(plan: Plan, X, Y, C, stream=None):

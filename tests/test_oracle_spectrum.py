@@ -45,10 +45,40 @@ def test_parseval_and_hamiltonian(N):
     E = energy_spectrum(W)
     l = np.arange(N)
     # orthonormal basis: sum_lm |omega_lm|^2 = ||W||_F^2 (omega_00 = 0 in su(N))
-    assert abs(np.sum(2 * l * (l + 1) * E) - np.linalg.norm(W) ** 2) < 1e-12 * np.linalg.norm(W) ** 2
+    fro2 = np.sum(W.real ** 2 + W.imag ** 2)
+    assert abs(np.sum(2 * l * (l + 1) * E) - fro2) < 1e-12 * fro2
     # the E_l sum to the Hamiltonian (1/2) tr(P W), P = Delta_N^{-1} W
     P = oracle.stream_solve(W)
     H = 0.5 * np.trace(P @ W)
     assert abs(H.imag) < 1e-12 * abs(H.real)
     assert abs(E.sum() - H.real) < 1e-12 * abs(H.real)
     assert (E >= 0).all()
+
+
+@pytest.mark.parametrize("N,L", [(2, 1), (5, 4), (33, 8), (128, 6), (129, 12)])
+def test_extended_low_modes_equal_the_eigensolver_route(N, L):
+    from oracle.spectrum import energy_spectrum_low
+    W = vorticity_w0(N, seed=9)
+    full = energy_spectrum(W)
+    low = energy_spectrum_low(W, L).astype(np.float64)
+    assert low[0] == 0.0
+    assert np.abs(low[1:] - full[1:L + 1]).max() <= 1e-12 * full[1:L + 1].max()
+
+
+def test_extended_low_modes_known_coefficients():
+    from oracle.spectrum import energy_spectrum_low
+    N = 9
+    om = paper_omega(N - 1, lmin=1, seed=3)
+    E = energy_spectrum_low(basis.w_from_omega(N, om, N - 1), 5).astype(np.float64)
+    for l in range(1, 6):
+        want = sum(abs(om[l * l + l + m]) ** 2 for m in range(-l, l + 1)) / (2 * l * (l + 1))
+        assert abs(E[l] - want) < 1e-14 * want
+
+
+@pytest.mark.parametrize("N", [2, 5, 8, 11])
+def test_reflection_parity_of_the_3j_basis(N):
+    # the half-vector routes rely on x_{n-1-i} = (-1)^(l-m) x_i along the diagonal (Eq. 11)
+    for l in range(N):
+        for m in range(l + 1):
+            v = np.diag(basis.that_lm(N, l, m), -m)
+            assert np.abs(v[::-1] - (-1) ** (l - m) * v).max() < 1e-14, (l, m)
