@@ -30,6 +30,7 @@ N_DEFAULT = 4096
 H = 0.005
 TOL = 1e-12
 MAXIT = 50
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal rate; no measured FP64 peak is available
 
 # DRAM traffic of the split product kernel per launch (mean over one IsoMP step), from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
@@ -304,6 +305,51 @@ def run_casimir(args):
     return 0
 
 
+def run_spectrum(args):
+    """Kinetic-energy spectrum alone (zeitlin_energy_spectrum at --n): time per call on the
+    stream with CUDA events, and its FP64 rate against the nominal FP64 peak."""
+    import torch
+
+    from paper_2206_05466_gb300 import zeitlin as z
+    from paper_2206_05466_gb300.inputs import vorticity_w0
+
+    torch.cuda.set_device(0)
+    N = args.n
+    plan = z.Plan(N)
+    W = torch.from_numpy(vorticity_w0(N, seed=0)).cuda()
+    E = torch.empty(N, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        z.zeitlin_energy_spectrum(plan, W, E)
+    torch.cuda.synchronize()
+    clk = ClockSampler(0)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    for _ in range(args.steps):
+        z.zeitlin_energy_spectrum(plan, W, E)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # algorithmic FP64 work per (l, m): half accumulation steps (3 FMA: the complex dot
+    # product with the folded lower diagonal and the norm) and half - 1 recurrence steps
+    # (2 FMA + 3 MUL) over the half diagonal, half = ceil((N - m) / 2)
+    flops = 0
+    for m in range(N):
+        half = (N - m + 1) // 2
+        flops += (N - m) * (6 * half + 7 * (half - 1))
+    tf = flops / (ms * 1e-3) / 1e12
+    out = {"mode": "spectrum", "N": N, "calls": args.steps, "warmup": args.warmup, "ms_per_call": ms,
+           "gpu_launches_per_call": 2, "fp64_flop_per_call": flops,
+           "roofline": {"bound": "fp64", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                        "frac": tf / FP64_NOMINAL_TFLOPS, "peak_kind": "nominal"},
+           "total_energy": float(E.sum().item()), "clocks": clocks, "data": "synthetic"}
+    plan.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def _ensemble(args, tun, steps, graph=True):
     """Ensemble of independent instances advanced by grouped (batched) steps."""
     import numpy as np
@@ -558,7 +604,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--mode", default="bench", choices=["bench", "casimir", "ensemble", "serving", "profile"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "casimir", "ensemble", "serving", "profile", "spectrum"])
     ap.add_argument("--ens-count", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=20)
     ap.add_argument("--serve-seconds", type=float, default=20.0)
@@ -585,6 +631,8 @@ def main():
         return run_casimir(args)
     if args.mode == "profile":
         return run_profile(args)
+    if args.mode == "spectrum":
+        return run_spectrum(args)
     if args.mode in ("ensemble", "serving"):
         import torch
 

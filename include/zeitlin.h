@@ -151,7 +151,9 @@ ZT_API int zeitlin_casimirs(zt_plan* plan, const double* W, double* C, void* str
  * |omega_lm|^2 / (2 l (l+1)) for l = 1 .. N-1 and E_0 = 0, with omega_lm the
  * coefficients of W in the quantised basis (Eq. 10) over every l <= N-1; the
  * E_l sum to the Hamiltonian (1/2) tr(P W), P = Delta_N^{-1} W.  W: device
- * N x N complex128; E: DEVICE array of N doubles.  Asynchronous on the
+ * N x N complex128 in su(N) (skew-Hermitian: only the lower triangle and the
+ * diagonal are read, |omega_{l,-m}| = |omega_lm|); E: DEVICE array of N
+ * doubles.  Asynchronous on the
  * stream; uses the plan's step workspace (not concurrently with a step of the
  * same plan).  About N^3/6 FP64 recurrence steps (no eigenvector is stored). */
 ZT_API int zeitlin_energy_spectrum(zt_plan* plan, const double* W, double* E, void* stream);

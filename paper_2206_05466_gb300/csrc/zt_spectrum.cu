@@ -3,8 +3,10 @@
 // E_l = sum_{|m| <= l} |omega_lm|^2 / (2 l (l+1)), l >= 1, E_0 = 0, where
 // |omega_{l,+-m}| = |v^T w_{+-m}| / |v| for the eigenvector v of the block
 // -Delta^m (Eq. 13) at the eigenvalue l(l+1) (Eq. 12), and w_{+-m} are the
-// diagonals +-m of W (lower: W[i+m, i], upper: W[i, i+m]).  The E_l sum to
-// the Hamiltonian (1/2) tr(P W), P = Delta_N^{-1} W.
+// diagonals +-m of W (lower: W[i+m, i], upper: W[i, i+m]).  For W in su(N)
+// the upper diagonal is -conj of the lower, so |omega_{l,-m}| = |omega_lm|
+// and only the lower triangle is read.  The E_l sum to the Hamiltonian
+// (1/2) tr(P W), P = Delta_N^{-1} W.
 //
 // Every eigenvector of every block takes part (N^3/3 work) and none is stored.
 //
@@ -34,7 +36,7 @@
 // to the bulk).
 //
 // One thread per (l, m): a CTA holds 128 consecutive l of one m and stages
-// p_i, q_i, their reciprocals and the folded diagonals in shared memory, 128
+// p_i, q_i, their reciprocals and the folded diagonal in shared memory, 128
 // positions at a time, so the inner loop is FP64 FMAs on broadcast
 // shared-memory operands with no division.  Per-(l, m) energies go to a
 // packed triangle in the plan's workspace; a second kernel sums them over m
@@ -57,10 +59,10 @@ __global__ void __launch_bounds__(SP_TH) spectrum_pairs_kernel(const double2* __
     const int half = (n + 1) >> 1;
     const int par = (l - m) & 1;   // 0: even about the centre, 1: odd
     __shared__ double s_p[SP_TH], s_rp[SP_TH], s_q[SP_TH], s_rq[SP_TH];
-    __shared__ double2 s_f[4][SP_TH];   // lower even, lower odd, upper even, upper odd
+    __shared__ double2 s_f[2][SP_TH];   // folded lower diagonal: even, odd
     const double mu = (double)(l - m) * (double)(l + m + 1);
     double x = 1.0, g = 0.0, qprev = 0.0, nrm = 0.0;
-    double lr = 0.0, li = 0.0, ur = 0.0, ui = 0.0;
+    double lr = 0.0, li = 0.0;
     for (int i0 = 0; i0 < half; i0 += SP_TH) {
         __syncthreads();   // the previous chunk is consumed
         const int i = i0 + tid;
@@ -73,31 +75,24 @@ __global__ void __launch_bounds__(SP_TH) spectrum_pairs_kernel(const double2* __
             s_q[tid] = qv;
             s_rq[tid] = 1.0 / qv;
             const int j = n - 1 - i;
-            const double2 lo_i = W[(size_t)(i + m) * N + i], up_i = W[(size_t)i * N + i + m];
+            const double2 lo_i = W[(size_t)(i + m) * N + i];
             if (i == j) {   // centre of an odd-length diagonal: counted once, zero in odd vectors
                 s_f[0][tid] = lo_i;
                 s_f[1][tid] = make_double2(0.0, 0.0);
-                s_f[2][tid] = up_i;
-                s_f[3][tid] = make_double2(0.0, 0.0);
             } else {
-                const double2 lo_j = W[(size_t)(j + m) * N + j], up_j = W[(size_t)j * N + j + m];
+                const double2 lo_j = W[(size_t)(j + m) * N + j];
                 s_f[0][tid] = make_double2(lo_i.x + lo_j.x, lo_i.y + lo_j.y);
                 s_f[1][tid] = make_double2(lo_i.x - lo_j.x, lo_i.y - lo_j.y);
-                s_f[2][tid] = make_double2(up_i.x + up_j.x, up_i.y + up_j.y);
-                s_f[3][tid] = make_double2(up_i.x - up_j.x, up_i.y - up_j.y);
             }
         }
         __syncthreads();
         if (active) {
             const int cnt = min(SP_TH, half - i0);
             const double2* fl = s_f[par];
-            const double2* fu = s_f[2 + par];
             for (int k = 0; k < cnt; ++k) {
-                const double2 wl = fl[k], wu = fu[k];
+                const double2 wl = fl[k];
                 lr = fma(x, wl.x, lr);
                 li = fma(x, wl.y, li);
-                ur = fma(x, wu.x, ur);
-                ui = fma(x, wu.y, ui);
                 nrm = fma(x, x, nrm);
                 if (i0 + k + 1 < half) {
                     const double pk = s_p[k];
@@ -110,8 +105,6 @@ __global__ void __launch_bounds__(SP_TH) spectrum_pairs_kernel(const double2* __
                         g *= 0x1p-400;
                         lr *= 0x1p-400;
                         li *= 0x1p-400;
-                        ur *= 0x1p-400;
-                        ui *= 0x1p-400;
                         nrm *= 0x1p-800;
                     }
                 }
@@ -124,7 +117,7 @@ __global__ void __launch_bounds__(SP_TH) spectrum_pairs_kernel(const double2* __
     double full = 2.0 * nrm;
     if (n & 1) full -= (par ? 2.0 : 1.0) * x * x;
     double num = lr * lr + li * li;
-    if (m > 0) num += ur * ur + ui * ui;   // diagonal 0 is its own mirror
+    if (m > 0) num *= 2.0;   // omega_{l,-m}: the mirrored upper diagonal (diagonal 0 is its own)
     e[zt_tri(l, m)] = num / full;
 }
 

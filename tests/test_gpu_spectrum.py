@@ -31,14 +31,17 @@ def test_spectrum_equals_oracle(N):
         assert np.abs(E[1:L + 1] / low[1:] - 1).max() < 1e-13
 
 
-def test_spectrum_of_a_general_complex_matrix():
-    # both diagonals of every m enter separately (W need not be skew-Hermitian)
+def test_spectrum_reads_only_the_lower_triangle():
+    # W in su(N): the upper diagonals are -conj of the lower ones and are not read
     N = 70
-    rng = np.random.default_rng(2)
-    W = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    W = vorticity_w0(N, seed=2)
     plan = z.Plan(N)
     E = z.zeitlin_energy_spectrum(plan, torch.from_numpy(W).cuda()).cpu().numpy()
+    Wc = W.copy()
+    Wc[np.triu_indices(N, 1)] = 123.0 - 7.0j
+    Ec = z.zeitlin_energy_spectrum(plan, torch.from_numpy(Wc).cuda()).cpu().numpy()
     plan.close()
+    assert np.array_equal(E, Ec)
     assert (np.abs(E[1:] - energy_spectrum(W)[1:]) <= _tol(W, N)).all()
 
 
