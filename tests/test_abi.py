@@ -45,6 +45,14 @@ def test_argument_validation_on_host():
     assert L.zt_plan_create(8, 0, None, None) == z.ZT_EINVAL
     assert L.zeitlin_stream_solve(None, None, None, None) == z.ZT_EINVAL
     assert L.isomp_step(None, None, 0.01, 1e-12, 50, None, None) == z.ZT_EINVAL
+    assert L.zeitlin_casimirs(None, None, None, None) == z.ZT_EINVAL
+    assert L.zeitlin_energy_spectrum(None, None, None, None) == z.ZT_EINVAL
+    assert L.zt_basis_create(None, 3, ctypes.byref(h)) == z.ZT_EINVAL and not h.value
+    assert L.zt_basis_create(None, 3, None) == z.ZT_EINVAL
+    assert L.zt_basis_vector(None, 0, 0, None) == z.ZT_EINVAL
+    assert L.zeitlin_w_from_omega(None, None, None, None) == z.ZT_EINVAL
+    assert L.zeitlin_omega_from_w(None, None, None, None) == z.ZT_EINVAL
+    L.zt_basis_destroy(None)   # no-op
 
 
 @pytest.mark.parametrize("bad", [dict(slices=2), dict(slices=9), dict(digit_bits=5), dict(digit_bits=9),

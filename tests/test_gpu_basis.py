@@ -87,3 +87,19 @@ def test_basis_outlives_its_plan():
     assert np.array_equal(B.vector(5, 2), want)
     B.close()
     assert np.abs(W.cpu().numpy() - ob.w_from_omega(N, om.cpu().numpy(), lmax)).max() < 1e-13
+
+
+def test_basis_argument_checks():
+    plan = z.Plan(8)
+    for bad in (8, -1):
+        with pytest.raises(z.ZeitlinError):
+            z.Basis(plan, bad)
+    B = z.Basis(plan, 3)
+    for l, m in ((2, 3), (4, 0), (1, -1)):
+        with pytest.raises(z.ZeitlinError):
+            B.vector(l, m)
+    W = torch.empty((8, 8), dtype=torch.complex128, device="cuda")
+    with pytest.raises(ValueError):
+        z.zeitlin_w_from_omega(B, torch.zeros(15, dtype=torch.complex128, device="cuda"), W)
+    B.close()
+    plan.close()
