@@ -195,7 +195,7 @@ struct SplitArgs {     // tcgen05 split product (zt_split.cu)
     int gate;
 };
 
-struct alignas(64) GemmEntry {   // grouped split product: tensor maps live in global memory
+struct GemmEntry {   // grouped split product: tensor maps live in global memory (aligned like CUtensorMap)
     CUtensorMap tmA;
     CUtensorMap tmB;
     SplitArgs a;
