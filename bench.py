@@ -334,11 +334,11 @@ def run_spectrum(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     # algorithmic FP64 work per (l, m): half accumulation steps (3 FMA: the complex dot
     # product with the folded lower diagonal and the norm) and half - 1 recurrence steps
-    # (2 FMA + 3 MUL) over the half diagonal, half = ceil((N - m) / 2)
+    # (2 FMA + 2 MUL) over the half diagonal, half = ceil((N - m) / 2)
     flops = 0
     for m in range(N):
         half = (N - m + 1) // 2
-        flops += (N - m) * (6 * half + 7 * (half - 1))
+        flops += (N - m) * (6 * half + 6 * (half - 1))
     tf = flops / (ms * 1e-3) / 1e12
     out = {"mode": "spectrum", "N": N, "calls": args.steps, "warmup": args.warmup, "ms_per_call": ms,
            "gpu_launches_per_call": 2, "fp64_flop_per_call": flops,

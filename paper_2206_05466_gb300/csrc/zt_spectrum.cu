@@ -19,7 +19,10 @@
 // At l(l+1) the shifted eigenvalue mu = (l-m)(l+m+1) is an exact integer and
 // the eigenvector x follows from C x = g, C^T g = mu x read row by row:
 //     g_i     = (mu x_i - q_{i-1} g_{i-1}) / p_i,
-//     x_{i+1} = (g_i - p_i x_i) / q_i,           x_0 = 1, g_{-1} = 0.
+//     x_{i+1} = (g_i - p_i x_i) / q_i,           x_0 = 1, g_{-1} = 0,
+// carried as G_i = g_i / q_i (4 FP64 instructions per step):
+//     G_i     = (mu x_i - Q_i G_{i-1}) d_i,   Q_i = q_{i-1}^2 = i (N - i) exact,
+//     x_{i+1} = G_i - r_i x_i,                 d_i = 1 / (p_i q_i), r_i = p_i / q_i.
 // No step subtracts quantities of size N^2 to leave one of size l(l+1), as
 // the three-term recurrence of the tridiagonal rows would (its low-l
 // eigenvectors lose accuracy like N^2 eps); these factors fix the small
@@ -31,12 +34,12 @@
 // diagonal to its centre only: the oscillatory range of the eigenvector is a
 // central interval, and outside it the recurrence runs in the growing
 // direction.  Folded diagonals w_i +- w_{n-1-i} turn the full dot product
-// into one over the half.  x and g are rescaled by 2^-400 whenever |x|
+// into one over the half.  x and G are rescaled by 2^-400 whenever |x|
 // passes 2^400 (the end entries can be far below the double range relative
 // to the bulk).
 //
 // One thread per (l, m): a CTA holds 128 consecutive l of one m and stages
-// p_i, q_i, their reciprocals and the folded diagonal in shared memory, 128
+// Q_i, d_i, r_i and the folded diagonal in shared memory, 128
 // positions at a time, so the inner loop is FP64 FMAs on broadcast
 // shared-memory operands with no division.  Per-(l, m) energies go to a
 // packed triangle in the plan's workspace; a second kernel sums them over m
@@ -58,22 +61,21 @@ __global__ void __launch_bounds__(SP_TH) spectrum_pairs_kernel(const double2* __
     const bool active = l <= N - 1;
     const int half = (n + 1) >> 1;
     const int par = (l - m) & 1;   // 0: even about the centre, 1: odd
-    __shared__ double s_p[SP_TH], s_rp[SP_TH], s_q[SP_TH], s_rq[SP_TH];
+    __shared__ double s_Q[SP_TH], s_d[SP_TH], s_r[SP_TH];
     __shared__ double2 s_f[2][SP_TH];   // folded lower diagonal: even, odd
     const double mu = (double)(l - m) * (double)(l + m + 1);
-    double x = 1.0, g = 0.0, qprev = 0.0, nrm = 0.0;
+    double x = 1.0, G = 0.0, nrm = 0.0;
     double lr = 0.0, li = 0.0;
     for (int i0 = 0; i0 < half; i0 += SP_TH) {
         __syncthreads();   // the previous chunk is consumed
         const int i = i0 + tid;
         if (i < half) {
-            // p_i, q_i for i <= half - 2 < n - 1 are nonzero (only those are read)
+            // p_i, q_i are nonzero for i <= half - 2 < n - 1 (only those steps run)
             const double pv = sqrt((double)(i + m + 1) * (double)(N - 1 - i - m));
             const double qv = -sqrt((double)(i + 1) * (double)(N - 1 - i));
-            s_p[tid] = pv;
-            s_rp[tid] = (pv != 0.0) ? 1.0 / pv : 0.0;
-            s_q[tid] = qv;
-            s_rq[tid] = 1.0 / qv;
+            s_Q[tid] = (double)i * (double)(N - i);
+            s_d[tid] = (pv != 0.0 && qv != 0.0) ? 1.0 / (pv * qv) : 0.0;
+            s_r[tid] = (qv != 0.0) ? pv / qv : 0.0;
             const int j = n - 1 - i;
             const double2 lo_i = W[(size_t)(i + m) * N + i];
             if (i == j) {   // centre of an odd-length diagonal: counted once, zero in odd vectors
@@ -95,14 +97,12 @@ __global__ void __launch_bounds__(SP_TH) spectrum_pairs_kernel(const double2* __
                 li = fma(x, wl.y, li);
                 nrm = fma(x, x, nrm);
                 if (i0 + k + 1 < half) {
-                    const double pk = s_p[k];
-                    g = fma(-qprev, g, mu * x) * s_rp[k];
-                    const double xn = fma(-pk, x, g) * s_rq[k];
-                    qprev = s_q[k];
+                    G = fma(-s_Q[k], G, mu * x) * s_d[k];
+                    const double xn = fma(-s_r[k], x, G);
                     x = xn;
                     if ((__double2hiint(xn) & 0x7ff00000) > ((1023 + 400) << 20)) {
                         x *= 0x1p-400;
-                        g *= 0x1p-400;
+                        G *= 0x1p-400;
                         lr *= 0x1p-400;
                         li *= 0x1p-400;
                         nrm *= 0x1p-800;
