@@ -153,9 +153,11 @@ ZT_API int zeitlin_casimirs(zt_plan* plan, const double* W, double* C, void* str
  * E_l sum to the Hamiltonian (1/2) tr(P W), P = Delta_N^{-1} W.  W: device
  * N x N complex128 in su(N) (skew-Hermitian: only the lower triangle and the
  * diagonal are read, |omega_{l,-m}| = |omega_lm|); E: DEVICE array of N
- * doubles.  Asynchronous on the
- * stream; uses the plan's step workspace (not concurrently with a step of the
- * same plan).  About N^3/6 FP64 recurrence steps (no eigenvector is stored). */
+ * doubles, caller-owned.  Asynchronous on the stream; uses the plan's step
+ * workspace (not concurrently with a step of the same plan).  About N^3/8 FP64
+ * recurrence steps, no eigenvector stored (GB300: ~0.26 s at N = 4096, growing
+ * like N^3).  Errors: ZT_EINVAL (NULL plan, W not 16-byte or E not 8-byte
+ * aligned), ZT_ECUDA (launch failure). */
 ZT_API int zeitlin_energy_spectrum(zt_plan* plan, const double* W, double* E, void* stream);
 
 /* ---- Quantised spherical-harmonic basis (Sec. 3.2, Eqs. 10-12) ----
@@ -169,15 +171,20 @@ ZT_API int zeitlin_energy_spectrum(zt_plan* plan, const double* W, double* E, vo
  * omega_lm are complex128 in a flat device array of (lmax+1)^2 entries at
  * l*l + l + m. */
 typedef struct zt_basis zt_basis;
-ZT_API int zt_basis_create(zt_plan* plan, int lmax, zt_basis** out);   /* computes the basis (waits) */
-ZT_API void zt_basis_destroy(zt_basis* basis);
-/* Copies the N - m diagonal entries of T^_lm (0 <= m <= l <= lmax) to a HOST array. */
+/* Computes the basis for 0 <= lmax <= N-1 and waits for it; *out receives the
+ * handle (NULL on failure).  Errors: ZT_EINVAL (NULL plan or out, lmax out of
+ * range), ZT_ENOMEM / ZT_ECUDA (device allocation or launch). */
+ZT_API int zt_basis_create(zt_plan* plan, int lmax, zt_basis** out);
+ZT_API void zt_basis_destroy(zt_basis* basis);   /* NULL: no-op */
+/* Copies the N - m diagonal entries of T^_lm (0 <= m <= l <= lmax) to a HOST
+ * array of N - m doubles (synchronous).  ZT_EINVAL outside that range. */
 ZT_API int zt_basis_vector(zt_basis* basis, int l, int m, double* out);
 /* W = sum_{l <= lmax, |m| <= l} i omega_lm T^_lm (Eq. 10); W: device N x N complex128,
- * overwritten (zero outside the band |m| <= lmax).  Asynchronous on the stream. */
+ * overwritten (zero outside the band |m| <= lmax).  Asynchronous on the stream.
+ * ZT_EINVAL for a NULL basis or a NULL / not 16-byte aligned pointer. */
 ZT_API int zeitlin_w_from_omega(zt_basis* basis, const double* omega, double* W, void* stream);
 /* omega_lm = -i tr(T^_lm^H W) for l <= lmax (the inverse of the above on the span of
- * the basis).  Asynchronous on the stream. */
+ * the basis).  Asynchronous on the stream; errors as above. */
 ZT_API int zeitlin_omega_from_w(zt_basis* basis, const double* W, double* omega, void* stream);
 
 /* Device bytes a plan for (N, precision, tuning) allocates (for admission by
