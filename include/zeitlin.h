@@ -154,7 +154,7 @@ ZT_API int zeitlin_casimirs(zt_plan* plan, const double* W, double* C, void* str
  * N x N complex128 in su(N) (skew-Hermitian: only the lower triangle and the
  * diagonal are read, |omega_{l,-m}| = |omega_lm|); E: DEVICE array of N
  * doubles, caller-owned.  Asynchronous on the stream; uses the plan's step
- * workspace (not concurrently with a step of the same plan).  About N^3/8 FP64
+ * workspace (not concurrently with a step of the same plan).  About N^3/6 FP64
  * recurrence steps, no eigenvector stored (GB300: ~0.26 s at N = 4096, growing
  * like N^3).  Errors: ZT_EINVAL (NULL plan, W not 16-byte or E not 8-byte
  * aligned), ZT_ECUDA (launch failure). */
