@@ -55,15 +55,19 @@ typedef struct zt_tuning {
     int exact_groups;    /* SPLIT: leading digit groups summed exactly (default 4)   */
     int final_mode;      /* ZT_FINAL_FRESH (default) or ZT_FINAL_REUSE               */
     int sweeps_per_sync; /* sweeps enqueued between host convergence checks (def. 4) */
-    int cluster_m;       /* SPLIT: CTAs sharing each B'^T tile by TMA multicast (1, 2, 4; def. 1) */
-    int cluster_n;       /* SPLIT: CTAs sharing each X' tile by TMA multicast (1, 2, 4; def. 1) */
     int dense;           /* SPLIT: 1 = multiply every digit pair; 0 (default) = skip digit-pair
                             tiles that are exactly zero (identical results)                  */
     int tile_order;      /* SPLIT launch order of output tiles: 0 (default) / 3 = column blocks of
-                            8 / 16 tile groups, rows walked inside a block; 1 = row-major;
+                            8 / 16 tiles, rows walked inside a block; 1 = row-major;
                             2 = tiles near the diagonal first */
     int no_persistent;   /* SPLIT: 0 (default) = persistent product kernel (one CTA per SM working
-                            through the tiles) when clusters are 1x1; 1 = one tile per CTA */
+                            through the tiles); 1 = one tile per CTA */
+    int wait_us;         /* SPLIT: limit of each bounded wait inside the product kernel, in
+                            microseconds (1 .. 60e6; default 2e6).  A wait that runs out makes
+                            the call return ZT_ETIMEOUT; W is then unspecified */
+    int debug_stall_loads; /* SPLIT, testing only: k > 0 stops the product kernel's operand
+                            loads after k - 1 of them, so that its bounded waits run out and
+                            the call returns ZT_ETIMEOUT (default 0: off) */
 } zt_tuning;
 
 typedef struct zt_step_stats {

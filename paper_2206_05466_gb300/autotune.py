@@ -1,4 +1,4 @@
-"""Autotuner for the split-precision product: digit count, digit width, cluster shape.
+"""Autotuner for the split-precision product: digit count, exact groups, launch order, kernel form.
 
 For a matrix size N it times each candidate tuning on seeded probe operands
 (the first product of an IsoMP sweep: X = Delta_N^{-1} W0, Y = W0, W0 from the
@@ -15,11 +15,10 @@ import json
 import os
 
 DEFAULT_CANDIDATES = [
-    dict(slices=s, digit_bits=7, exact_groups=eg, cluster_m=cm, cluster_n=1, tile_order=to, no_persistent=np_)
-    for s in (7, 6) for eg in (4, 3, 2) for cm in (1, 2) for to in (0, 1, 3) for np_ in (0, 1)
-    if cm == 1 or np_ == 0   # the persistent form exists for 1x1 clusters only
+    dict(slices=s, digit_bits=7, exact_groups=eg, tile_order=to, no_persistent=np_)
+    for s in (7, 6) for eg in (4, 3, 2) for to in (0, 1, 3) for np_ in (0, 1)
 ]
-REFERENCE = dict(slices=8, digit_bits=7, exact_groups=8, cluster_m=2, cluster_n=1)
+REFERENCE = dict(slices=8, digit_bits=7, exact_groups=8)
 
 
 def _cache_path():

@@ -31,7 +31,6 @@ struct Op {          // one grouped launch: table and CTA prefix sums in device 
     int* offs = nullptr;
     int n = 0;
     int total = 0;
-    int cluster = 1;
 };
 
 }  // namespace
@@ -115,12 +114,11 @@ struct Builder {
         return off;
     }
     template <class T>
-    void add(Op* op, const std::vector<T>& tab, const std::vector<int>& ctas, int cluster = 1) {
+    void add(Op* op, const std::vector<T>& tab, const std::vector<int>& ctas) {
         std::vector<int> offs(ctas.size() + 1, 0);
         for (size_t i = 0; i < ctas.size(); ++i) offs[i + 1] = offs[i] + ctas[i];
         op->n = (int)tab.size();
         op->total = offs.back();
-        op->cluster = cluster;
         const size_t t = put(tab.data(), tab.size() * sizeof(T), 128);
         const size_t o = put(offs.data(), offs.size() * sizeof(int), 16);
         pend.push_back({op, t, o});
@@ -160,13 +158,13 @@ int enqueue_products(zt_batch* b, cudaStream_t s, int gate) {
                                         b->split_W.total, s, gate)))
             return rc;
         if ((rc = zt_split_gemm_grouped((const GemmEntry*)b->gemm1.tab, b->gemm1.offs, b->gemm1.n, b->gemm1.total,
-                                        b->gemm1.cluster, s, gate)))
+                                        s, gate)))
             return rc;
         if ((rc = zt_split_rows_grouped((const SplitRowsArgs*)b->split_A.tab, b->split_A.offs, b->split_A.n,
                                         b->split_A.total, s, gate)))
             return rc;
         if ((rc = zt_split_gemm_grouped((const GemmEntry*)b->gemm2.tab, b->gemm2.offs, b->gemm2.n, b->gemm2.total,
-                                        b->gemm2.cluster, s, gate)))
+                                        s, gate)))
             return rc;
         b->launches += 8;
     }
@@ -300,7 +298,6 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
     int dev = 0;
     cudaGetDevice(&dev);
     b->device = dev;
-    int cluster = 0;
     for (int i = 0; i < count; ++i) {
         zt_plan* p = plans[i];
         if (!p || !W[i]) return fail(zt_fail(ZT_EINVAL, "zt_batch_create: instance %d has a NULL plan or W", i));
@@ -314,12 +311,6 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
         if (p->tun.final_mode != b->final_mode)
             return fail(zt_fail(ZT_EINVAL, "zt_batch_create: instances must share the final mode"));
         if (p->tun.sweeps_per_sync < b->sweeps_per_sync || i == 0) b->sweeps_per_sync = p->tun.sweeps_per_sync;
-        if (p->precision == ZT_PRECISION_SPLIT) {
-            const int cs = p->tun.cluster_m * p->tun.cluster_n;
-            if (cluster && cs != cluster)
-                return fail(zt_fail(ZT_EINVAL, "zt_batch_create: split instances must share the cluster shape"));
-            cluster = cs;
-        }
         b->plans.push_back(p);
         b->W.push_back(reinterpret_cast<double2*>(W[i]));
         b->h.push_back(h[i]);
@@ -354,11 +345,11 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
             sA.push_back(ra);
             c_sP.push_back(N);
             GemmEntry e;
-            int ctas, cl;
-            if ((rc = zt_split_gemm_entry(p, 0, p->A, -1.0, 0, &e, &ctas, &cl))) return fail(rc);
+            int ctas;
+            if ((rc = zt_split_gemm_entry(p, 0, p->A, -1.0, 0, &e, &ctas))) return fail(rc);
             g1.push_back(e);
             c_g1.push_back(ctas);
-            if ((rc = zt_split_gemm_entry(p, 1, p->B, -1.0, 1, &e, &ctas, &cl))) return fail(rc);
+            if ((rc = zt_split_gemm_entry(p, 1, p->B, -1.0, 1, &e, &ctas))) return fail(rc);
             g2.push_back(e);
             c_g2.push_back(ctas);
         } else {
@@ -402,8 +393,8 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
         bl.add(&b->split_P, sP, c_sP);
         bl.add(&b->split_W, sW, c_sP);
         bl.add(&b->split_A, sA, c_sP);
-        bl.add(&b->gemm1, g1, c_g1, cluster);
-        bl.add(&b->gemm2, g2, c_g2, cluster);
+        bl.add(&b->gemm1, g1, c_g1);
+        bl.add(&b->gemm2, g2, c_g2);
     }
     if (!fa.empty()) {
         bl.add(&b->f64a, fa, c_fa);

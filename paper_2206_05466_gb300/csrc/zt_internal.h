@@ -182,10 +182,11 @@ struct SplitArgs {     // tcgen05 split product (zt_split.cu)
     const int* occA;
     const int* occB;
     unsigned long long* units;   // if not NULL: += MMA units (128 x 256 x 64) issued by each CTA
-    int cm, cn;        // cluster shape: cm row tiles share B'^T slices, cn column tiles share X' slices
-    int ntmg, ntng;    // tile groups (one cluster each) along rows and columns
-    const int* order;  // launch order of tile groups (linear index tig * ntng + tjg)
-    int ngroups;       // tile groups of the launch
+    int ntng;          // output tiles along the columns of C'
+    const int* order;  // launch order of tiles (linear index tig * ntng + tjg)
+    int ngroups;       // tiles of the launch
+    unsigned long long wait_ns;  // limit of one bounded mbarrier wait
+    int stall_loads;   // testing only: > 0 stops the TMA producer after stall_loads - 1 loads
     unsigned int* tickets;   // persistent form: tile ticket counter, zero at launch
     double alpha;
     const int* eA;
@@ -295,9 +296,8 @@ int zt_solve_grouped(const SolveArgs* tab, const int* offs, int n, int total, in
 int zt_split_rows_args(zt_plan* p, const double2* X, int to_a, int b_slot, SplitRowsArgs* out);
 int zt_split_rows_grouped(const SplitRowsArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
 int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, GemmEntry* out,
-                        int* ctas, int* cluster);
-int zt_split_gemm_grouped(const GemmEntry* tab, const int* offs, int n, int total, int cluster, cudaStream_t s,
-                          int gate);
+                        int* ctas);
+int zt_split_gemm_grouped(const GemmEntry* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
 int zt_fp64_gemm_args(zt_plan* p, const double2* X, const double2* Y, double2* C, double alpha, int lower_only,
                       Fp64GemmArgs* out, int* ctas);
 int zt_fp64_gemm_grouped(const Fp64GemmArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);

@@ -554,8 +554,7 @@ static void fill_tuning_defaults(zt_tuning& t) {
     if (t.digit_bits == 0) t.digit_bits = 7;
     if (t.exact_groups == 0) t.exact_groups = 4;
     if (t.sweeps_per_sync == 0) t.sweeps_per_sync = 4;
-    if (t.cluster_m == 0) t.cluster_m = 1;
-    if (t.cluster_n == 0) t.cluster_n = 1;
+    if (t.wait_us == 0) t.wait_us = 2000000;
 }
 
 extern "C" long long zt_plan_estimate_bytes(int N, int precision, const zt_tuning* opt) {
@@ -594,15 +593,14 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     if (precision == ZT_PRECISION_SPLIT) {   // checked before any device work
         const zt_tuning& t = p->tun;
         const char* bad = nullptr;
-        auto side = [](int v) { return v == 1 || v == 2 || v == 4; };
         if (t.slices < 3 || t.slices > 8) bad = "slices outside [3, 8]";
         else if (t.digit_bits < 6 || t.digit_bits > 8) bad = "digit_bits outside [6, 8]";
         else if (t.exact_groups < 1 || t.exact_groups > t.slices) bad = "exact_groups outside [1, slices]";
         else if (t.slices * t.digit_bits > 62) bad = "slices*digit_bits above 62";
-        else if (!side(t.cluster_m) || !side(t.cluster_n) || t.cluster_m * t.cluster_n > 8)
-            bad = "cluster sides must be 1, 2 or 4, at most 8 CTAs";
         else if (t.tile_order < 0 || t.tile_order > 3) bad = "tile_order outside [0, 3]";
         else if (t.no_persistent != 0 && t.no_persistent != 1) bad = "no_persistent must be 0 or 1";
+        else if (t.wait_us < 1 || t.wait_us > 60000000) bad = "wait_us outside [1, 60000000]";
+        else if (t.debug_stall_loads < 0) bad = "debug_stall_loads must be >= 0";
         if (bad) {
             delete p;
             return zt_fail(ZT_EINVAL, "zt_plan_create: %s", bad);

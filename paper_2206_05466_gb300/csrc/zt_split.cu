@@ -35,11 +35,14 @@
 //           each); the last drain of a tile adds, scales and stores FP64;
 //   warp 10 (persistent form) takes tiles from a ticket counter and fills
 //           the tile slots the other roles work through.
-// The persistent form (1x1 clusters) keeps one CTA per SM for the whole
-// launch, so one tile's last drain overlaps the next tile's MMAs; the
-// one-tile-per-CTA form serves thread-block clusters and grouped launches.
-// Every mbarrier wait is bounded by a wall-clock limit; on expiry the kernel
-// records a timeout in the step state, lets in-flight work retire and exits.
+// The persistent form keeps one CTA per SM for the whole launch, so one
+// tile's last drain overlaps the next tile's MMAs; the one-tile-per-CTA form
+// serves grouped launches.  Operand tiles are fetched with plain (unicast)
+// TMA loads into each CTA's own shared memory.
+// Every mbarrier wait is bounded by a wall-clock limit (a kernel argument);
+// on expiry the CTA records a timeout in the step state, stops issuing work,
+// waits (bounded) for the copies and MMAs it has already issued, frees its
+// TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -68,7 +71,7 @@ constexpr int CTAS_PER_SM = 1;     // resident CTAs per SM the launch bounds ask
 constexpr uint32_t TMEM_COLS = NBUF * BN;   // 128 x 256 FP32 accumulators
 constexpr int MAX_KB = 512;        // K blocks of 64 for N <= 16384
 constexpr int EXP_NAN = 0x7fff;    // row exponent marking a non-finite entry
-constexpr unsigned long long WAIT_NS = 2000000000ull;   // 2 s per wait
+constexpr unsigned long long SETTLE_NS = 2000000000ull;   // teardown waits for issued work: 2 s
 
 // instruction descriptor, kind::f16: D F32, A/B BF16, K-major, M=128, N=256
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
@@ -77,7 +80,8 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
 
 struct zt_split_ws {
     int s = 7, beta = 7, exact_groups = 4;
-    int cm = 1, cn = 1;            // cluster shape of the product kernel
+    unsigned long long wait_ns = 2000000000ull;   // limit of one mbarrier wait
+    int stall_loads = 0;                          // testing only (zt_tuning.debug_stall_loads)
     int ldk = 0, Mpad = 0, Npad = 0, u = 0;
     __nv_bfloat16* dA = nullptr;   // [s][Mpad][ldk]
     __nv_bfloat16* dB[2] = {nullptr, nullptr};   // two B'^T slots, each [s][Npad][ldk]
@@ -88,7 +92,7 @@ struct zt_split_ws {
     int* order_lower = nullptr;
     int n_full = 0, n_lower = 0;
     int skip_zero = 1;                           // skip digit-pair units whose tiles are all zero
-    int persistent = 1;                          // persistent product kernel (1x1 clusters only)
+    int persistent = 1;                          // persistent product kernel
     int nsm = 0;                                 // SMs of the device
     unsigned int* tickets = nullptr;             // tile ticket counter of the persistent kernel
     int* occA = nullptr;                         // [ngA][nkb]
@@ -126,17 +130,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity; false on timeout/abort.
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait for the phase with the given parity: false once another role
+// has aborted the CTA or after limit_ns of wall-clock time (which aborts it).
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = gtimer();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (gtimer() - t0 > WAIT_NS) {
+        if (gtimer() - t0 > limit_ns) {
             *abort_flag = 1;
             return false;
         }
+    }
+}
+// Teardown wait for work this CTA has already issued (copies, MMAs): it
+// completes on its own, so the wait ignores the abort flag; bounded all the same.
+__device__ bool mbar_settle(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (gtimer() - t0 > SETTLE_NS) return false;
     }
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -146,28 +161,8 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
         : "memory");
 }
-// Multicast variant: the box lands at the same shared-memory offset in every
-// CTA of the cluster named in `mask`, and completes on each one's mbarrier.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                               uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_ctarank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// barrier 1 among the drain warps only
-__device__ __forceinline__ void drain_bar() { asm volatile("bar.sync 1, %0;" ::"n"(NDRAIN) : "memory"); }
 
 // K-major operand tile with 128-byte swizzle: rows of 128 B, 8-row atoms of 1 KiB.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -189,15 +184,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
-}
-// Arrive on the mbarrier at this offset in every CTA of `mask` once the
-// tcgen05 operations issued so far by this thread have completed.
-__device__ __forceinline__ void umma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
 }
 // Asynchronous bulk reduce-add of `bytes` (a multiple of 16) of int64 from
 // shared to global memory; the L2 performs the additions.
@@ -492,26 +478,19 @@ __device__ __forceinline__ SmemMap smem_map() {
     return m;
 }
 
-// Tile group of a linear launch index; false when the group has no element in
-// the requested (lower) triangle.
+// Tile of a linear launch index; false when it has no element in the
+// requested (lower) triangle.
 __device__ __forceinline__ bool tile_group(const SplitArgs& a, int grp, int& tig, int& tjg) {
-    if (a.order) {   // explicit order (only groups that have work are listed)
+    if (a.order) {   // explicit order (only tiles that have work are listed)
         const int gl = a.order[grp];
         tig = gl / a.ntng;
         tjg = gl % a.ntng;
         return true;
     }
-    if (a.lower_only && a.cm == a.cn) {   // groups on or below the diagonal, triangular order
-        int r = (int)((sqrtf(8.0f * grp + 1.0f) - 1.0f) * 0.5f);
-        while (r * (r + 1) / 2 > grp) --r;
-        while ((r + 1) * (r + 2) / 2 <= grp) ++r;
-        tig = r;
-        tjg = grp - r * (r + 1) / 2;
-        return true;
-    }
     tig = grp / a.ntng;
     tjg = grp % a.ntng;
-    return !(a.lower_only && tjg * a.cn >= (tig + 1) * a.cm);
+    // a 128 x 256 tile of C' covers complex columns [128 tjg, 128 tjg + 128)
+    return !(a.lower_only && tjg * (BN / 2) >= (tig + 1) * BM);
 }
 
 // One warp fills a tile slot: occupancy, active units per group, segments.
@@ -549,26 +528,21 @@ __device__ __forceinline__ void fill_slot_warp(const SplitArgs& a, TileSlot& ts,
 }
 
 // ---- TMA producer (one thread): digit tiles of every active unit of the tile ----
+// nload counts the loads issued over the launch (for the teardown).  Returns
+// false when the CTA aborted or the testing stall stopped the producer.
 __device__ __forceinline__ bool produce_tile(const SplitArgs& a, const TileSlot& ts, const SmemMap& m,
                                              const CUtensorMap* tmA_p, const CUtensorMap* tmB_p, int i0, int c0,
-                                             int a_off, int b_off, uint16_t mask_a, uint16_t mask_b, int nkb,
-                                             int& stage, uint32_t& ph) {
+                                             int nkb, int& stage, uint32_t& ph, long long& nload) {
     for (int g = 0; g < a.s; ++g)
         for (int kb = 0; kb < nkb; ++kb)
             for (int p = ts.fa[kb]; p <= g - ts.fb[kb]; ++p) {
-                if (!mbar_wait(&m.empty[stage], ph ^ 1, m.abort_flag)) return false;
+                // testing only: stop issuing so that the consumers' bounded waits run out
+                if (a.stall_loads > 0 && nload >= a.stall_loads - 1) return false;
+                if (!mbar_wait(&m.empty[stage], ph ^ 1, m.abort_flag, a.wait_ns)) return false;
                 mbar_expect_tx(&m.full[stage], STAGE_BYTES);
-                uint8_t* dA = m.sA + stage * A_TILE + a_off * 128;
-                uint8_t* dB = m.sB + stage * B_TILE + b_off * 128;
-                const int ya = p * a.Mpad + i0 + a_off, yb = (g - p) * a.Npad + c0 + b_off;
-                if (a.cn > 1)
-                    tma_load_2d_mc(dA, tmA_p, &m.full[stage], kb * BK, ya, mask_a);
-                else
-                    tma_load_2d(dA, tmA_p, &m.full[stage], kb * BK, ya);
-                if (a.cm > 1)
-                    tma_load_2d_mc(dB, tmB_p, &m.full[stage], kb * BK, yb, mask_b);
-                else
-                    tma_load_2d(dB, tmB_p, &m.full[stage], kb * BK, yb);
+                tma_load_2d(m.sA + stage * A_TILE, tmA_p, &m.full[stage], kb * BK, p * a.Mpad + i0);
+                tma_load_2d(m.sB + stage * B_TILE, tmB_p, &m.full[stage], kb * BK, (g - p) * a.Npad + c0);
+                ++nload;
                 if (++stage == STAGES) {
                     stage = 0;
                     ph ^= 1;
@@ -577,11 +551,19 @@ __device__ __forceinline__ bool produce_tile(const SplitArgs& a, const TileSlot&
     return true;
 }
 
+// Before the CTA leaves: the last STAGES loads issued may still be landing
+// (after an abort nobody consumed them).  Load j went to stage j % STAGES as
+// phase j / STAGES; earlier loads have completed, because the load j + STAGES
+// into the same stage was issued only after the MMA consumed load j.
+__device__ __forceinline__ void producer_settle(const SmemMap& m, long long nload) {
+    for (long long j = nload > STAGES ? nload - STAGES : 0; j < nload; ++j)
+        mbar_settle(&m.full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+}
+
 // ---- MMA issuer (one thread): one accumulation segment per exactness budget ----
 // stage/ph/seg continue from tile to tile; seg numbers the accumulator buffers.
 __device__ __forceinline__ bool mma_tile(const SplitArgs& a, const TileSlot& ts, const SmemMap& m, uint32_t tmem,
-                                         int nkb, int cs, uint16_t mask_all, int& stage, uint32_t& ph, int& seg,
-                                         unsigned long long& issued) {
+                                         int nkb, int& stage, uint32_t& ph, int& seg, unsigned long long& issued) {
     for (int g = 0; g < a.s; ++g) {
         const int ulim = seg_units(g, a.beta, a.exact_groups);
         int cnt = 0, b = 0;
@@ -593,13 +575,13 @@ __device__ __forceinline__ bool mma_tile(const SplitArgs& a, const TileSlot& ts,
                     b = seg % NBUF;
                     const int use = seg / NBUF;
                     ++seg;
-                    if (!mbar_wait(&m.acce[b], (use & 1) ^ 1, m.abort_flag)) return false;
+                    if (!mbar_wait(&m.acce[b], (use & 1) ^ 1, m.abort_flag, a.wait_ns)) return false;
                     tc_fence_after();
                     d = tmem + (uint32_t)(b * BN);
                     open = true;
                     cnt = 0;
                 }
-                if (!mbar_wait(&m.full[stage], ph, m.abort_flag)) return false;
+                if (!mbar_wait(&m.full[stage], ph, m.abort_flag, a.wait_ns)) return false;
                 tc_fence_after();
                 const uint64_t ad = sw128_desc(smem_u32(m.sA + stage * A_TILE));
                 const uint64_t bd = sw128_desc(smem_u32(m.sB + stage * B_TILE));
@@ -608,10 +590,7 @@ __device__ __forceinline__ bool mma_tile(const SplitArgs& a, const TileSlot& ts,
                     umma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), (cnt == 0 && k == 0) ? 0u : 1u);
                 ++cnt;
                 ++issued;
-                if (cs > 1)
-                    umma_commit_mc(&m.empty[stage], mask_all);
-                else
-                    umma_commit(&m.empty[stage]);
+                umma_commit(&m.empty[stage]);
                 if (++stage == STAGES) {
                     stage = 0;
                     ph ^= 1;
@@ -625,6 +604,14 @@ __device__ __forceinline__ bool mma_tile(const SplitArgs& a, const TileSlot& ts,
         if (open) umma_commit(&m.accf[b]);
     }
     return true;
+}
+
+// After the MMA thread's last issue (or an abort): every MMA it issued retires
+// before TMEM is released or the CTA leaves.
+__device__ __forceinline__ void mma_settle(const SmemMap& m, const SplitArgs& a, unsigned long long issued) {
+    if (a.units) atomicAdd(a.units, issued);
+    umma_commit(m.drain);
+    if (!mbar_settle(m.drain, 0)) *m.abort_flag = 1;
 }
 
 // ---- drain / epilogue (the 8 drain warps): every segment of the tile into the
@@ -663,7 +650,7 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
         for (int q = 0; q < nsegs; ++q) {
             const int b = seg % NBUF, use = seg / NBUF;
             ++seg;
-            if (!mbar_wait(&m.accf[b], use & 1, m.abort_flag)) {
+            if (!mbar_wait(&m.accf[b], use & 1, m.abort_flag, a.wait_ns)) {
                 if (nstg) bulk_wait_all();
                 return false;
             }
@@ -787,22 +774,16 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
     return true;
 }
 
-// Teardown shared by both kernels: on a timeout the CTA records it, gives
-// copies in flight time to land, frees TMEM and leaves.
-__device__ __forceinline__ void split_teardown(const SplitArgs& a, const SmemMap& m, uint32_t tmem, int warp, int cs) {
+// Teardown shared by both kernels.  By now the producer has settled its
+// loads, the MMA thread its MMAs and every drain thread its bulk copies, so
+// nothing is in flight: record an abort as a timeout, free TMEM and leave.
+__device__ __forceinline__ void split_teardown(const SplitArgs& a, const SmemMap& m, uint32_t tmem, int warp) {
     __syncthreads();
-    if (*m.abort_flag) {
-        if (threadIdx.x == 0) atomicExch(&a.st->timeout, 1);
-        const unsigned long long t0 = gtimer();
-        while (gtimer() - t0 < 200000ull) {
-        }
-    }
+    if (*m.abort_flag && threadIdx.x == 0) atomicExch(&a.st->timeout, 1);
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
-    // no CTA leaves while a peer may still write into its shared memory or barriers
-    if (cs > 1) cluster_sync();
 }
 
 __device__ __forceinline__ void tmem_alloc_warp(const SmemMap& m) {
@@ -812,55 +793,44 @@ __device__ __forceinline__ void tmem_alloc_warp(const SmemMap& m) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void init_barriers(const SmemMap& m) {
+    for (int i = 0; i < STAGES; ++i) {
+        mbar_init(&m.full[i], 1);
+        mbar_init(&m.empty[i], 1);
+    }
+    for (int i = 0; i < NBUF; ++i) {
+        mbar_init(&m.accf[i], 1);
+        mbar_init(&m.acce[i], NDRAIN);
+    }
+    for (int i = 0; i < TSLOTS; ++i) {
+        mbar_init(&m.tfull[i], 1);
+        mbar_init(&m.tempty[i], NDRAIN);   // released by every drain thread after the tile's last drain
+    }
+    mbar_init(m.drain, 1);
+    *m.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
-// One output tile (cluster group) per CTA; clusters share operand slices by
-// TMA multicast.
+// One output tile per CTA (grouped launches, the allocation-free entry point,
+// and no_persistent = 1).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const CUtensorMap* tmB_p,
                                                  const SplitArgs& a, int bid, bool global_maps) {
     if (zt_gate_skip(a.st, a.gate)) return;
     const SmemMap m = smem_map();
     TileSlot& ts = m.slots[0];
-
-    // A cluster of cm x cn CTAs owns a group of cm row tiles and cn column
-    // tiles; CTA rank r sits at (r % cm, r / cm).
-    const int cs = a.cm * a.cn;
-    const int rank = cs > 1 ? (int)cluster_ctarank() : 0;
     int tig, tjg;
-    if (!tile_group(a, bid / cs, tig, tjg)) return;   // whole cluster leaves
-    const int rm = rank % a.cm, rn = rank / a.cm;
-    const int ti = tig * a.cm + rm, tj = tjg * a.cn + rn;
-    const int i0 = ti * BM, c0 = tj * BN;
-    // each CTA fetches one slice of its X' tile (shared along the cluster row)
-    // and one slice of its B'^T tile (shared along the cluster column)
-    const int a_off = rn * (BM / a.cn), b_off = rm * (BN / a.cm);
-    uint16_t mask_a = 0, mask_b = 0;
-    for (int n2 = 0; n2 < a.cn; ++n2) mask_a |= (uint16_t)(1u << (rm + a.cm * n2));
-    for (int m2 = 0; m2 < a.cm; ++m2) mask_b |= (uint16_t)(1u << (m2 + a.cm * rn));
-    const uint16_t mask_all = (uint16_t)((1u << cs) - 1u);
+    if (!tile_group(a, bid, tig, tjg)) return;
+    const int i0 = tig * BM, c0 = tjg * BN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = a.ldk / BK;
 
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; ++i) {
-            mbar_init(&m.full[i], 1);
-            mbar_init(&m.empty[i], cs);   // released by the MMA of every CTA that reads this stage's slices
-        }
-        for (int i = 0; i < NBUF; ++i) {
-            mbar_init(&m.accf[i], 1);
-            mbar_init(&m.acce[i], NDRAIN);
-        }
-        mbar_init(m.drain, 1);
-        *m.abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (threadIdx.x == 0) init_barriers(m);
     if (warp == 1) tmem_alloc_warp(m);
     if (warp == 2) fill_slot_warp(a, ts, tig, tjg, nkb, lane);
     tc_fence_before();
-    if (cs > 1)
-        cluster_sync();   // peers' barriers exist before any multicast lands
-    else
-        __syncthreads();
+    __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *m.tmem_slot;
 
@@ -872,33 +842,31 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
             }
             int stage = 0;
             uint32_t ph = 0;
-            produce_tile(a, ts, m, tmA_p, tmB_p, i0, c0, a_off, b_off, mask_a, mask_b, nkb, stage, ph);
+            long long nload = 0;
+            produce_tile(a, ts, m, tmA_p, tmB_p, i0, c0, nkb, stage, ph, nload);
+            producer_settle(m, nload);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             int stage = 0, seg = 0;
             uint32_t ph = 0;
             unsigned long long issued = 0;
-            mma_tile(a, ts, m, tmem, nkb, cs, mask_all, stage, ph, seg, issued);
-            if (a.units) atomicAdd(a.units, issued);
-            // all MMAs issued by this thread retire before TMEM is released
-            umma_commit(m.drain);
-            volatile int dummy = 0;
-            if (!mbar_wait(m.drain, 0, &dummy)) *m.abort_flag = 1;
+            mma_tile(a, ts, m, tmem, nkb, stage, ph, seg, issued);
+            mma_settle(m, a, issued);
         }
     } else if (warp < 2 + NDRAIN / 32) {
         int seg = 0;
         drain_tile(a, ts, m, tmem, i0, c0, warp, lane, seg);
     }
-    split_teardown(a, m, tmem, warp, cs);
+    split_teardown(a, m, tmem, warp);
 }
 
 // ---------------------------------------------------------------------------
-// Persistent form (1x1 clusters): one CTA per SM works through the launch
-// order, taking tile groups from a ticket counter (zeroed by the host before
-// every launch).  A scheduler warp fills a ring of tile slots ahead of the
-// roles, and the accumulator buffers rotate across tiles, so the last drain
-// and the FP64 epilogue of one tile overlap the first MMAs of the next.
+// Persistent form: one CTA per SM works through the launch order, taking
+// tiles from a ticket counter (zeroed by the host before every launch).  A
+// scheduler warp fills a ring of tile slots ahead of the roles, and the
+// accumulator buffers rotate across tiles, so the last drain and the FP64
+// epilogue of one tile overlap the first MMAs of the next.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void zgemm_split_persistent_body(const CUtensorMap* tmA_p, const CUtensorMap* tmB_p,
                                                             const SplitArgs& a) {
@@ -907,23 +875,7 @@ __device__ __forceinline__ void zgemm_split_persistent_body(const CUtensorMap* t
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = a.ldk / BK;
 
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; ++i) {
-            mbar_init(&m.full[i], 1);
-            mbar_init(&m.empty[i], 1);
-        }
-        for (int i = 0; i < NBUF; ++i) {
-            mbar_init(&m.accf[i], 1);
-            mbar_init(&m.acce[i], NDRAIN);
-        }
-        for (int i = 0; i < TSLOTS; ++i) {
-            mbar_init(&m.tfull[i], 1);
-            mbar_init(&m.tempty[i], NDRAIN);   // released by every drain thread after the tile's last drain
-        }
-        mbar_init(m.drain, 1);
-        *m.abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    if (threadIdx.x == 0) init_barriers(m);
     if (warp == 1) tmem_alloc_warp(m);
     tc_fence_before();
     __syncthreads();
@@ -934,12 +886,13 @@ __device__ __forceinline__ void zgemm_split_persistent_body(const CUtensorMap* t
         if (lane == 0) {
             int stage = 0;
             uint32_t ph = 0;
+            long long nload = 0;
             for (int k = 0;; ++k) {
                 const TileSlot& ts = m.slots[k % TSLOTS];
-                if (!mbar_wait(&m.tfull[k % TSLOTS], (k / TSLOTS) & 1, m.abort_flag) || !ts.valid) break;
-                if (!produce_tile(a, ts, m, tmA_p, tmB_p, ts.tig * BM, ts.tjg * BN, 0, 0, 0, 0, nkb, stage, ph))
-                    break;
+                if (!mbar_wait(&m.tfull[k % TSLOTS], (k / TSLOTS) & 1, m.abort_flag, a.wait_ns) || !ts.valid) break;
+                if (!produce_tile(a, ts, m, tmA_p, tmB_p, ts.tig * BM, ts.tjg * BN, nkb, stage, ph, nload)) break;
             }
+            producer_settle(m, nload);
         }
     } else if (warp == 1) {   // ---- MMA issuer ----
         if (lane == 0) {
@@ -948,26 +901,23 @@ __device__ __forceinline__ void zgemm_split_persistent_body(const CUtensorMap* t
             unsigned long long issued = 0;
             for (int k = 0;; ++k) {
                 const TileSlot& ts = m.slots[k % TSLOTS];
-                if (!mbar_wait(&m.tfull[k % TSLOTS], (k / TSLOTS) & 1, m.abort_flag) || !ts.valid) break;
-                if (!mma_tile(a, ts, m, tmem, nkb, 1, 1, stage, ph, seg, issued)) break;
+                if (!mbar_wait(&m.tfull[k % TSLOTS], (k / TSLOTS) & 1, m.abort_flag, a.wait_ns) || !ts.valid) break;
+                if (!mma_tile(a, ts, m, tmem, nkb, stage, ph, seg, issued)) break;
             }
-            if (a.units) atomicAdd(a.units, issued);
-            umma_commit(m.drain);
-            volatile int dummy = 0;
-            if (!mbar_wait(m.drain, 0, &dummy)) *m.abort_flag = 1;
+            mma_settle(m, a, issued);
         }
     } else if (warp < 2 + NDRAIN / 32) {   // ---- drain / epilogue ----
         int seg = 0;
         for (int k = 0;; ++k) {
             const TileSlot& ts = m.slots[k % TSLOTS];
-            if (!mbar_wait(&m.tfull[k % TSLOTS], (k / TSLOTS) & 1, m.abort_flag) || !ts.valid) break;
+            if (!mbar_wait(&m.tfull[k % TSLOTS], (k / TSLOTS) & 1, m.abort_flag, a.wait_ns) || !ts.valid) break;
             if (!drain_tile(a, ts, m, tmem, ts.tig * BM, ts.tjg * BN, warp, lane, seg)) break;
             mbar_arrive(&m.tempty[k % TSLOTS]);   // this thread is done with the slot
         }
     } else {   // ---- scheduler: tile slots filled ahead of the roles ----
         for (int k = 0;; ++k) {
             TileSlot& ts = m.slots[k % TSLOTS];
-            if (!mbar_wait(&m.tempty[k % TSLOTS], ((k / TSLOTS) & 1) ^ 1, m.abort_flag)) break;
+            if (!mbar_wait(&m.tempty[k % TSLOTS], ((k / TSLOTS) & 1) ^ 1, m.abort_flag, a.wait_ns)) break;
             unsigned int ticket = 0;
             if (lane == 0) ticket = atomicAdd(a.tickets, 1u);
             ticket = __shfl_sync(0xffffffffu, ticket, 0);
@@ -984,7 +934,7 @@ __device__ __forceinline__ void zgemm_split_persistent_body(const CUtensorMap* t
             if (lane == 0) mbar_arrive(&m.tfull[k % TSLOTS]);
         }
     }
-    split_teardown(a, m, tmem, warp, 1);
+    split_teardown(a, m, tmem, warp);
 }
 
 __global__ void __launch_bounds__(NTHREADS, CTAS_PER_SM)
@@ -999,8 +949,7 @@ zgemm_split_persistent(const __grid_constant__ CUtensorMap tmA, const __grid_con
     zgemm_split_persistent_body(&tmA, &tmB, a);
 }
 
-// Grouped: instances (each with its own tensor maps in global memory) share one
-// cluster launch; every instance's CTA count is a multiple of the cluster size.
+// Grouped: instances (each with its own tensor maps in global memory) share one launch.
 __global__ void __launch_bounds__(NTHREADS, CTAS_PER_SM)
 zgemm_split_grouped(const GemmEntry* tab, const int* offs, int n, int gate) {
     const int inst = zt_group_find(offs, n, blockIdx.x);
@@ -1049,22 +998,18 @@ int zt_split_create(zt_plan* p) {
     if (beta < 6 || beta > 8) return zt_fail(ZT_EINVAL, "digit_bits=%d outside [6, 8]", beta);
     if (eg < 1 || eg > s) return zt_fail(ZT_EINVAL, "exact_groups=%d outside [1, slices]", eg);
     if (s * beta > 62) return zt_fail(ZT_EINVAL, "slices*digit_bits must be <= 62");
-    const int cm = p->tun.cluster_m, cn = p->tun.cluster_n;
-    auto pow2 = [](int v) { return v == 1 || v == 2 || v == 4; };
-    if (!pow2(cm) || !pow2(cn) || cm * cn > 8)
-        return zt_fail(ZT_EINVAL, "cluster %dx%d: each side 1, 2 or 4 and at most 8 CTAs", cm, cn);
     zt_split_ws* w = new (std::nothrow) zt_split_ws();
     if (!w) return zt_fail(ZT_ENOMEM, "host allocation failed");
     p->split = w;
     w->s = s;
     w->beta = beta;
     w->exact_groups = eg;
-    w->cm = cm;
-    w->cn = cn;
+    w->wait_ns = (unsigned long long)p->tun.wait_us * 1000ull;
+    w->stall_loads = p->tun.debug_stall_loads;
     w->skip_zero = p->tun.dense ? 0 : 1;
     w->ldk = round_up(2 * N, BK);
-    w->Mpad = round_up(N, BM * cm);
-    w->Npad = round_up(2 * N, BN * cn);
+    w->Mpad = round_up(N, BM);
+    w->Npad = round_up(2 * N, BN);
     // smallest u >= 0 with the worst-case int64 accumulator below 2^62
     {
         const double R = std::ldexp(1.0, beta);
@@ -1083,11 +1028,11 @@ int zt_split_create(zt_plan* p) {
     ZT_CU(ZT_DMALLOC(w->eA, (size_t)w->Mpad * sizeof(int), cs));
     ZT_CU(cudaMemsetAsync(w->eA, 0, (size_t)w->Mpad * sizeof(int), cs));
     int rc;
-    if ((rc = make_map(&w->tmA, w->dA, s * w->Mpad, w->ldk, BM / cn))) return rc;
+    if ((rc = make_map(&w->tmA, w->dA, s * w->Mpad, w->ldk, BM))) return rc;
     w->nkb = w->ldk / BK;
     if (w->nkb > MAX_KB) return zt_fail(ZT_EINVAL, "N too large for the split product (K blocks > %d)", MAX_KB);
-    w->ngA = w->Mpad / (BM * cm);
-    w->ngB = w->Npad / (BN * cn);
+    w->ngA = w->Mpad / BM;
+    w->ngB = w->Npad / BN;
     ZT_CU(ZT_DMALLOC(w->occA, (size_t)w->ngA * w->nkb * sizeof(int), cs));
     ZT_CU(cudaMemsetAsync(w->occA, 0, (size_t)w->ngA * w->nkb * sizeof(int), cs));
     for (int b = 0; b < 2; ++b) {
@@ -1097,7 +1042,7 @@ int zt_split_create(zt_plan* p) {
         ZT_CU(cudaMemsetAsync(w->dB[b], 0, szB, cs));
         ZT_CU(ZT_DMALLOC(w->eB[b], (size_t)w->Npad * sizeof(int), cs));
         ZT_CU(cudaMemsetAsync(w->eB[b], 0, (size_t)w->Npad * sizeof(int), cs));
-        if ((rc = make_map(&w->tmB[b], w->dB[b], s * w->Npad, w->ldk, BN / cm))) return rc;
+        if ((rc = make_map(&w->tmB[b], w->dB[b], s * w->Npad, w->ldk, BN))) return rc;
     }
     // Launch orders.  0, 3: column blocks of 8 or 16 tile groups, rows walked
     // inside a block, so that the tiles resident at one time share a few
@@ -1108,17 +1053,16 @@ int zt_split_create(zt_plan* p) {
     // most of the work, so they are dispatched first and the light far tiles
     // fill the tail (longest-first ordering).
     {
-        const int ntmg = w->Mpad / (BM * cm), ntng = w->Npad / (BN * cn);
+        const int ntmg = w->Mpad / BM, ntng = w->Npad / BN;
         const int order = p->tun.tile_order;
         const int cblk = order == 0 ? 8 : order == 3 ? 16 : ntng;
         std::vector<std::pair<double, int>> full, lower;
         for (int cb0 = 0; cb0 < ntng; cb0 += cblk)
             for (int tg = 0; tg < ntmg; ++tg)
                 for (int ug = cb0; ug < cb0 + cblk && ug < ntng; ++ug) {
-                    const double rc = tg * cm + 0.5 * (cm - 1), cc = ug * cn + 0.5 * (cn - 1);
-                    const double dist = std::fabs(rc - cc);
+                    const double dist = std::fabs((double)tg - (double)ug);
                     full.push_back({dist, tg * ntng + ug});
-                    if (ug * cn < (tg + 1) * cm) lower.push_back({dist, tg * ntng + ug});
+                    if (ug < tg + 1) lower.push_back({dist, tg * ntng + ug});
                 }
         if (order == 2) {   // otherwise the enumeration order above
             std::stable_sort(full.begin(), full.end(), [](auto& x, auto& y) { return x.first < y.first; });
@@ -1135,7 +1079,7 @@ int zt_split_create(zt_plan* p) {
         ZT_CU(cudaMemcpyAsync(w->order_lower, ol.data(), ol.size() * sizeof(int), cudaMemcpyHostToDevice, cs));
         ZT_CU(cudaStreamSynchronize(cs));   // host vectors go out of scope
     }
-    w->persistent = (cm == 1 && cn == 1 && !p->tun.no_persistent) ? 1 : 0;
+    w->persistent = p->tun.no_persistent ? 0 : 1;
     ZT_CU(cudaDeviceGetAttribute(&w->nsm, cudaDevAttrMultiProcessorCount, p->device));
     ZT_CU(ZT_DMALLOC(w->tickets, 16, cs));
     ZT_CU(cudaMemsetAsync(w->tickets, 0, 16, cs));
@@ -1150,10 +1094,10 @@ int zt_split_create(zt_plan* p) {
 }
 
 size_t zt_split_bytes(int N, const zt_tuning& t) {
-    const int s = t.slices, cm = t.cluster_m, cn = t.cluster_n;
-    const size_t ldk = (size_t)round_up(2 * N, BK), Mpad = (size_t)round_up(N, BM * cm),
-                 Npad = (size_t)round_up(2 * N, BN * cn);
-    const size_t nkb = ldk / BK, ngA = Mpad / (BM * cm), ngB = Npad / (BN * cn);
+    const int s = t.slices;
+    const size_t ldk = (size_t)round_up(2 * N, BK), Mpad = (size_t)round_up(N, BM),
+                 Npad = (size_t)round_up(2 * N, BN);
+    const size_t nkb = ldk / BK, ngA = Mpad / BM, ngB = Npad / BN;
     return (size_t)s * Mpad * ldk * 2 + 2 * (size_t)s * Npad * ldk * 2 + Mpad * 4 + 2 * Npad * 4 +
            ngA * nkb * 4 + 2 * ngB * nkb * 4 + 16;
 }
@@ -1193,10 +1137,10 @@ int zt_split_rows_args(zt_plan* p, const double2* X, int to_a, int b_slot, Split
     a.Npad = w->Npad;
     a.eB = b_slot >= 0 ? w->eB[b_slot] : nullptr;
     a.occA = to_a ? w->occA : nullptr;
-    a.occA_rows = BM * w->cm;
+    a.occA_rows = BM;
     a.occA_n = w->ngA * w->nkb;
     a.occB = b_slot >= 0 ? w->occB[b_slot] : nullptr;
-    a.occB_rows = (BN / 2) * w->cn;
+    a.occB_rows = BN / 2;
     a.occB_n = w->ngB * w->nkb;
     a.st = p->state;
     a.gate = ZT_GATE_NONE;
@@ -1234,7 +1178,7 @@ int zt_split_operand(zt_plan* p, const double2* X, int to_a, int b_slot, cudaStr
 }
 
 static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, SplitArgs& a,
-                         int* ngroups_out, int* ntiles_out) {
+                         int* ngroups_out) {
     zt_split_ws* w = p->split;
     const int N = p->N;
     a.N = N;
@@ -1247,10 +1191,9 @@ static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int l
     a.exact_groups = w->exact_groups;
     a.ntn = w->Npad / BN;
     a.lower_only = lower_only;
-    a.cm = w->cm;
-    a.cn = w->cn;
-    a.ntmg = w->Mpad / (BM * w->cm);
-    a.ntng = w->Npad / (BN * w->cn);
+    a.ntng = w->Npad / BN;
+    a.wait_ns = w->wait_ns;
+    a.stall_loads = w->stall_loads;
     a.occA = w->skip_zero ? w->occA : nullptr;
     a.occB = w->skip_zero ? w->occB[b_slot] : nullptr;
     a.units = nullptr;
@@ -1260,49 +1203,28 @@ static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int l
     a.C = reinterpret_cast<double*>(C);
     a.st = p->state;
     a.gate = ZT_GATE_NONE;
-    const int cs = w->cm * w->cn;
-    a.order = lower_only ? w->order_lower : w->order_full;   // only groups with work, heaviest first
+    a.order = lower_only ? w->order_lower : w->order_full;   // only tiles with work
     const int ngroups = lower_only ? w->n_lower : w->n_full;
     a.ngroups = ngroups;
     a.tickets = nullptr;
     *ngroups_out = ngroups;
-    *ntiles_out = ngroups * cs;
 }
 
 int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, GemmEntry* out,
-                        int* ctas, int* cluster) {
+                        int* ctas) {
     zt_split_ws* w = p->split;
     if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
-    int ngroups, ntiles;
-    product_args(p, b_slot, C, alpha, lower_only, out->a, &ngroups, &ntiles);
+    int ngroups;
+    product_args(p, b_slot, C, alpha, lower_only, out->a, &ngroups);
     out->tmA = w->tmA;
     out->tmB = w->tmB[b_slot];
-    *cluster = w->cm * w->cn;
-    *ctas = ngroups * *cluster;
+    *ctas = ngroups;
     return ZT_OK;
 }
 
-int zt_split_gemm_grouped(const GemmEntry* tab, const int* offs, int n, int total, int cluster, cudaStream_t s,
-                          int gate) {
-    cudaError_t e;
-    if (cluster > 1) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(total);
-        cfg.blockDim = dim3(NTHREADS);
-        cfg.dynamicSmemBytes = SMEM_BYTES;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cluster;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, zgemm_split_grouped, tab, offs, n, gate);
-    } else {
-        zgemm_split_grouped<<<total, NTHREADS, SMEM_BYTES, s>>>(tab, offs, n, gate);
-        e = cudaGetLastError();
-    }
+int zt_split_gemm_grouped(const GemmEntry* tab, const int* offs, int n, int total, cudaStream_t s, int gate) {
+    zgemm_split_grouped<<<total, NTHREADS, SMEM_BYTES, s>>>(tab, offs, n, gate);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "zgemm_split_grouped");
     return ZT_OK;
 }
@@ -1312,34 +1234,14 @@ int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower
     if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
     const int N = p->N;
     SplitArgs a;
-    int ngroups, ntiles;
-    product_args(p, b_slot, C, alpha, lower_only, a, &ngroups, &ntiles);
+    int ngroups;
+    product_args(p, b_slot, C, alpha, lower_only, a, &ngroups);
     a.gate = gate;
-    a.units = p->timing ? p->d_units : nullptr;
-    const int cs = w->cm * w->cn;
-    (void)ntiles;   // issued work is counted on the device (skipped units vary with the data)
+    a.units = p->timing ? p->d_units : nullptr;   // issued work is counted on the device
     const double alg = lower_only ? 4.0 * N * (double)N * (N + 1.0) : 8.0 * (double)N * N * N;
     const int t = zt_timer_begin(p, ZT_KERNEL_PRODUCT, 0.0, alg, s);
     cudaError_t e;
-    if (cs > 1) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(ngroups * cs);
-        cfg.blockDim = dim3(NTHREADS);
-        cfg.dynamicSmemBytes = SMEM_BYTES;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = cs;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, zgemm_split_kernel, w->tmA, w->tmB[b_slot], a);
-        if (e != cudaSuccess) {
-            zt_timer_end(p, t, s);
-            return zt_cuda_check(e, "cudaLaunchKernelEx(zgemm_split_kernel)");
-        }
-    } else if (w->persistent) {   // one CTA per SM works through the tile groups
+    if (w->persistent) {   // one CTA per SM works through the tile groups
         e = cudaMemsetAsync(w->tickets, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) {
             zt_timer_end(p, t, s);
@@ -1489,10 +1391,9 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
     a.ntn = NA_NPAD / BN;
     a.lower_only = 0;
     a.tickets = nullptr;
-    a.cm = 1;
-    a.cn = 1;
-    a.ntmg = NA_MPAD / BM;
     a.ntng = NA_NPAD / BN;
+    a.wait_ns = 2000000000ull;
+    a.stall_loads = 0;
     a.occA = nullptr;   // no zero-unit skipping: every digit pair is multiplied
     a.occB = nullptr;
     a.units = nullptr;

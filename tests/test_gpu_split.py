@@ -122,26 +122,6 @@ def test_isomp_split_n1024_first_steps():
         assert _rel(Wd.cpu().numpy(), Wo) <= 1e-10
 
 
-@pytest.mark.parametrize("cm,cn", [(1, 1), (2, 1), (1, 2), (2, 2), (4, 1), (1, 4), (4, 2), (2, 4)])
-def test_cluster_shapes(cm, cn):
-    # TMA multicast within clusters of cm x cn CTAs: bit-exact integer products
-    # (full grid) and IsoMP steps (lower-triangle product grouping).
-    for N in (130, 300):
-        rng = np.random.default_rng(N + cm + 10 * cn)
-        Xi = rng.integers(-60, 61, (N, N)) + 1j * rng.integers(-60, 61, (N, N))
-        Yi = _int_su(N, N + 7)
-        got = _gemm(_split_plan(N, cluster_m=cm, cluster_n=cn), Xi, Yi)
-        assert np.array_equal(got, Xi @ Yi), (N, cm, cn)
-    N, h = 300, 0.01
-    W0 = vorticity_w0(N, seed=cm + cn)
-    plan = _split_plan(N, cluster_m=cm, cluster_n=cn)
-    Wd = _cuda(W0)
-    for _ in range(2):
-        z.isomp_step(plan, Wd, h)
-    want, _ = oracle.isomp_run(W0, h, 2)
-    assert _rel(Wd.cpu().numpy(), want) <= 1e-10
-
-
 def test_autotuner_picks_an_accurate_tuning(tmp_path, monkeypatch):
     from paper_2206_05466_gb300 import autotune
 
