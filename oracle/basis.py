@@ -145,12 +145,17 @@ def w_from_omega(N: int, omega: np.ndarray, lmax: int) -> np.ndarray:
     return W
 
 
-def omega_from_w(N: int, W: np.ndarray, lmax: int) -> np.ndarray:
-    """omega_lm = -i tr(T^_lm^H W) (orthonormal basis), l <= lmax."""
+def omega_from_w(N: int, W: np.ndarray, lmax: int, route: str = "3j") -> np.ndarray:
+    """omega_lm = -i tr(T^_lm^H W) (orthonormal basis), l <= lmax.
+
+    route "3j" builds T^_lm from Eq. 11 (exact 3j symbols, slow beyond N ~ 100);
+    route "eig" from the eigenvectors of the blocks with the sign rule (Sec. 3.2).
+    """
+    make = {"3j": that_lm, "eig": that_lm_eig}[route]
     out = np.zeros((lmax + 1) ** 2, dtype=np.complex128)
     for l in range(lmax + 1):
         for m in range(0, l + 1):
-            T = that_lm(N, l, m)
+            T = make(N, l, m)
             out[omega_index(l, m)] = -1j * np.sum(T * W)   # T real: tr(T^T W) = sum T_rc W_rc
             if m > 0:
                 out[omega_index(l, -m)] = -1j * ((-1) ** m) * np.sum(T.T * W)

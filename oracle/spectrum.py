@@ -22,12 +22,21 @@ import scipy.linalg
 from .zeitlin import laplacian_block
 
 
-def energy_spectrum(W: np.ndarray) -> np.ndarray:
-    """E_l, l = 0 .. N-1, of an N x N complex matrix W (see the module docstring)."""
+def energy_spectrum(W: np.ndarray, diagonals=None) -> np.ndarray:
+    """E_l, l = 0 .. N-1, of an N x N complex matrix W (see the module docstring).
+
+    `diagonals`: if given, W must vanish off the diagonals +-m for m in it (checked),
+    and only those blocks are visited (the others contribute nothing).
+    """
     W = np.asarray(W, dtype=np.complex128)
     N = W.shape[0]
     E = np.zeros(N)
-    for m in range(N):
+    ms = range(N)
+    if diagonals is not None:
+        ms = sorted(set(int(m) for m in diagonals))
+        r, c = np.indices((N, N))
+        assert not np.any(W[~np.isin(np.abs(r - c), ms)]), "W has content on other diagonals"
+    for m in ms:
         n = N - m
         a, b = laplacian_block(N, m)
         if n == 1:

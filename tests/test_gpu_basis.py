@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from oracle import basis as ob
-from paper_2206_05466_gb300.inputs import paper_omega
+from paper_2206_05466_gb300.inputs import paper_omega, vorticity_w0
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -103,3 +103,22 @@ def test_basis_argument_checks():
         z.zeitlin_w_from_omega(B, torch.zeros(15, dtype=torch.complex128, device="cuda"), W)
     B.close()
     plan.close()
+
+
+@pytest.mark.parametrize("N,lmax,route", [(40, 12, "3j"), (256, 20, "eig")])
+def test_omega_from_w_projects_a_full_matrix(N, lmax, route):
+    # W with content at every l <= N-1 (the seeded recipe): omega_from_w must
+    # return the projection onto the l <= lmax span, omega_lm = -i tr(T^_lm^H W),
+    # not just invert w_from_omega on that span
+    W = vorticity_w0(N, seed=9)
+    plan = z.Plan(N)
+    B = z.Basis(plan, lmax)
+    om = torch.empty((lmax + 1) ** 2, dtype=torch.complex128, device="cuda")
+    z.zeitlin_omega_from_w(B, torch.from_numpy(W).cuda(), om)
+    got = om.cpu().numpy()
+    B.close()
+    plan.close()
+    want = ob.omega_from_w(N, W, lmax, route=route)
+    assert np.abs(got - want).max() < 1e-12 * np.sqrt(N) * np.abs(W).max()
+    # the part of W off the span is really there: the projection loses norm
+    assert np.linalg.norm(want) < 0.999 * np.linalg.norm(W)

@@ -83,3 +83,37 @@ def test_spectrum_properties_at_n4096():
     # conditioned like cond(T_0) ~ N^2/2 on the lowest modes, which dominate H
     assert abs(H.imag) < 1e-12 * abs(H.real)
     assert abs(Eh.sum() - H.real) < 0.5 * N * N * np.finfo(float).eps * abs(H.real)
+
+
+def _on_diagonals(N, ms, seed):
+    rng = np.random.default_rng(seed)
+    W = np.zeros((N, N), complex)
+    for m in ms:
+        v = rng.standard_normal(N - m) + 1j * rng.standard_normal(N - m)
+        W[np.arange(m, N), np.arange(0, N - m)] = v
+        W[np.arange(0, N - m), np.arange(m, N)] = -np.conj(v)
+    d = np.diag_indices(N)
+    W[d] = 1j * W[d].imag
+    return W
+
+
+@pytest.mark.parametrize("N,ms", [(2048, [0, 1, 5, 64, 1024, 2046, 2047]),
+                                  (4096, [2, 1500, 3000, 4000, 4094, 4095])])
+def test_spectrum_element_wise_at_large_n(N, ms):
+    # content on a few diagonals only, so that the oracle visits just those
+    # blocks: element-wise at the benchmark sizes, including l close to large m
+    # (the last entries of the diagonals, where the recurrence starts) and the
+    # lowest l (extended-precision route)
+    W = _on_diagonals(N, ms, seed=N)
+    plan = z.Plan(N)
+    E = z.zeitlin_energy_spectrum(plan, torch.from_numpy(W).cuda()).cpu().numpy()
+    plan.close()
+    want = energy_spectrum(W, diagonals=ms)
+    L = 8
+    assert (np.abs(E[L + 1:] - want[L + 1:]) <= _tol(W, N)[L:]).all(), np.abs(E[L + 1:] - want[L + 1:]).max()
+    low = energy_spectrum_low(W, L).astype(np.float64)
+    nz = low[1:] > 0
+    if nz.any():
+        assert np.abs(E[1:L + 1][nz] / low[1:][nz] - 1).max() < 1e-13
+    assert np.all(E[1:L + 1][~nz] == 0.0) or not (~nz).any()
+    assert E[ms[-1]] > 0 and E[ms[-2]] > 0   # l = N-1, N-2 blocks of size 1 and 2

@@ -91,6 +91,7 @@ def test_w_from_omega_is_in_su_n_and_round_trips(N, lmax):
     assert abs(np.trace(W)) < 1e-13
     back = basis.omega_from_w(N, W, lmax)
     assert np.abs(back - om).max() < 1e-13
+    assert np.abs(basis.omega_from_w(N, W, lmax, route="eig") - om).max() < 1e-13
 
 
 @pytest.mark.parametrize("N,pairs", [(64, [(50, 40), (63, 63), (40, 1), (63, 0), (30, 29), (17, 9)]),

@@ -82,3 +82,19 @@ def test_reflection_parity_of_the_3j_basis(N):
         for m in range(l + 1):
             v = np.diag(basis.that_lm(N, l, m), -m)
             assert np.abs(v[::-1] - (-1) ** (l - m) * v).max() < 1e-14, (l, m)
+
+
+def test_restricting_to_the_occupied_diagonals_changes_nothing():
+    # a matrix with content on a few diagonals only: visiting just those blocks
+    # gives the same spectrum as visiting all of them
+    N = 40
+    rng = np.random.default_rng(3)
+    W = np.zeros((N, N), complex)
+    for m in (0, 2, 17, 39):
+        v = rng.standard_normal(N - m) + 1j * rng.standard_normal(N - m)
+        W[np.arange(m, N), np.arange(0, N - m)] = v
+        W[np.arange(0, N - m), np.arange(m, N)] = -np.conj(v)
+    W[np.diag_indices(N)] = 1j * W[np.diag_indices(N)].imag
+    assert np.array_equal(energy_spectrum(W, diagonals=[0, 2, 17, 39]), energy_spectrum(W))
+    with pytest.raises(AssertionError):
+        energy_spectrum(W, diagonals=[0, 2])
