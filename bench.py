@@ -206,7 +206,7 @@ def _tuning(args, N):
         return dict(res["tuning"]), {"mode": "auto", "target_rel_err": args.tune_target,
                                      "probe_rel_err": res["rel_err"], "probe_ms": res["ms"]}
     tun = dict(slices=args.slices, digit_bits=args.digit_bits, exact_groups=args.exact_groups,
-               cluster_m=args.cluster_m, cluster_n=args.cluster_n, tile_order=args.tile_order)
+               tile_order=args.tile_order)
     return tun, {"mode": "fixed"}
 
 
@@ -424,6 +424,79 @@ def _serving(args, duration):
     return rep
 
 
+def _drift_leg(N, prec, h, steps, tun=None):
+    """`steps` IsoMP steps from the seeded W0; relative drift of the Casimirs C2..C5
+    (device, with an FP64 plan's products) and of the spectrum (host eigenvalues)."""
+    import numpy as np
+    import torch
+
+    from paper_2206_05466_gb300 import zeitlin as z
+    from paper_2206_05466_gb300.inputs import vorticity_w0
+
+    W0 = vorticity_w0(N, seed=0)
+    plan = z.Plan(N, prec, **(tun or {}))
+    meas = z.Plan(N, z.PRECISION_FP64)   # Casimirs with FP64 products: rounding far below the drift bound
+    W = torch.from_numpy(W0).cuda()
+    c0 = z.zeitlin_casimirs(meas, W)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = z.isomp_run(plan, W, h, steps, TOL, MAXIT)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    c1 = z.zeitlin_casimirs(meas, W)
+    W1 = W.cpu().numpy()
+    plan.close()
+    meas.close()
+    mu0 = np.linalg.eigvalsh(-1j * W0)
+    mu1 = np.linalg.eigvalsh(-1j * W1)
+    scale = {k: float(np.sum(np.abs(mu0) ** k)) for k in (2, 3, 4, 5)}
+    per = 1000.0 / steps
+    dev = {f"C{k}": float(abs(c1[k] - c0[k]) / scale[k]) * per for k in (2, 3, 4, 5)}
+    host = {f"C{k}": float(abs(np.sum(mu1 ** k) - np.sum(mu0 ** k)) / scale[k]) * per for k in (2, 3, 4)}
+    return {"N": N, "precision": "split" if prec == z.PRECISION_SPLIT else "fp64", "h": h, "steps": steps,
+            "steps_per_s": steps / dt, "sweeps_total": r["total_iters"], "all_converged": r["all_converged"],
+            "per_1000_steps": dev, "max_per_1000_steps": max(dev.values()),
+            "host_eig_per_1000_steps": host,
+            "spectrum_max_abs_per_1000_steps": float(np.max(np.abs(mu1 - mu0))) * per,
+            "measure": "C_k = tr(W^k) on the device with FP64 products, relative to sum_j |lambda_j|^k of W0; "
+                       "host: power sums of eigvalsh(-i W)",
+            "bound": 1e-10}
+
+
+def _dense_product(N, tun):
+    """Throughput of the split product with every digit pair multiplied (dense=1): the
+    kernel's efficiency without the zero-tile skipping the decaying workload allows."""
+    import torch
+
+    from paper_2206_05466_gb300 import zeitlin as z
+    from paper_2206_05466_gb300.inputs import vorticity_w0
+
+    t = dict(tun)
+    t["dense"] = 1
+    plan = z.Plan(N, z.PRECISION_SPLIT, **t)
+    W = torch.from_numpy(vorticity_w0(N, seed=0)).cuda()
+    P = torch.empty_like(W)
+    C = torch.empty_like(W)
+    z.zeitlin_stream_solve(plan, W, P)
+    for _ in range(2):
+        z.zt_zgemm_skew(plan, P, W, C)
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    reps = 5
+    for _ in range(reps):
+        z.zt_zgemm_skew(plan, P, W, C)
+    torch.cuda.synchronize()
+    k = plan.kernel_time(z.KERNEL_PRODUCT)
+    plan.set_timing(False)
+    plan.close()
+    tf = k["work"] / (k["total_ms"] / 1e3) / 1e12
+    peak = _peaks()["bf16_tflops"]   # timed alone, back to back: the burst peak
+    return {"N": N, "launches": k["launches"], "avg_launch_ms": k["total_ms"] / k["launches"],
+            "achieved_tflops": tf, "peak_tflops": peak, "frac": tf / peak,
+            "peak_source": f"{_peaks()['source']} bf16 burst",
+            "fp64_equivalent_tflops": k["work_alg"] / (k["total_ms"] / 1e3) / 1e12}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -542,6 +615,16 @@ def run_gpu(args):
                 pl.close()
         accuracy = acc
 
+    drift = dense = None
+    if rank == 0 and args.casimir_steps > 0:
+        _log("casimir drift (split)")
+        drift = {"split": _drift_leg(N, z.PRECISION_SPLIT, H, args.casimir_steps, tun)}
+        if args.casimir_fp64_steps > 0:
+            _log("casimir drift (fp64)")
+            drift["fp64"] = _drift_leg(args.casimir_fp64_n, z.PRECISION_FP64, 0.01, args.casimir_fp64_steps)
+    if rank == 0 and args.dense_product:
+        _log("dense product")
+        dense = _dense_product(N, tun)
     ens = serve = None
     _log("ensemble")
     if rank == 0 and args.ens_steps > 0:
@@ -591,6 +674,8 @@ def run_gpu(args):
         "accuracy": accuracy,
         "ensemble": ens,
         "serving": serve,
+        "casimir_drift_per_1000": drift,
+        "dense_product": dense,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -607,7 +692,13 @@ def main():
     ap.add_argument("--mode", default="bench", choices=["bench", "casimir", "ensemble", "serving", "profile", "spectrum"])
     ap.add_argument("--ens-count", type=int, default=256)
     ap.add_argument("--ens-steps", type=int, default=20)
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=120.0)
+    ap.add_argument("--casimir-steps", type=int, default=1000,
+                    help="split steps at --n for the Casimir drift (0: skip)")
+    ap.add_argument("--casimir-fp64-n", type=int, default=1024)
+    ap.add_argument("--casimir-fp64-steps", type=int, default=1000,
+                    help="FP64-form steps at --casimir-fp64-n, h = 0.01, for its Casimir drift (0: skip)")
+    ap.add_argument("--dense-product", type=int, default=1, help="time the product with dense=1 (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-target-ms", type=float, default=100.0,
                     help="step latency above which a serving class admits no further job")
@@ -616,8 +707,6 @@ def main():
     ap.add_argument("--slices", type=int, default=7)
     ap.add_argument("--digit-bits", type=int, default=7)
     ap.add_argument("--exact-groups", type=int, default=4)
-    ap.add_argument("--cluster-m", type=int, default=1)
-    ap.add_argument("--cluster-n", type=int, default=1)
     ap.add_argument("--tile-order", type=int, default=0)
     ap.add_argument("--fp64", action="store_true", help="profile mode: the FP64 form")
     ap.add_argument("--fp64-steps", type=int, default=2)
