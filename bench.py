@@ -203,8 +203,12 @@ def _tuning(args, N):
         from paper_2206_05466_gb300 import autotune
 
         res = autotune.autotune(N, target=args.tune_target)
+        timed = sorted((t for t in res["trials"] if "ms" in t), key=lambda t: t["ms"])
         return dict(res["tuning"]), {"mode": "auto", "target_rel_err": args.tune_target,
-                                     "probe_rel_err": res["rel_err"], "probe_ms": res["ms"]}
+                                     "probe_rel_err": res["rel_err"], "probe_ms": res["ms"],
+                                     "candidates": len(res["trials"]),
+                                     "fastest": [{**t["tuning"], "ms": round(t["ms"], 3),
+                                                  "rel_err": t["rel_err"]} for t in timed[:6]]}
     tun = dict(slices=args.slices, digit_bits=args.digit_bits, exact_groups=args.exact_groups,
                tile_order=args.tile_order)
     return tun, {"mode": "fixed"}

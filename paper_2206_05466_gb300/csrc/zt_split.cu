@@ -1044,10 +1044,11 @@ int zt_split_create(zt_plan* p) {
         ZT_CU(cudaMemsetAsync(w->eB[b], 0, (size_t)w->Npad * sizeof(int), cs));
         if ((rc = make_map(&w->tmB[b], w->dB[b], s * w->Npad, w->ldk, BN))) return rc;
     }
-    // Launch orders.  0, 3: column blocks of 8 or 16 tile groups, rows walked
-    // inside a block, so that the tiles resident at one time share a few
-    // B'^T panels across many rows (at N = 4096 the digit planes exceed L2:
-    // DRAM reads per product fall from 8.0 to 5.0 GB against row-major).
+    // Launch orders.  0, 3, 4, 5: column blocks of 8, 16, 4 or 2 tiles, rows
+    // walked inside a block, so that the tiles resident at one time share a
+    // few B'^T panels across many rows (at N = 4096 the digit planes exceed
+    // L2: DRAM reads per product fall from 8.0 to 5.0 GB against row-major
+    // with blocks of 8; narrower blocks keep the active panels inside L2).
     // 1: row-major.  2: with all-zero digit tiles skipped, tiles near the
     // diagonal (where the leading digits of both operands are nonzero) carry
     // most of the work, so they are dispatched first and the light far tiles
@@ -1055,7 +1056,7 @@ int zt_split_create(zt_plan* p) {
     {
         const int ntmg = w->Mpad / BM, ntng = w->Npad / BN;
         const int order = p->tun.tile_order;
-        const int cblk = order == 0 ? 8 : order == 3 ? 16 : ntng;
+        const int cblk = order == 0 ? 8 : order == 3 ? 16 : order == 4 ? 4 : order == 5 ? 2 : ntng;
         std::vector<std::pair<double, int>> full, lower;
         for (int cb0 = 0; cb0 < ntng; cb0 += cblk)
             for (int tg = 0; tg < ntmg; ++tg)

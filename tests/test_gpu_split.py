@@ -189,3 +189,21 @@ def test_persistent_kernel_equals_one_tile_per_cta(N):
         outs.append(Wd.cpu().numpy())
         plan.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("order", [0, 1, 2, 3, 4, 5])
+def test_launch_orders_give_identical_products(order):
+    # the launch order permutes the tiles, never their arithmetic
+    N = 700
+    W = vorticity_w0(N, seed=12)
+    P = oracle.stream_solve(W)
+    base = _gemm(_split_plan(N, slices=6, digit_bits=8, exact_groups=2), P, W)
+    got = _gemm(_split_plan(N, slices=6, digit_bits=8, exact_groups=2, tile_order=order), P, W)
+    assert np.array_equal(got, base)
+    for flag in (0, 1):
+        plan = z.Plan(N, z.PRECISION_SPLIT, tile_order=order, no_persistent=flag)
+        Wd = torch.from_numpy(W.copy()).cuda()
+        z.isomp_step(plan, Wd, 0.01)
+        want, _ = oracle.isomp_step(W, 0.01)
+        assert _rel(Wd.cpu().numpy(), want) <= 1e-10
+        plan.close()
