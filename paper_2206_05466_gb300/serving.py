@@ -2,20 +2,23 @@
 
 Jobs (N, number of steps, h, precision, initial state) arrive over time.  Jobs
 of like N and precision form a class; each class has its own first-come,
-first-served queue.  The head of a class's queue is admitted when its plan's
-device footprint fits the memory budget and the class's step latency allows
-it: a class with no resident job always takes its head job; otherwise a new job
-joins only after the class has completed a step with its current set and while
-the class's measured step latency (moving average) is below the target.  Under
-overload the queues absorb the excess (reported as queueing delay) instead of
-the batches growing until every resident job's step takes seconds.  An admitted
-job's state stays resident on the device until its last step.  Each class is
-advanced by its own worker thread on its own CUDA stream (smaller N at higher
-priority), one batched step (grouped kernels over all the class's jobs) per
-iteration.  Jobs that are admitted while others are running join their class's
-batch at its next step, and classes run concurrently on the device.  A class's
-batch is rebuilt only when its resident set changes.  All arithmetic runs in
-the library's kernels; this module only schedules.
+first-served queue.  Before serving, each class's solo step time (a batched
+step of one and of two instances alone on the device) is calibrated.  The head
+of a class's queue is admitted when its plan's device footprint fits the memory
+budget and the admission policy (next_admission) allows it: at most two classes
+are resident at once (so each shares the device with at most one other), and a
+resident class takes another job only after it completed a step with its
+current set, while its measured step time stays within twice its solo step time
+and its solo step time with one more job stays below an absolute target; after
+a session of 20 s a class stops taking jobs while other classes wait, so that
+the resident classes rotate.  Under overload the queues absorb the excess
+(reported as queueing delay).  An admitted job's state stays resident on the
+device until its last step.  Each class is advanced by its own worker thread on
+its own CUDA stream, one batched step (grouped kernels over all the class's
+jobs) per iteration; jobs admitted while others run join their class's batch
+at its next step, and the two resident classes run concurrently on the device.
+A class's batch is rebuilt only when its resident set changes.  All arithmetic
+runs in the library's kernels; this module only schedules.
 
 Reported: per-step latency of resident jobs (time between a job's consecutive
 completed steps; p50/p99, overall and per class), aggregate job-steps/s,
@@ -58,23 +61,57 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs) * 1e3, q)) if len(xs) else None
 
 
-def next_admission(queues, resident, used, budget, stepped, ema, target, estimate):
+def solo_step_s(solo, cls, n):
+    """Calibrated step time of class `cls` with n resident jobs, running alone on the
+    device: solo[cls] = (t1, per_job), t1 + per_job * (n - 1) seconds."""
+    t1, per = solo[cls]
+    return t1 + per * max(0, n - 1)
+
+
+def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate, factor=2.0,
+                   max_active=2, target=None, active_since=None, now=0.0, session_s=None):
     """The class whose head job is admitted next, or None (the admission policy).
 
     queues: class -> deque of waiting jobs (FIFO per class); classes are tried in
     the order of their head job's arrival.  resident: class -> number of resident
-    jobs.  A head job fits when its plan footprint estimate(N, precision) fits the
-    remaining budget, or nothing at all is resident.  A class with resident jobs
-    admits another only after a completed step with its current set (stepped)
-    and while its step-time average ema[class] is below target (seconds; None:
-    footprint only).
+    jobs; a class with resident jobs is active.
+      * Device sharing: at most `max_active` classes are active at once, so that a
+        class's steps share the device with at most max_active - 1 others (with
+        two, each gets at least about half the device: step time <= 2x solo).
+      * Memory: the head job's plan footprint estimate(N, precision) must fit the
+        remaining budget, unless nothing at all is resident.
+      * Latency: an active class admits another job only after it completed a step
+        with its current set (stepped), while its measured step time ema[cls] is
+        within `factor` times its calibrated solo step time with that set
+        (solo_step_s), and while the solo step time with one more job stays within
+        the absolute `target` (seconds).  With neither (both None) admission is by
+        footprint and the number of active classes alone.
+      * Sessions: an active class that has been active for more than session_s
+        seconds (active_since[cls]) admits no further job while a class that is not
+        active has jobs waiting, so that the active classes drain and free their
+        place (None: no limit).
     """
-    anything = sum(resident.values()) > 0
+    active = {c for c, n in resident.items() if n > 0}
+    anything = bool(active)
+    waiting_inactive = any(queues[c] for c in queues if c not in active)
     for cls in sorted((c for c in queues if queues[c]), key=lambda c: queues[c][0].arrival):
         head = queues[cls][0]
         if used + estimate(head.N, head.precision) > budget and anything:
             continue
-        if resident.get(cls) and target is not None and not (stepped.get(cls) and ema.get(cls, 0.0) < target):
+        n = resident.get(cls, 0)
+        if n == 0:
+            if len(active) >= max_active:
+                continue
+            return cls
+        if factor is not None or target is not None:
+            if not stepped.get(cls):
+                continue
+            if factor is not None and (cls not in ema or ema[cls] > factor * solo_step_s(solo, cls, n)):
+                continue
+            if target is not None and solo_step_s(solo, cls, n + 1) > target:
+                continue
+        if (session_s is not None and active_since is not None and waiting_inactive
+                and now - active_since.get(cls, now) > session_s):
             continue
         return cls
     return None
@@ -82,33 +119,78 @@ def next_admission(queues, resident, used, budget, stepped, ema, target, estimat
 
 class Server:
     def __init__(self, budget_bytes: int, tol: float = 1e-12, maxit: int = 50, graph: bool = False,
-                 target_step_ms: float | None = 100.0):
-        """target_step_ms: step latency above which a class admits no further job
-        (None: admission by memory footprint alone)."""
+                 target_step_ms: float | None = 100.0, latency_factor: float = 2.0, max_active: int = 2,
+                 session_s: float | None = 20.0):
+        """target_step_ms: a class admits another job only while its solo step time with
+        that job stays below this (None: no absolute bound); latency_factor: ... and
+        while its measured step time is within this factor of its solo step time;
+        max_active: classes resident at once; session_s: after this long, an active
+        class stops admitting while other classes wait (None: no limit)."""
         self.budget = int(budget_bytes)
         self.tol = tol
         self.maxit = maxit
         self.graph = graph
         self.target = None if target_step_ms is None else float(target_step_ms) * 1e-3
+        self.factor = None if latency_factor is None else float(latency_factor)
+        self.max_active = int(max_active)
+        self.session_s = session_s
 
-    def run(self, jobs, time_limit: float | None = None, keep_results: bool = False, clock=time.perf_counter):
-        """Serve `jobs`; returns a report dict (results by job id if keep_results)."""
+    def calibrate(self, classes, W0s, h=0.01, reps=2):
+        """Solo step time of each class (N, precision), alone on the device: batched steps
+        of one and of two instances (seconds), as {cls: (t1, per_job)}."""
         import torch
+
+        out = {}
+        for cls in classes:
+            N, prec = cls
+            times = []
+            for n in (1, 2):
+                plans = [z.Plan(N, prec) for _ in range(n)]
+                Ws = [torch.from_numpy(np.ascontiguousarray(W0s[cls])).cuda() for _ in range(n)]
+                b = z.Batch(plans, Ws, [h] * n)
+                b.step(self.tol, self.maxit, allow_not_converged=True)   # warm-up
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                for _ in range(reps):
+                    b.step(self.tol, self.maxit, allow_not_converged=True)
+                torch.cuda.synchronize()
+                times.append((time.perf_counter() - t) / reps)
+                b.close()
+                for p in plans:
+                    p.close()
+            out[cls] = (times[0], max(0.0, times[1] - times[0]))
+        return out
+
+    def run(self, jobs, time_limit: float | None = None, keep_results: bool = False, clock=time.perf_counter,
+            solo=None):
+        """Serve `jobs`; returns a report dict (results by job id if keep_results).
+        solo: calibrated solo step times ({cls: (t1, per_job)}); measured with
+        calibrate() on the jobs' classes when None."""
+        import torch
+
+        if solo is None:
+            firsts = {}
+            for j in jobs:
+                firsts.setdefault((j.N, j.precision), j.W0)
+            tc = time.perf_counter()
+            solo = self.calibrate(sorted(firsts), firsts)
+            calib_s = time.perf_counter() - tc
+        else:
+            calib_s = 0.0
 
         dev = torch.cuda.current_device()
         low, high = torch.cuda.Stream.priority_range()   # e.g. (0, -5): lower number = higher priority
         # admissions copy state on the highest-priority stream, never waiting on running steps
         upload = torch.cuda.Stream(priority=high)
-        sizes = sorted({j.N for j in jobs})
 
-        def class_priority(N):   # smaller matrices are the latency-sensitive classes
-            rank = sizes.index(N)
-            span = max(1, len(sizes) - 1)
-            return int(round(high + (low - high) * rank / span))
+        def class_priority(N):   # the two active classes share the device evenly
+            return low
         lock = threading.Lock()
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
         queues: dict[tuple, collections.deque] = collections.defaultdict(collections.deque)
         ema: dict[tuple, float] = {}            # moving average of the class's step time (s)
+        active_since: dict[tuple, float] = {}   # start of the class's current session (s)
+        res_hist: dict[tuple, list] = collections.defaultdict(list)   # resident count at each step
         stepped: dict[tuple, bool] = {}         # a step completed since the class's last admission
         classes: dict[tuple, dict[int, _Resident]] = {}
         dirty: dict[tuple, bool] = {}
@@ -163,6 +245,7 @@ class Server:
                         dt = t_done - t_start
                         ema[cls] = dt if cls not in ema else 0.7 * ema[cls] + 0.3 * dt
                         stepped[cls] = True
+                        res_hist[cls].append(len(order))
                         for j in order:
                             r = classes[cls][j]
                             lat[cls].append(t_done - r.last_done)
@@ -206,10 +289,15 @@ class Server:
                 job = None
                 with lock:
                     cls = next_admission(queues, {c: len(v) for c, v in classes.items()}, st["used"], self.budget,
-                                         stepped, ema, self.target, z.plan_estimate_bytes)
+                                         stepped, ema, solo, z.plan_estimate_bytes, factor=self.factor,
+                                         max_active=self.max_active, target=self.target,
+                                         active_since=active_since, now=clock() - t0, session_s=self.session_s)
                     if cls is not None:
                         job = queues[cls].popleft()
                         stepped[cls] = False
+                        if not classes.get(cls):
+                            active_since[cls] = clock() - t0
+                            ema.pop(cls, None)   # a new session measures afresh
                 if job is None:
                     break
                 need = z.plan_estimate_bytes(job.N, job.precision)
@@ -266,8 +354,18 @@ class Server:
             "step_latency_ms_p99": _pct(allat, 99),
             "per_class": {f"N={k[0]},{'split' if k[1] == z.PRECISION_SPLIT else 'fp64'}":
                           {"job_steps": len(v), "p50_ms": _pct(v, 50), "p99_ms": _pct(v, 99),
-                           "max_resident": max_res[k]}
+                           "max_resident": max_res[k],
+                           "solo_ms_at_mean_resident": 1e3 * solo_step_s(solo, k, round(np.mean(res_hist[k])))
+                           if res_hist[k] else None,
+                           "p99_over_solo": (_pct(v, 99) / (1e3 * solo_step_s(solo, k, round(np.mean(res_hist[k])))))
+                           if res_hist[k] else None}
                           for k, v in lat.items()},
+            "solo_calibration_ms": {f"N={k[0]},{'split' if k[1] == z.PRECISION_SPLIT else 'fp64'}":
+                                    [1e3 * solo[k][0], 1e3 * solo[k][1]] for k in solo},
+            "calibration_s": calib_s,
+            "policy": {"max_active_classes": self.max_active, "latency_factor": self.factor,
+                       "target_step_ms": None if self.target is None else self.target * 1e3,
+                       "session_s": self.session_s},
             "queue_delay_s_p50": float(np.percentile(qdelay, 50)) if qdelay else None,
             "peak_admitted_bytes": st["peak"],
             "admit_plan_ms_mean": float(np.mean([a for a, _ in admit_times]) * 1e3) if admit_times else None,

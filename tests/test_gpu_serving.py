@@ -49,7 +49,8 @@ def test_results_alone_equal_results_in_the_mix():
 
 def test_latency_target_admits_one_job_per_class_at_a_time():
     """A target no step can meet: each class keeps exactly one resident job, the
-    rest wait in the class's queue; results are unchanged."""
+    rest wait in the class's queue; at most two classes are resident at once;
+    results are unchanged."""
     jobs = _jobs()
     rep = serving.Server(1 << 40, target_step_ms=1e-6).run(jobs, keep_results=True)
     assert rep["jobs_completed"] == len(jobs)
@@ -63,7 +64,7 @@ def test_footprint_only_admission_batches_jobs_of_a_class():
     start are admitted together and stepped as one batch."""
     jobs = [serving.Job(jid=k, N=40, nsteps=40, h=0.01, precision=z.PRECISION_SPLIT, arrival=0.0,
                         W0=vorticity_w0(40, seed=40 + k)) for k in range(4)]
-    rep = serving.Server(1 << 40, target_step_ms=None).run(jobs, keep_results=True)
+    rep = serving.Server(1 << 40, target_step_ms=None, latency_factor=None).run(jobs, keep_results=True)
     assert rep["jobs_completed"] == 4
     assert rep["per_class"]["N=40,split"]["max_resident"] == 4
     assert rep["batched_steps"] < rep["job_steps"]

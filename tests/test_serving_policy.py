@@ -2,7 +2,7 @@
 import collections
 import dataclasses
 
-from paper_2206_05466_gb300.serving import next_admission
+from paper_2206_05466_gb300.serving import next_admission, solo_step_s
 
 
 @dataclasses.dataclass
@@ -23,38 +23,78 @@ def est(N, precision):
     return N * 10
 
 
+SOLO = collections.defaultdict(lambda: (0.010, 0.002))   # 10 ms for one job, +2 ms per further job
+
+
+def pick(q, res, used=0, budget=10**9, stepped=None, ema=None, **kw):
+    return next_admission(q, res, used, budget, stepped or {}, ema or {}, SOLO, est, **kw)
+
+
+def test_solo_model():
+    assert abs(solo_step_s({"c": (0.01, 0.002)}, "c", 1) - 0.01) < 1e-15
+    assert abs(solo_step_s({"c": (0.01, 0.002)}, "c", 4) - 0.016) < 1e-15
+
+
 def test_classes_in_order_of_their_head_arrival():
     q = _q(J(512, 0, 2.0), J(256, 1, 1.0), J(256, 1, 3.0))
-    assert next_admission(q, {}, 0, 10**9, {}, {}, 0.1, est) == (256, 1)
+    assert pick(q, {}) == (256, 1)
 
 
 def test_budget_skips_a_head_that_does_not_fit_but_not_when_nothing_is_resident():
     q = _q(J(4096, 0, 0.0), J(256, 0, 1.0))
     # nothing resident: the first head is admitted even above the budget
-    assert next_admission(q, {}, 0, 1000, {}, {}, None, est) == (4096, 0)
+    assert pick(q, {}, 0, 1000) == (4096, 0)
     # something resident: the big head waits, the later small class goes first
-    assert next_admission(q, {(512, 0): 1}, 500, 4000, {}, {}, None, est) == (256, 0)
+    assert pick(q, {(512, 0): 1}, 500, 4000) == (256, 0)
     # nothing fits
-    assert next_admission(q, {(512, 0): 1}, 3990, 4000, {}, {}, None, est) is None
+    assert pick(q, {(512, 0): 1}, 3990, 4000) is None
 
 
-def test_latency_target_gates_a_class_with_resident_jobs():
+def test_at_most_two_classes_resident():
+    q = _q(J(256, 1, 0.0), J(1024, 0, 1.0))
+    res = {(512, 0): 2, (2048, 1): 1}
+    assert pick(q, res) is None                     # two classes active: no third
+    assert pick(q, res, max_active=3) == (256, 1)
+    assert pick(q, {(512, 0): 2}) == (256, 1)       # one active: a second may start
+
+
+def test_latency_gates_a_resident_class():
+    c = (256, 1)
     q = _q(J(256, 1, 0.0))
-    res = {(256, 1): 3}
+    res = {c: 3}   # solo with 3 jobs: 14 ms
     # no completed step since the last admission: wait
-    assert next_admission(q, res, 0, 10**9, {(256, 1): False}, {(256, 1): 0.01}, 0.1, est) is None
-    # stepped, but slower than the target: wait
-    assert next_admission(q, res, 0, 10**9, {(256, 1): True}, {(256, 1): 0.2}, 0.1, est) is None
-    # stepped and fast enough: admit
-    assert next_admission(q, res, 0, 10**9, {(256, 1): True}, {(256, 1): 0.05}, 0.1, est) == (256, 1)
-    # no target: footprint only
-    assert next_admission(q, res, 0, 10**9, {}, {}, None, est) == (256, 1)
+    assert pick(q, res, stepped={c: False}, ema={c: 0.014}) is None
+    # stepped, but slower than twice solo (28 ms): wait
+    assert pick(q, res, stepped={c: True}, ema={c: 0.030}) is None
+    # stepped, within twice solo: admit
+    assert pick(q, res, stepped={c: True}, ema={c: 0.020}) == c
+    # the absolute target bounds the solo step time with one more job (16 ms)
+    assert pick(q, res, stepped={c: True}, ema={c: 0.020}, target=0.015) is None
+    assert pick(q, res, stepped={c: True}, ema={c: 0.020}, target=0.017) == c
+    # an empty class always takes its head job, whatever the target
+    assert pick(_q(J(1024, 0, 0.0)), {}, target=0.001) == (1024, 0)
 
 
-def test_an_empty_class_always_takes_its_head_job():
-    q = _q(J(1024, 0, 0.0))
-    assert next_admission(q, {(256, 1): 5}, 0, 10**9, {}, {(1024, 0): 9.9}, 0.1, est) == (1024, 0)
+def test_sessions_rotate_classes():
+    c, other = (256, 1), (512, 0)
+    q = _q(J(256, 1, 5.0), J(512, 0, 1.0))
+    res = {c: 2, (1024, 0): 1}   # two active classes; `other` waits for a place
+    kw = dict(stepped={c: True}, ema={c: 0.012}, session_s=20.0)
+    # within its session the active class keeps admitting
+    assert pick(q, res, active_since={c: 0.0}, now=10.0, **kw) == c
+    # past its session, with another class waiting, it admits no more
+    assert pick(q, res, active_since={c: 0.0}, now=30.0, **kw) is None
+    # ... but it does when nobody else waits
+    q2 = _q(J(256, 1, 5.0))
+    assert pick(q2, res, active_since={c: 0.0}, now=30.0, **kw) == c
 
 
 def test_empty_queues():
-    assert next_admission(_q(), {}, 0, 10**9, {}, {}, 0.1, est) is None
+    assert pick(_q(), {}) is None
+
+
+def test_no_latency_gate_admits_by_footprint_and_class_count():
+    c = (40, 1)
+    q = _q(J(40, 1, 0.0), J(40, 1, 0.0))
+    assert pick(q, {c: 1}, factor=None, target=None) == c
+    assert pick(q, {c: 1}, factor=None, target=None, stepped={c: False}) == c
