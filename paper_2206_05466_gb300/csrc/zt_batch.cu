@@ -18,11 +18,12 @@
 
 namespace {
 
-struct CopyArgs {   // W -> W_n and W -> Wt
+struct CopyArgs {   // W -> W_n and W -> Wt, and the instance's step state reset
     const double2* src;
     double2* d1;
     double2* d2;
     long long count;
+    zt_dev_state* st;
 };
 constexpr int COPY_PER_CTA = 256 * 4;
 
@@ -35,9 +36,22 @@ struct Op {          // one grouped launch: table and CTA prefix sums in device 
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) copy_grouped(const CopyArgs* tab, const int* offs, int n) {
+__global__ void __launch_bounds__(256) copy_grouped(const CopyArgs* tab, const int* offs, int n, double tol,
+                                                    int maxit) {
     const int inst = zt_group_find(offs, n, blockIdx.x);
     const CopyArgs a = tab[inst];
+    if (blockIdx.x == offs[inst] && threadIdx.x == 0) {   // the instance's first CTA resets its state
+        zt_dev_state* st = a.st;
+        st->done = 0;
+        st->iters = 0;
+        st->converged = 0;
+        st->nonfinite = 0;
+        st->timeout = 0;
+        st->maxit = maxit;
+        st->residual = 0.0;
+        st->tol = tol;
+        st->finalized = 0;
+    }
     const long long base = (long long)(blockIdx.x - offs[inst]) * COPY_PER_CTA;
     for (int q = 0; q < 4; ++q) {
         const long long i = base + threadIdx.x + 256 * q;
@@ -47,21 +61,6 @@ __global__ void __launch_bounds__(256) copy_grouped(const CopyArgs* tab, const i
             a.d2[i] = v;
         }
     }
-}
-
-__global__ void state_init_grouped(zt_dev_state* const* sts, int n, double tol, int maxit) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    zt_dev_state* st = sts[i];
-    st->done = 0;
-    st->iters = 0;
-    st->converged = 0;
-    st->nonfinite = 0;
-    st->timeout = 0;
-    st->maxit = maxit;
-    st->residual = 0.0;
-    st->tol = tol;
-    st->finalized = 0;
 }
 
 __global__ void state_gather(zt_dev_state* const* sts, int n, zt_dev_state* out) {
@@ -82,7 +81,7 @@ struct zt_batch {
     zt_dev_state** dstates = nullptr;
     zt_dev_state* gathered = nullptr;
     zt_dev_state* hstates = nullptr;   // pinned host copy of the states (also the captured memcpy target)
-    Op copy, solve, split_P, split_W, split_A, gemm1, gemm2, f64a, f64b, upd_sweep, upd_final, conv;
+    Op copy, solve, split_PW, split_A, gemm1, gemm2, f64a, f64b, upd_sweep, upd_final;
     int sweeps_per_sync = 4;
     long launches = 0;
     int use_graph = 0;
@@ -151,11 +150,9 @@ int enqueue_products(zt_batch* b, cudaStream_t s, int gate) {
         return rc;
     b->launches += ZT_SOLVE_LAUNCHES;
     if (b->gemm1.n) {
-        if ((rc = zt_split_rows_grouped((const SplitRowsArgs*)b->split_P.tab, b->split_P.offs, b->split_P.n,
-                                        b->split_P.total, s, gate)))
-            return rc;
-        if ((rc = zt_split_rows_grouped((const SplitRowsArgs*)b->split_W.tab, b->split_W.offs, b->split_W.n,
-                                        b->split_W.total, s, gate)))
+        // Pt into the X' planes and B'^T slot 1, Wt into slot 0: one launch
+        if ((rc = zt_split_rows_grouped((const SplitRowsArgs*)b->split_PW.tab, b->split_PW.offs, b->split_PW.n,
+                                        b->split_PW.total, s, gate)))
             return rc;
         if ((rc = zt_split_gemm_grouped((const GemmEntry*)b->gemm1.tab, b->gemm1.offs, b->gemm1.n, b->gemm1.total,
                                         s, gate)))
@@ -166,7 +163,7 @@ int enqueue_products(zt_batch* b, cudaStream_t s, int gate) {
         if ((rc = zt_split_gemm_grouped((const GemmEntry*)b->gemm2.tab, b->gemm2.offs, b->gemm2.n, b->gemm2.total,
                                         s, gate)))
             return rc;
-        b->launches += 8;
+        b->launches += 4;
     }
     if (b->f64a.n) {
         if ((rc = zt_fp64_gemm_grouped((const Fp64GemmArgs*)b->f64a.tab, b->f64a.offs, b->f64a.n, b->f64a.total, s,
@@ -186,9 +183,7 @@ int enqueue_sweep(zt_batch* b, cudaStream_t s) {
     if ((rc = zt_update_grouped((const UpdateArgs*)b->upd_sweep.tab, b->upd_sweep.offs, b->upd_sweep.n,
                                 b->upd_sweep.total, s, ZT_GATE_SWEEP)))
         return rc;
-    b->launches++;
-    if ((rc = zt_converge_grouped((const ConvArgs*)b->conv.tab, b->conv.n, s))) return rc;
-    b->launches++;
+    b->launches++;   // each instance's last CTA takes its stop decision
     return ZT_OK;
 }
 
@@ -198,9 +193,7 @@ int enqueue_final(zt_batch* b, cudaStream_t s) {
     if ((rc = zt_update_grouped((const UpdateArgs*)b->upd_final.tab, b->upd_final.offs, b->upd_final.n,
                                 b->upd_final.total, s, ZT_GATE_FINAL)))
         return rc;
-    b->launches++;
-    if ((rc = zt_finalize_mark_grouped(b->dstates, b->n, s))) return rc;
-    b->launches++;
+    b->launches++;   // each instance's last CTA marks it finalised
     return ZT_OK;
 }
 
@@ -214,10 +207,8 @@ int enqueue_read_states(zt_batch* b, cudaStream_t s) {
 
 int enqueue_first_round(zt_batch* b, double tol, int maxit, int nsweeps, cudaStream_t s) {
     int rc;
-    copy_grouped<<<b->copy.total, 256, 0, s>>>((const CopyArgs*)b->copy.tab, b->copy.offs, b->copy.n);
+    copy_grouped<<<b->copy.total, 256, 0, s>>>((const CopyArgs*)b->copy.tab, b->copy.offs, b->copy.n, tol, maxit);
     if ((rc = count_launch(b, "copy_grouped"))) return rc;
-    state_init_grouped<<<(b->n + 127) / 128, 128, 0, s>>>(b->dstates, b->n, tol, maxit);
-    if ((rc = count_launch(b, "state_init_grouped"))) return rc;
     for (int c = 0; c < nsweeps; ++c)
         if ((rc = enqueue_sweep(b, s))) return rc;
     if ((rc = enqueue_final(b, s))) return rc;
@@ -318,18 +309,17 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
     Builder bl;
     std::vector<CopyArgs> cp;
     std::vector<SolveArgs> sv;
-    std::vector<SplitRowsArgs> sP, sW, sA;
+    std::vector<SplitRowsArgs> sP, sW, sA;   // Pt and Wt splits share one table (Pt entries first)
     std::vector<GemmEntry> g1, g2;
     std::vector<Fp64GemmArgs> fa, fb;
     std::vector<UpdateArgs> us, uf;
-    std::vector<ConvArgs> cv;
     std::vector<int> c_cp, c_sv, c_sP, c_g1, c_g2, c_fa, c_fb, c_up;
     int rc;
     for (int i = 0; i < count; ++i) {
         zt_plan* p = plans[i];
         const int N = p->N;
         const long long nn = (long long)N * N;
-        cp.push_back({b->W[i], p->Wn, p->Wt, nn});
+        cp.push_back({b->W[i], p->Wn, p->Wt, nn, p->state});
         c_cp.push_back((int)((nn + COPY_PER_CTA - 1) / COPY_PER_CTA));
         SolveArgs sa;
         zt_solve_args(p, p->Wt, p->P, &sa);
@@ -370,6 +360,8 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
         u.N = N;
         u.st = p->state;
         u.gate = ZT_GATE_NONE;
+        u.done = p->upd_done;
+        u.nctas = zt_update_ctas(N);
         u.base = p->Wn;   // sweep: Wt <- W_n + h/2 (A - A^H) + h^2/4 B
         u.old = p->Wt;
         u.out = p->Wt;
@@ -385,13 +377,15 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
         u.final_write = 1;
         uf.push_back(u);
         c_up.push_back(zt_update_ctas(N));
-        cv.push_back({p->partials, p->npartials, p->state});
     }
     bl.add(&b->copy, cp, c_cp);
     bl.add(&b->solve, sv, c_sv);
     if (!sP.empty()) {
-        bl.add(&b->split_P, sP, c_sP);
-        bl.add(&b->split_W, sW, c_sP);
+        std::vector<SplitRowsArgs> sPW(sP);
+        sPW.insert(sPW.end(), sW.begin(), sW.end());
+        std::vector<int> c_PW(c_sP);
+        c_PW.insert(c_PW.end(), c_sP.begin(), c_sP.end());
+        bl.add(&b->split_PW, sPW, c_PW);
         bl.add(&b->split_A, sA, c_sP);
         bl.add(&b->gemm1, g1, c_g1);
         bl.add(&b->gemm2, g2, c_g2);
@@ -402,8 +396,6 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
     }
     bl.add(&b->upd_sweep, us, c_up);
     bl.add(&b->upd_final, uf, c_up);
-    std::vector<int> ones(count, 1);
-    bl.add(&b->conv, cv, ones);
     if ((rc = bl.upload(b))) return fail(rc);
     std::vector<zt_dev_state*> sts(count);
     for (int i = 0; i < count; ++i) sts[i] = plans[i]->state;

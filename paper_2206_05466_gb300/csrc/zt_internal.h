@@ -88,26 +88,28 @@ struct zt_plan {
     double* partials = nullptr;
     double* cas_part = nullptr;   // Casimir partial sums [CTAs + 1][8]
     int npartials = 0;
-    // segmented stream solve: factors and their products within a segment,
-    // diagonal-major (diagonal m at dof[m], padded to 8 entries), constant
-    double* fac_l = nullptr;   // LDL^T multiplier l_i  (l_0 = 0)
-    double* fac_nd = nullptr;  // -1 / d_i              (0 for the dropped m=0 row)
-    double* fac_g = nullptr;   // G_i = prod_{j = segment start .. i} (-l_j)
-    double* fac_h = nullptr;   // H_i = prod_{j = i+1 .. segment end} (-l_j)
-    long long* dof = nullptr;  // [N + 1]
-    // per-(diagonal, segment) end/start values and inflows
-    int nseg = 0;
-    double2* seg_z = nullptr;
-    double* seg_g = nullptr;
-    double2* seg_x = nullptr;
-    double* seg_h = nullptr;
-    double2* carry_f = nullptr;
-    double2* carry_b = nullptr;
-    double2* sum_x = nullptr;
-    double* sum_h = nullptr;
-    double2* sol_mu = nullptr;   // mean of the m = 0 solution
+    // Stream solve by bands of 32 diagonals and segments of 32 rows (zt_solve.cu).
+    // Per element, packed lower-triangular row-major (entry (r, c) at zt_tri(r, c)):
+    double* fac_l = nullptr;   // LDL^T multiplier l_i (l_0 = 0)
+    double* fac_nd = nullptr;  // -1 / d_i (0 for the dropped m = 0 row)
+    double* fac_f = nullptr;   // F_i: the segment's response to its forward inflow
+    double* fac_h = nullptr;   // H_i: the segment's response to its backward inflow
+    // Per (segment k, diagonal m), [K][N] (coalesced over m):
+    int nseg = 0;              // K = ceil(N / 32)
+    double2* seg_z = nullptr;  // local forward sweep at the segment's last position
+    double2* seg_x = nullptr;  // local backward sweep at the segment's first position
+    double* seg_g = nullptr;   // G at the last position (constant)
+    double* seg_f = nullptr;   // F at the first position (constant)
+    double* seg_h = nullptr;   // H at the first position (constant)
+    double2* carry_f = nullptr;   // forward inflow of the segment
+    double2* carry_b = nullptr;   // backward inflow of the segment
+    double2* sum_x = nullptr;  // [K] m = 0: sum of the local backward sweep over the segment
+    double* sum_f = nullptr;   // [K] m = 0: sum of F over the segment (constant)
+    double* sum_h = nullptr;   // [K] m = 0: sum of H over the segment (constant)
+    double2* sol_mu = nullptr;   // m = 0: mean of the solution before its removal
     zt_dev_state* state = nullptr;
     zt_dev_state* h_state = nullptr;   // pinned host mirror
+    unsigned int* upd_done = nullptr;  // finished CTAs of the running update launch
     zt_split_ws* split = nullptr;
     long launches = 0;
     // Device memory of the plan comes from the stream-ordered allocator on a
@@ -139,20 +141,21 @@ int zt_timer_collect(zt_plan* p, int iters);
 struct SolveArgs {     // stream solve (zt_solve.cu)
     const double2* W;
     double2* P;
-    const double* fl;  // diagonal-major l, nd, G_i, H_i (constant)
+    const double* fl;      // packed lower-triangular l, nd, F, H (constant)
     const double* fnd;
-    const double* fg;
+    const double* ff;
     const double* fh;
-    const long long* dof;  // diagonal offsets
-    double2* seg_z;    // [N][K] end value of z0 in a segment
-    const double* seg_g;   // [N][K] product G over the segment (constant)
-    double2* seg_x;    // [N][K] start value of x0 in a segment
-    const double* seg_h;   // [N][K] H at the segment start (constant)
-    double2* cf;       // [N][K] forward inflow z_{kL-1} of a segment
-    double2* cb;       // [N][K] backward inflow x_{kL+L} of a segment
-    double2* sum_x;    // [K] m = 0 only: sum of x0 over the segment
-    const double* sum_h;   // [K] m = 0 only: sum of H over the segment (constant)
-    double2* mu;       // m = 0 only: mean of the solution
+    double2* seg_z;        // [K][N]
+    double2* seg_x;        // [K][N]
+    const double* seg_g;   // [K][N] (constant)
+    const double* seg_f;   // [K][N] (constant)
+    const double* seg_h;   // [K][N] (constant)
+    double2* cf;           // [K][N] forward inflow (z at the position before the segment)
+    double2* cb;           // [K][N] backward inflow (x at the position after the segment)
+    double2* sum_x;        // [K] m = 0 only
+    const double* sum_f;   // [K] m = 0 only (constant)
+    const double* sum_h;   // [K] m = 0 only (constant)
+    double2* mu;           // m = 0 only: mean of the solution
     int N, K;
     const zt_dev_state* st;
     int gate;
@@ -187,6 +190,15 @@ struct SplitArgs {     // tcgen05 split product (zt_split.cu)
     int ngroups;       // tiles of the launch
     unsigned long long wait_ns;  // limit of one bounded mbarrier wait
     int stall_loads;   // testing only: > 0 stops the TMA producer after stall_loads - 1 loads
+    // The occupancy arrays this product reads are accumulated with atomicMax by the
+    // splitter; the launch's last CTA to finish (counted in `done`, nctas CTAs)
+    // zeroes them for the next split.  NULL: nothing to clear.
+    int* clr_a;
+    int clr_a_n;
+    int* clr_b;
+    int clr_b_n;
+    unsigned int* done;
+    int nctas;
     unsigned int* tickets;   // persistent form: tile ticket counter, zero at launch
     double alpha;
     const int* eA;
@@ -223,12 +235,11 @@ struct UpdateArgs {    // fixed-point update / W_{n+1} assembly (zt_plan.cu)
     int N, final_write;
     zt_dev_state* st;
     int gate;
-};
-
-struct ConvArgs {      // residual reduction and stop decision (zt_plan.cu)
-    const double* partials;
-    int n;
-    zt_dev_state* st;
+    // The launch's last CTA to finish (counted in `done`, nctas CTAs) reduces the
+    // residual partials and takes the stop decision (sweeps), or marks the state
+    // finalised (the W_{n+1} assembly).
+    unsigned int* done;
+    int nctas;
 };
 
 // Plan set-up work goes to a private non-blocking stream of the greatest
@@ -282,7 +293,7 @@ int zt_solve_create(zt_plan* p);
 // uploaded to the plan in the solve's layout; waits for its own copies.
 int zt_solve_upload_factors(zt_plan* p, const double* host_l, const double* host_nd);
 size_t zt_solve_bytes(int N);   // device bytes of the solve workspace
-constexpr int ZT_SOLVE_LAUNCHES = 5;
+constexpr int ZT_SOLVE_LAUNCHES = 3;
 void zt_solve_destroy(zt_plan* p);
 // C = alpha * X conj(Y)^T, FP64 DFMA.  With lower_only, only tiles that
 // touch the lower triangle (i >= j) are computed.
@@ -303,8 +314,6 @@ int zt_fp64_gemm_args(zt_plan* p, const double2* X, const double2* Y, double2* C
 int zt_fp64_gemm_grouped(const Fp64GemmArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
 int zt_update_ctas(int N);
 int zt_update_grouped(const UpdateArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
-int zt_converge_grouped(const ConvArgs* tab, int n, cudaStream_t s);
-int zt_finalize_mark_grouped(zt_dev_state* const* sts, int n, cudaStream_t s);
 // Split-precision version (tcgen05).  Same contract.
 int zt_split_create(zt_plan* p);
 size_t zt_split_bytes(int N, const zt_tuning& t);   // device bytes of the split workspace
@@ -315,4 +324,6 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
 // the X' planes and/or one of two B'^T slots) and the tcgen05 product of the
 // X' planes with a B'^T slot.
 int zt_split_operand(zt_plan* p, const double2* X, int to_a, int b_slot, cudaStream_t s, int gate);
+// Two operands split in one launch: X1 into the X' planes and B'^T slot 1, X2 into slot 0.
+int zt_split_operands2(zt_plan* p, const double2* X1, const double2* X2, cudaStream_t s, int gate);
 int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, cudaStream_t s, int gate);

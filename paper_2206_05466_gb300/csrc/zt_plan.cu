@@ -320,6 +320,34 @@ namespace {
 constexpr int UT = 32;
 }
 
+// Fixed-order reduction of the residual partials and the stop decision.
+__device__ __forceinline__ void converge_body(const double* __restrict__ partials, int n, zt_dev_state* st) {
+    if (st->done) return;
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += 256) s += __ldcg(partials + k);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double r = sqrt(sh[0]);
+        st->iters += 1;
+        st->residual = r;
+        if (!isfinite(r)) {
+            st->nonfinite = 1;
+            st->done = 1;
+        } else if (r < st->tol) {
+            st->converged = 1;
+            st->done = 1;
+        } else if (st->iters >= st->maxit || st->timeout) {
+            st->done = 1;
+        }
+    }
+}
+
 __device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
     if (zt_gate_skip(ua.st, ua.gate)) return;
     const double2* __restrict__ base = ua.base;
@@ -381,25 +409,19 @@ __device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
         }
         if (threadIdx.x == 0) partials[t] = sred[0];
     }
-}
-
-// After the final assembly has completed (a separate launch: CTAs of the
-// assembly itself may still be waiting to start when its first CTA ends),
-// mark converged-and-assembled states so later rounds skip their final kernels.
-__global__ void finalize_mark_kernel(zt_dev_state* st) {
-    if (st->done) st->finalized = 1;
-}
-
-__global__ void finalize_mark_grouped(zt_dev_state* const* sts, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n && sts[i]->done) sts[i]->finalized = 1;
-}
-
-int zt_finalize_mark_grouped(zt_dev_state* const* sts, int n, cudaStream_t s) {
-    finalize_mark_grouped<<<(n + 127) / 128, 128, 0, s>>>(sts, n);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return zt_cuda_check(e, "finalize_mark_grouped");
-    return ZT_OK;
+    // the launch's last CTA: residual and stop decision (sweeps) or the finalised mark
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();   // this CTA's partial and stores, before it counts as finished
+        last = atomicAdd(ua.done, 1u) == (unsigned int)ua.nctas - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (partials) converge_body(partials, ua.nctas, ua.st);
+    else if (threadIdx.x == 0 && ua.st->done) ua.st->finalized = 1;   // W_{n+1} written by every CTA
+    if (threadIdx.x == 0) *ua.done = 0u;
 }
 
 __global__ void __launch_bounds__(256) update_kernel(const UpdateArgs a) { update_body(a, blockIdx.x); }
@@ -420,50 +442,6 @@ int zt_update_grouped(const UpdateArgs* tab, const int* offs, int n, int total, 
     update_grouped<<<total, 256, 0, s>>>(tab, offs, n, gate);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "update_grouped");
-    return ZT_OK;
-}
-
-// Fixed-order reduction of the residual partials and the stop decision.
-__device__ __forceinline__ void converge_body(const double* __restrict__ partials, int n, zt_dev_state* st) {
-    if (st->done) return;
-    __shared__ double sh[256];
-    double s = 0.0;
-    for (int k = threadIdx.x; k < n; k += 256) s += partials[k];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double r = sqrt(sh[0]);
-        st->iters += 1;
-        st->residual = r;
-        if (!isfinite(r)) {
-            st->nonfinite = 1;
-            st->done = 1;
-        } else if (r < st->tol) {
-            st->converged = 1;
-            st->done = 1;
-        } else if (st->iters >= st->maxit || st->timeout) {
-            st->done = 1;
-        }
-    }
-}
-
-__global__ void converge_kernel(const double* __restrict__ partials, int n, zt_dev_state* st) {
-    converge_body(partials, n, st);
-}
-
-__global__ void converge_grouped(const ConvArgs* tab) {
-    const ConvArgs a = tab[blockIdx.x];
-    converge_body(a.partials, a.n, a.st);
-}
-
-int zt_converge_grouped(const ConvArgs* tab, int n, cudaStream_t s) {
-    converge_grouped<<<n, 256, 0, s>>>(tab);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return zt_cuda_check(e, "converge_grouped");
     return ZT_OK;
 }
 
@@ -500,6 +478,8 @@ static int launch_update(zt_plan* p, const double2* base, const double2* old, do
     ua.final_write = resid ? 0 : 1;
     ua.st = p->state;
     ua.gate = gate;
+    ua.done = p->upd_done;   // the last CTA: residual and stop decision, or the finalised mark
+    ua.nctas = ntiles;
     const int t = zt_timer_begin(p, ZT_KERNEL_UPDATE, bytes, bytes, s);
     update_kernel<<<ntiles, 256, 0, s>>>(ua);
     zt_timer_end(p, t, s);
@@ -537,6 +517,7 @@ extern "C" void zt_plan_destroy(zt_plan* p) {
     zt_dfree(p->partials, ms);
     zt_dfree(p->cas_part, ms);
     zt_dfree(p->state, ms);
+    zt_dfree(p->upd_done, ms);
     zt_dfree(p->d_units, ms);
     zt_host_states_release(p->h_state, 1);   // no copy into it is in flight: steps end synchronised
     for (int i = 0; i < p->caprecs; ++i) {
@@ -636,6 +617,8 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     ZT_TRY(ZT_DMALLOC(p->partials, (size_t)p->npartials * sizeof(double), cs));
     ZT_TRY(ZT_DMALLOC(p->cas_part, ((size_t)CAS_CTAS + 1) * 8 * sizeof(double), cs));
     ZT_TRY(ZT_DMALLOC(p->state, sizeof(zt_dev_state), cs));
+    ZT_TRY(ZT_DMALLOC(p->upd_done, 16, cs));
+    ZT_TRY(cudaMemsetAsync(p->upd_done, 0, 16, cs));
     ZT_TRY(ZT_DMALLOC(p->d_units, sizeof(unsigned long long), cs));
     tr.mark("allocations");
     p->h_state = zt_host_states_acquire(1);
@@ -808,8 +791,8 @@ static int enqueue_products(zt_plan* p, cudaStream_t s, int gate) {
     int rc;
     if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, gate))) return rc;
     if (p->precision == ZT_PRECISION_SPLIT) {
-        if ((rc = zt_split_operand(p, p->P, 1, 1, s, gate))) return rc;    // Pt: X' planes and B'^T slot 1
-        if ((rc = zt_split_operand(p, p->Wt, 0, 0, s, gate))) return rc;   // Wt: B'^T slot 0
+        // Pt into the X' planes and B'^T slot 1, Wt into slot 0, in one launch
+        if ((rc = zt_split_operands2(p, p->P, p->Wt, s, gate))) return rc;
         if ((rc = zt_split_product(p, 0, p->A, -1.0, 0, s, gate))) return rc;   // A = Pt Wt
         if ((rc = zt_split_operand(p, p->A, 1, -1, s, gate))) return rc;   // A: X' planes
         return zt_split_product(p, 1, p->B, -1.0, 1, s, gate);                // B = A Pt
@@ -822,10 +805,10 @@ static int enqueue_sweep(zt_plan* p, int k, double h, cudaStream_t s) {
     int rc;
     p->cur_sweep = k;
     if ((rc = enqueue_products(p, s, ZT_GATE_SWEEP))) return rc;
-    if ((rc = launch_update(p, p->Wn, p->Wt, p->Wt, h, +1.0, true, s, ZT_GATE_SWEEP))) return rc;
-    converge_kernel<<<1, 256, 0, s>>>(p->partials, p->npartials, p->state);
+    // the update's last CTA reduces the residual and takes the stop decision
+    rc = launch_update(p, p->Wn, p->Wt, p->Wt, h, +1.0, true, s, ZT_GATE_SWEEP);
     p->cur_sweep = -1;
-    return launch_check(p, "converge_kernel");
+    return rc;
 }
 
 // Second line of Eq. 8; runs only once the sweeps are done.
@@ -833,11 +816,10 @@ static int enqueue_final(zt_plan* p, int tag, double2* W, double h, cudaStream_t
     int rc;
     p->cur_sweep = tag;
     if (p->tun.final_mode == ZT_FINAL_FRESH && (rc = enqueue_products(p, s, ZT_GATE_FINAL))) return rc;
+    // the assembly's last CTA marks the state finalised (W_{n+1} written by every CTA)
     rc = launch_update(p, p->Wt, nullptr, W, h, -1.0, false, s, ZT_GATE_FINAL);
     p->cur_sweep = -1;
-    if (rc) return rc;
-    finalize_mark_kernel<<<1, 1, 0, s>>>(p->state);
-    return launch_check(p, "finalize_mark_kernel");
+    return rc;
 }
 
 static int step_impl_(zt_plan* p, double2* W, double h, double tol, int maxit, zt_step_stats* stats,

@@ -94,7 +94,8 @@ struct zt_split_ws {
     int skip_zero = 1;                           // skip digit-pair units whose tiles are all zero
     int persistent = 1;                          // persistent product kernel
     int nsm = 0;                                 // SMs of the device
-    unsigned int* tickets = nullptr;             // tile ticket counter of the persistent kernel
+    unsigned int* tickets = nullptr;             // tile ticket counter of the persistent kernel,
+                                                 // then the count of finished CTAs (occupancy clear)
     int* occA = nullptr;                         // [ngA][nkb]
     int* occB[2] = {nullptr, nullptr};           // [ngB][nkb]
     CUtensorMap tmA, tmB[2];
@@ -391,17 +392,7 @@ __device__ __forceinline__ void split_rows_body(const SplitRowsArgs& ra, int j) 
 
 __global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsArgs a) { split_rows_body(a, blockIdx.x); }
 
-// Grouped: the occupancy arrays of every instance are cleared first (one CTA
-// per instance), then one CTA per row of every instance splits.
-__global__ void __launch_bounds__(256) occ_clear_grouped(const SplitRowsArgs* tab, int gate) {
-    const SplitRowsArgs a = tab[blockIdx.x];
-    if (zt_gate_skip(a.st, gate)) return;
-    if (a.occA)
-        for (int i = threadIdx.x; i < a.occA_n; i += 256) a.occA[i] = 0;
-    if (a.occB)
-        for (int i = threadIdx.x; i < a.occB_n; i += 256) a.occB[i] = 0;
-}
-
+// Grouped: one CTA per row of every instance.
 __global__ void __launch_bounds__(256) split_rows_grouped(const SplitRowsArgs* tab, const int* offs, int n, int gate) {
     const int inst = zt_group_find(offs, n, blockIdx.x);
     SplitRowsArgs a = tab[inst];
@@ -774,6 +765,26 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
     return true;
 }
 
+// The launch's last CTA to finish zeroes the occupancy arrays the product read
+// (every other CTA has finished reading them), for the splitter's next atomicMax
+// accumulation, and resets the counter for the next launch.  A clear that does
+// not happen (a launch cut short) leaves occupancy too high, never too low: more
+// units are multiplied, and the result is the same.
+__device__ __forceinline__ void clear_after_last(const SplitArgs& a) {
+    if (!a.done) return;
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(a.done, 1u) == (unsigned int)a.nctas - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    for (int i = threadIdx.x; i < a.clr_a_n; i += blockDim.x) a.clr_a[i] = 0;
+    for (int i = threadIdx.x; i < a.clr_b_n; i += blockDim.x) a.clr_b[i] = 0;
+    if (threadIdx.x == 0) *a.done = 0u;
+}
+
 // Teardown shared by both kernels.  By now the producer has settled its
 // loads, the MMA thread its MMAs and every drain thread its bulk copies, so
 // nothing is in flight: record an abort as a timeout, free TMEM and leave.
@@ -821,7 +832,10 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
     const SmemMap m = smem_map();
     TileSlot& ts = m.slots[0];
     int tig, tjg;
-    if (!tile_group(a, bid, tig, tjg)) return;
+    if (!tile_group(a, bid, tig, tjg)) {   // the whole CTA leaves; it still counts as finished
+        clear_after_last(a);
+        return;
+    }
     const int i0 = tig * BM, c0 = tjg * BN;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = a.ldk / BK;
@@ -859,6 +873,7 @@ __device__ __forceinline__ void zgemm_split_body(const CUtensorMap* tmA_p, const
         drain_tile(a, ts, m, tmem, i0, c0, warp, lane, seg);
     }
     split_teardown(a, m, tmem, warp);
+    clear_after_last(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -935,6 +950,7 @@ __device__ __forceinline__ void zgemm_split_persistent_body(const CUtensorMap* t
         }
     }
     split_teardown(a, m, tmem, warp);
+    clear_after_last(a);
 }
 
 __global__ void __launch_bounds__(NTHREADS, CTAS_PER_SM)
@@ -1082,7 +1098,7 @@ int zt_split_create(zt_plan* p) {
     }
     w->persistent = p->tun.no_persistent ? 0 : 1;
     ZT_CU(cudaDeviceGetAttribute(&w->nsm, cudaDevAttrMultiProcessorCount, p->device));
-    ZT_CU(ZT_DMALLOC(w->tickets, 16, cs));
+    ZT_CU(ZT_DMALLOC(w->tickets, 16, cs));   // [0] tile tickets, [1] finished CTAs
     ZT_CU(cudaMemsetAsync(w->tickets, 0, 16, cs));
     if (zt_attr_needed(ZT_ATTR_SPLIT)) {
         ZT_CU(cudaFuncSetAttribute(zgemm_split_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
@@ -1149,7 +1165,7 @@ int zt_split_rows_args(zt_plan* p, const double2* X, int to_a, int b_slot, Split
 }
 
 int zt_split_rows_grouped(const SplitRowsArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate) {
-    occ_clear_grouped<<<n, 256, 0, s>>>(tab, gate);
+    // occupancy arrays start at zero: the products that read them clear them
     split_rows_grouped<<<total, 256, 0, s>>>(tab, offs, n, gate);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "split_rows_grouped");
@@ -1166,15 +1182,39 @@ int zt_split_operand(zt_plan* p, const double2* X, int to_a, int b_slot, cudaStr
     ra.gate = gate;
     const double bytes = 16.0 * N * N + (to_a ? 2.0 * w->s * (double)N * w->ldk : 0.0) +
                          (b_slot >= 0 ? 4.0 * w->s * (double)N * w->ldk : 0.0);
-    // occupancy is reduced with atomicMax over the rows of each group: start from 0
-    if (to_a) ZT_CU(cudaMemsetAsync(w->occA, 0, (size_t)w->ngA * w->nkb * sizeof(int), s));
-    if (b_slot >= 0) ZT_CU(cudaMemsetAsync(w->occB[b_slot], 0, (size_t)w->ngB * w->nkb * sizeof(int), s));
+    // occupancy is reduced with atomicMax over the rows of each group; the arrays are
+    // zero here (plan creation, then cleared by the product that read them)
     const int t = zt_timer_begin(p, ZT_KERNEL_SPLIT, bytes, bytes, s);
     split_rows_kernel<<<N, 256, 0, s>>>(ra);
     zt_timer_end(p, t, s);
     p->launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return zt_cuda_check(e, "split_rows_kernel");
+    return ZT_OK;
+}
+
+__global__ void __launch_bounds__(256) split_rows2_kernel(const SplitRowsArgs a0, const SplitRowsArgs a1, int n0) {
+    if ((int)blockIdx.x < n0)
+        split_rows_body(a0, blockIdx.x);
+    else
+        split_rows_body(a1, blockIdx.x - n0);
+}
+
+int zt_split_operands2(zt_plan* p, const double2* X1, const double2* X2, cudaStream_t s, int gate) {
+    zt_split_ws* w = p->split;
+    if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
+    const int N = p->N;
+    SplitRowsArgs r1, r2;
+    int rc;
+    if ((rc = zt_split_rows_args(p, X1, 1, 1, &r1)) || (rc = zt_split_rows_args(p, X2, 0, 0, &r2))) return rc;
+    r1.gate = r2.gate = gate;
+    const double bytes = 2 * 16.0 * N * N + 2.0 * w->s * (double)N * w->ldk + 2 * 4.0 * w->s * (double)N * w->ldk;
+    const int t = zt_timer_begin(p, ZT_KERNEL_SPLIT, bytes, bytes, s);
+    split_rows2_kernel<<<2 * N, 256, 0, s>>>(r1, r2, N);
+    zt_timer_end(p, t, s);
+    p->launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return zt_cuda_check(e, "split_rows2_kernel");
     return ZT_OK;
 }
 
@@ -1208,6 +1248,18 @@ static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int l
     const int ngroups = lower_only ? w->n_lower : w->n_full;
     a.ngroups = ngroups;
     a.tickets = nullptr;
+    if (w->skip_zero) {   // the occupancy this product reads is cleared by its last CTA
+        a.clr_a = w->occA;
+        a.clr_a_n = w->ngA * w->nkb;
+        a.clr_b = w->occB[b_slot];
+        a.clr_b_n = w->ngB * w->nkb;
+        a.done = w->tickets + 1;
+    } else {
+        a.clr_a = a.clr_b = nullptr;
+        a.clr_a_n = a.clr_b_n = 0;
+        a.done = nullptr;
+    }
+    a.nctas = ngroups;   // one tile per CTA; the persistent launch sets its grid
     *ngroups_out = ngroups;
 }
 
@@ -1250,6 +1302,7 @@ int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower
         }
         a.tickets = w->tickets;
         const int grid = ngroups < w->nsm ? ngroups : w->nsm;
+        a.nctas = grid;
         if (grid > 0) zgemm_split_persistent<<<grid, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB[b_slot], a);
     } else {
         zgemm_split_kernel<<<ngroups, NTHREADS, SMEM_BYTES, s>>>(w->tmA, w->tmB[b_slot], a);
@@ -1395,6 +1448,10 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
     a.ntng = NA_NPAD / BN;
     a.wait_ns = 2000000000ull;
     a.stall_loads = 0;
+    a.clr_a = a.clr_b = nullptr;
+    a.clr_a_n = a.clr_b_n = 0;
+    a.done = nullptr;
+    a.nctas = 0;
     a.occA = nullptr;   // no zero-unit skipping: every digit pair is multiplied
     a.occB = nullptr;
     a.units = nullptr;
