@@ -6,7 +6,8 @@ first-served queue.  Before serving, each class's solo step time (a batched
 step of one and of two instances alone on the device) is calibrated.  The head
 of a class's queue is admitted when its plan's device footprint fits the memory
 budget and the admission policy (next_admission) allows it: at most two classes
-are resident at once (so each shares the device with at most one other), and a
+are resident at once (so each shares the device with at most one other), only
+classes whose solo step times are within a factor 8 share the device, and a
 resident class takes another job only after it completed a step with its
 current set, while its measured step time stays within twice its solo step time
 and its solo step time with one more job stays below an absolute target; after
@@ -69,7 +70,7 @@ def solo_step_s(solo, cls, n):
 
 
 def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate, factor=2.0,
-                   max_active=2, target=None, active_since=None, now=0.0, session_s=None):
+                   max_active=2, target=None, active_since=None, now=0.0, session_s=None, compat=None):
     """The class whose head job is admitted next, or None (the admission policy).
 
     queues: class -> deque of waiting jobs (FIFO per class); classes are tried in
@@ -90,6 +91,10 @@ def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate,
         seconds (active_since[cls]) admits no further job while a class that is not
         active has jobs waiting, so that the active classes drain and free their
         place (None: no limit).
+      * Compatibility: a class becomes active next to others only if its solo step
+        time with one job and theirs are within a factor `compat` of each other
+        (None: any), so that millisecond steps never share the device with
+        kernels whose CTAs hold an SM for longer than such a step.
     """
     active = {c for c, n in resident.items() if n > 0}
     anything = bool(active)
@@ -101,6 +106,9 @@ def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate,
         n = resident.get(cls, 0)
         if n == 0:
             if len(active) >= max_active:
+                continue
+            if compat is not None and any(max(solo[cls][0], solo[a][0]) > compat * min(solo[cls][0], solo[a][0])
+                                          for a in active):
                 continue
             return cls
         if factor is not None or target is not None:
@@ -120,12 +128,15 @@ def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate,
 class Server:
     def __init__(self, budget_bytes: int, tol: float = 1e-12, maxit: int = 50, graph: bool = False,
                  target_step_ms: float | None = 100.0, latency_factor: float = 2.0, max_active: int = 2,
-                 session_s: float | None = 20.0):
+                 session_s: float | None = 20.0, compat: float | None = 8.0, burst: int = 4):
         """target_step_ms: a class admits another job only while its solo step time with
         that job stays below this (None: no absolute bound); latency_factor: ... and
         while its measured step time is within this factor of its solo step time;
         max_active: classes resident at once; session_s: after this long, an active
-        class stops admitting while other classes wait (None: no limit)."""
+        class stops admitting while other classes wait (None: no limit); compat:
+        largest ratio of solo step times of two classes resident together (None:
+        any); burst: jobs a resident class may take after one completed step (one
+        batch rebuild for all of them)."""
         self.budget = int(budget_bytes)
         self.tol = tol
         self.maxit = maxit
@@ -134,6 +145,8 @@ class Server:
         self.factor = None if latency_factor is None else float(latency_factor)
         self.max_active = int(max_active)
         self.session_s = session_s
+        self.compat = compat
+        self.burst = max(1, int(burst))
 
     def calibrate(self, classes, W0s, h=0.01, reps=2):
         """Solo step time of each class (N, precision), alone on the device: batched steps
@@ -192,6 +205,7 @@ class Server:
         active_since: dict[tuple, float] = {}   # start of the class's current session (s)
         res_hist: dict[tuple, list] = collections.defaultdict(list)   # resident count at each step
         stepped: dict[tuple, bool] = {}         # a step completed since the class's last admission
+        took: dict[tuple, int] = collections.defaultdict(int)   # jobs admitted since the class's last step
         classes: dict[tuple, dict[int, _Resident]] = {}
         dirty: dict[tuple, bool] = {}
         workers: dict[tuple, threading.Thread] = {}
@@ -245,6 +259,7 @@ class Server:
                         dt = t_done - t_start
                         ema[cls] = dt if cls not in ema else 0.7 * ema[cls] + 0.3 * dt
                         stepped[cls] = True
+                        took[cls] = 0
                         res_hist[cls].append(len(order))
                         for j in order:
                             r = classes[cls][j]
@@ -291,10 +306,13 @@ class Server:
                     cls = next_admission(queues, {c: len(v) for c, v in classes.items()}, st["used"], self.budget,
                                          stepped, ema, solo, z.plan_estimate_bytes, factor=self.factor,
                                          max_active=self.max_active, target=self.target,
-                                         active_since=active_since, now=clock() - t0, session_s=self.session_s)
+                                         active_since=active_since, now=clock() - t0, session_s=self.session_s,
+                                         compat=self.compat)
                     if cls is not None:
                         job = queues[cls].popleft()
-                        stepped[cls] = False
+                        took[cls] += 1
+                        if took[cls] >= self.burst:   # the next job waits for a step with this set
+                            stepped[cls] = False
                         if not classes.get(cls):
                             active_since[cls] = clock() - t0
                             ema.pop(cls, None)   # a new session measures afresh
@@ -365,7 +383,7 @@ class Server:
             "calibration_s": calib_s,
             "policy": {"max_active_classes": self.max_active, "latency_factor": self.factor,
                        "target_step_ms": None if self.target is None else self.target * 1e3,
-                       "session_s": self.session_s},
+                       "session_s": self.session_s, "compat": self.compat, "burst": self.burst},
             "queue_delay_s_p50": float(np.percentile(qdelay, 50)) if qdelay else None,
             "peak_admitted_bytes": st["peak"],
             "admit_plan_ms_mean": float(np.mean([a for a, _ in admit_times]) * 1e3) if admit_times else None,

@@ -98,3 +98,14 @@ def test_no_latency_gate_admits_by_footprint_and_class_count():
     q = _q(J(40, 1, 0.0), J(40, 1, 0.0))
     assert pick(q, {c: 1}, factor=None, target=None) == c
     assert pick(q, {c: 1}, factor=None, target=None, stepped={c: False}) == c
+
+
+def test_compatibility_keeps_light_and_heavy_classes_apart():
+    solo = {(256, 1): (0.0015, 0.0), (2048, 0): (0.36, 0.3), (512, 1): (0.003, 0.0)}
+    q = _q(J(2048, 0, 0.0), J(512, 1, 1.0))
+    res = {(256, 1): 2}
+    got = next_admission(q, res, 0, 10**9, {}, {}, solo, est, compat=8.0)
+    assert got == (512, 1)            # the heavy head waits; the compatible class goes first
+    assert next_admission(_q(J(2048, 0, 0.0)), res, 0, 10**9, {}, {}, solo, est, compat=8.0) is None
+    assert next_admission(_q(J(2048, 0, 0.0)), res, 0, 10**9, {}, {}, solo, est, compat=None) == (2048, 0)
+    assert next_admission(_q(J(2048, 0, 0.0)), {}, 0, 10**9, {}, {}, solo, est, compat=8.0) == (2048, 0)
