@@ -424,6 +424,9 @@ struct TileSlot {
     int gunits[MAX_S];
     uint8_t fa[MAX_KB];   // the unit (p, q, kb) is all zero unless p >= fa[kb] and q >= fb[kb]
     uint8_t fb[MAX_KB];
+    // bit kb of amask[g] is set when K block kb has a unit in digit group g
+    // (fa[kb] + fb[kb] <= g), so the producer visits only those blocks
+    uint32_t amask[MAX_S][MAX_KB / 32];
 };
 constexpr int TSLOTS = 2;   // tile slots of the persistent kernel (one being worked, one being filled)
 // Drain staging: per drain thread two 128-byte slots (16 int64) for the bulk
@@ -489,14 +492,22 @@ __device__ __forceinline__ void fill_slot_warp(const SplitArgs& a, TileSlot& ts,
     int u[MAX_S];
 #pragma unroll
     for (int g = 0; g < MAX_S; ++g) u[g] = 0;
-    for (int kb = lane; kb < nkb; kb += 32) {
-        const int fa = a.occA ? a.s - a.occA[(size_t)tig * nkb + kb] : 0;
-        const int fb = a.occB ? a.s - a.occB[(size_t)tjg * nkb + kb] : 0;
-        ts.fa[kb] = (uint8_t)fa;
-        ts.fb[kb] = (uint8_t)fb;
-        const int c = fa + fb;
+    for (int kb0 = 0; kb0 < nkb; kb0 += 32) {   // nkb is a multiple of 32 or below it: whole warp iterates
+        const int kb = kb0 + lane;
+        int c = 2 * MAX_S;   // no unit
+        if (kb < nkb) {
+            const int fa = a.occA ? a.s - a.occA[(size_t)tig * nkb + kb] : 0;
+            const int fb = a.occB ? a.s - a.occB[(size_t)tjg * nkb + kb] : 0;
+            ts.fa[kb] = (uint8_t)fa;
+            ts.fb[kb] = (uint8_t)fb;
+            c = fa + fb;
+        }
 #pragma unroll
-        for (int g = 0; g < MAX_S; ++g) u[g] += max(0, g - c + 1);
+        for (int g = 0; g < MAX_S; ++g) {
+            u[g] += max(0, g - c + 1);
+            const uint32_t bits = __ballot_sync(0xffffffffu, c <= g);
+            if (lane == 0) ts.amask[g][kb0 >> 5] = bits;
+        }
     }
     int total = 0;
 #pragma unroll
@@ -524,9 +535,13 @@ __device__ __forceinline__ void fill_slot_warp(const SplitArgs& a, TileSlot& ts,
 __device__ __forceinline__ bool produce_tile(const SplitArgs& a, const TileSlot& ts, const SmemMap& m,
                                              const CUtensorMap* tmA_p, const CUtensorMap* tmB_p, int i0, int c0,
                                              int nkb, int& stage, uint32_t& ph, long long& nload) {
+    const int nw = (nkb + 31) >> 5;
     for (int g = 0; g < a.s; ++g)
-        for (int kb = 0; kb < nkb; ++kb)
-            for (int p = ts.fa[kb]; p <= g - ts.fb[kb]; ++p) {
+        for (int wi = 0; wi < nw; ++wi)
+            for (uint32_t bits = ts.amask[g][wi]; bits; bits &= bits - 1) {
+              const int kb = (wi << 5) + __ffs(bits) - 1;
+              const int p1 = g - ts.fb[kb];
+              for (int p = ts.fa[kb]; p <= p1; ++p) {
                 // testing only: stop issuing so that the consumers' bounded waits run out
                 if (a.stall_loads > 0 && nload >= a.stall_loads - 1) return false;
                 if (!mbar_wait(&m.empty[stage], ph ^ 1, m.abort_flag, a.wait_ns)) return false;
@@ -538,6 +553,7 @@ __device__ __forceinline__ bool produce_tile(const SplitArgs& a, const TileSlot&
                     stage = 0;
                     ph ^= 1;
                 }
+              }
             }
     return true;
 }
@@ -555,13 +571,17 @@ __device__ __forceinline__ void producer_settle(const SmemMap& m, long long nloa
 // stage/ph/seg continue from tile to tile; seg numbers the accumulator buffers.
 __device__ __forceinline__ bool mma_tile(const SplitArgs& a, const TileSlot& ts, const SmemMap& m, uint32_t tmem,
                                          int nkb, int& stage, uint32_t& ph, int& seg, unsigned long long& issued) {
+    (void)nkb;
+    // The units of a digit group arrive in the producer's order; the MMA thread
+    // needs only how many there are (the stage ring says where each one is).
     for (int g = 0; g < a.s; ++g) {
         const int ulim = seg_units(g, a.beta, a.exact_groups);
+        const int nunits = ts.gunits[g];
         int cnt = 0, b = 0;
         bool open = false;
         uint32_t d = 0;
-        for (int kb = 0; kb < nkb; ++kb) {
-            for (int p = ts.fa[kb]; p <= g - ts.fb[kb]; ++p) {
+        {
+            for (int un = 0; un < nunits; ++un) {
                 if (!open) {   // next accumulation segment: wait for its TMEM buffer to be drained
                     b = seg % NBUF;
                     const int use = seg / NBUF;
