@@ -210,7 +210,7 @@ def _tuning(args, N):
                                      "fastest": [{**t["tuning"], "ms": round(t["ms"], 3),
                                                   "rel_err": t["rel_err"]} for t in timed[:6]]}
     tun = dict(slices=args.slices, digit_bits=args.digit_bits, exact_groups=args.exact_groups,
-               tile_order=args.tile_order)
+               tile_order=args.tile_order, no_persistent=args.no_persistent)
     return tun, {"mode": "fixed"}
 
 
@@ -708,10 +708,11 @@ def main():
                     help="step latency above which a serving class admits no further job")
     ap.add_argument("--tuning", default="auto", choices=["auto", "fixed"])
     ap.add_argument("--tune-target", type=float, default=1e-11)
-    ap.add_argument("--slices", type=int, default=7)
-    ap.add_argument("--digit-bits", type=int, default=7)
-    ap.add_argument("--exact-groups", type=int, default=4)
+    ap.add_argument("--slices", type=int, default=6)
+    ap.add_argument("--digit-bits", type=int, default=8)
+    ap.add_argument("--exact-groups", type=int, default=2)
     ap.add_argument("--tile-order", type=int, default=0)
+    ap.add_argument("--no-persistent", type=int, default=0, help="fixed tuning: 1 = one tile per CTA")
     ap.add_argument("--fp64", action="store_true", help="profile mode: the FP64 form")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--oracle-steps", type=int, default=2)

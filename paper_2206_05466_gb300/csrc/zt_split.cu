@@ -59,7 +59,7 @@ namespace {
 constexpr int BM = 128;            // tile rows (X' rows)
 constexpr int BN = 256;            // tile cols (B'^T rows = real output columns)
 constexpr int BK = 64;             // K per stage: 64 BF16 = 128 bytes per row
-constexpr int STAGES = 3;
+constexpr int STAGES = 4;
 constexpr int A_TILE = BM * BK * 2;
 constexpr int B_TILE = BN * BK * 2;
 constexpr int STAGE_BYTES = A_TILE + B_TILE;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void bulk_reduce_add_s64(long long* gdst, uint32_t ss
                  : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_shared() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -429,10 +429,11 @@ struct TileSlot {
     uint32_t amask[MAX_S][MAX_KB / 32];
 };
 constexpr int TSLOTS = 2;   // tile slots of the persistent kernel (one being worked, one being filled)
-// Drain staging: per drain thread two 128-byte slots (16 int64) for the bulk
-// reduce-adds of intermediate segments; a 272-byte stride keeps the 16-byte
-// shared stores of a quarter-warp on distinct banks.
-constexpr int STG_STRIDE = 272;
+// Drain staging: per drain thread one 64-byte slot (8 int64) for the bulk
+// reduce-adds of intermediate segments (a 16-column chunk goes out in two
+// halves); an 80-byte stride keeps the 16-byte shared stores of a quarter-warp
+// on distinct banks.  Small, so that the operand ring has four stages.
+constexpr int STG_STRIDE = 80;
 constexpr size_t SMEM_BYTES = 1024 /*align slack*/ + (size_t)STAGES * STAGE_BYTES + 256 /*barriers*/ +
                               TSLOTS * sizeof(TileSlot) + (size_t)NDRAIN * STG_STRIDE;
 
@@ -649,7 +650,7 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
     const bool apow2 = (abits & 0xFFFFFFFFFFFFFLL) == 0 && aef != 0 && aef != 0x7FF;
     const int aexp = apow2 ? aef - 1023 : 0;
     const unsigned long long asign = apow2 ? ((unsigned long long)abits & 0x8000000000000000ull) : 0ull;
-    // staging slots of this thread for the bulk reduce-adds of intermediate segments
+    // staging slot of this thread for the bulk reduce-adds of intermediate segments
     uint8_t* stg = m.stg + (size_t)(threadIdx.x - 64) * STG_STRIDE;
     int nstg = 0;   // bulk operations issued by this thread in this tile
     int tseg = 0;   // segments of this tile drained so far
@@ -699,14 +700,19 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
                 }
                 long long* dst = Crow + cb;
                 if (!first && !last) {   // intermediate segment: reduce-add through L2, asynchronously
-                    uint8_t* slot = stg + (nstg & 1) * 128;
-                    if (nstg >= 2) bulk_wait_read_1();   // the slot's previous copy has been read
 #pragma unroll
-                    for (int t = 0; t < 16; t += 2)
-                        if (t < lim) *reinterpret_cast<longlong2*>(slot + t * 8) = make_longlong2(v[t], v[t + 1]);
-                    fence_proxy_async_shared();
-                    bulk_reduce_add_s64(dst, smem_u32(slot), lim * 8);
-                    ++nstg;
+                    for (int h = 0; h < 2; ++h) {   // two halves of 8 values through the one slot
+                        const int n = min(8, lim - 8 * h);
+                        if (n <= 0) break;
+                        if (nstg >= 1) bulk_wait_read_0();   // the slot's previous copy has been read
+#pragma unroll
+                        for (int t = 0; t < 8; t += 2)
+                            if (t < n)
+                                *reinterpret_cast<longlong2*>(stg + t * 8) = make_longlong2(v[8 * h + t], v[8 * h + t + 1]);
+                        fence_proxy_async_shared();
+                        bulk_reduce_add_s64(dst + 8 * h, smem_u32(stg), n * 8);
+                        ++nstg;
+                    }
                     continue;
                 }
                 if (!first) {   // add the accumulator (all loads first)
