@@ -539,9 +539,11 @@ def run_gpu(args):
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    step_iters = []
+    step_iters, host_ms = [], []
     for _ in range(args.steps):
+        th = time.perf_counter()
         step_iters.append(z.isomp_step(plan, Wd, H, TOL, MAXIT)["iters"])
+        host_ms.append(1e3 * (time.perf_counter() - th))
     ev1.record(stream)
     torch.cuda.synchronize()
     _barrier(ws)
@@ -657,6 +659,8 @@ def run_gpu(args):
                    "parallelism": f"replicas x{ws}",
                    "l2": "working set > L2 (digit planes ~1.4 GB + 6 matrices of 268 MB)"},
         "sweeps_per_step": statistics.mean(step_iters) if step_iters else None,
+        "step_host_ms": {"min": min(host_ms), "median": statistics.median(host_ms), "max": max(host_ms)}
+        if host_ms else None,
         "gpu_launches": gpu_launches,
         "e2e": e2e,
         "fp64_form": fp64,

@@ -54,7 +54,8 @@ typedef struct zt_tuning {
     int digit_bits;      /* SPLIT: bits per balanced digit, 6..8 (default 7)         */
     int exact_groups;    /* SPLIT: leading digit groups summed exactly (default 4)   */
     int final_mode;      /* ZT_FINAL_FRESH (default) or ZT_FINAL_REUSE               */
-    int sweeps_per_sync; /* sweeps enqueued between host convergence checks (def. 4) */
+    int sweeps_per_sync; /* sweeps enqueued between host convergence checks, 1..64; 0 (default):
+                            as many as the previous step took (4 for a plan's first step) */
     int dense;           /* SPLIT: 1 = multiply every digit pair; 0 (default) = skip digit-pair
                             tiles that are exactly zero (identical results)                  */
     int tile_order;      /* SPLIT launch order of output tiles: 0 (default) / 3 / 4 / 5 = column
@@ -85,6 +86,9 @@ typedef struct zt_run_stats {
 } zt_run_stats;
 
 /* Create a plan for size N (1 <= N <= 16384) and precision ZT_PRECISION_*.
+ * Plans allocate from the device's default stream-ordered memory pool; the
+ * first plan on a device raises that pool's release threshold, so memory of
+ * destroyed plans stays pooled for reuse (cudaMemPoolTrimTo returns it).
  * Precomputes, once, the tridiagonal blocks of Delta_N (Sec. 3.2, Eq.
  * 13) and their LDL^T factors (the factorisation behind the HPD
  * tridiagonal solve of Sec. 3.3), and allocates the step workspace (about

@@ -82,7 +82,9 @@ struct zt_batch {
     zt_dev_state* gathered = nullptr;
     zt_dev_state* hstates = nullptr;   // pinned host copy of the states (also the captured memcpy target)
     Op copy, solve, split_PW, split_A, gemm1, gemm2, f64a, f64b, upd_sweep, upd_final;
-    int sweeps_per_sync = 4;
+    int sweeps_per_sync = 0;    // fixed chunk of sweeps per host check; 0: adaptive
+    int last_max = 0;           // largest sweep count of an instance in the previous step
+    int g_spc = 0;              // chunk the graphs were captured for
     long launches = 0;
     int use_graph = 0;
     cudaGraphExec_t g_first = nullptr, g_more = nullptr;
@@ -301,7 +303,9 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
         if (i == 0) b->final_mode = p->tun.final_mode;
         if (p->tun.final_mode != b->final_mode)
             return fail(zt_fail(ZT_EINVAL, "zt_batch_create: instances must share the final mode"));
-        if (p->tun.sweeps_per_sync < b->sweeps_per_sync || i == 0) b->sweeps_per_sync = p->tun.sweeps_per_sync;
+        // a fixed chunk if any instance asks for one (the smallest), else adaptive
+        if (p->tun.sweeps_per_sync > 0 && (b->sweeps_per_sync == 0 || p->tun.sweeps_per_sync < b->sweeps_per_sync))
+            b->sweeps_per_sync = p->tun.sweeps_per_sync;
         b->plans.push_back(p);
         b->W.push_back(reinterpret_cast<double2*>(W[i]));
         b->h.push_back(h[i]);
@@ -430,18 +434,21 @@ extern "C" long zt_batch_launch_count(const zt_batch* b) { return b ? b->launche
 
 static int batch_step_impl(zt_batch* b, double tol, int maxit, zt_step_stats* stats, cudaStream_t s) {
     int rc;
-    const int spc = b->sweeps_per_sync;
+    // sweeps per host check: fixed, or as many as the slowest instance took in the previous step
+    const int spc = b->sweeps_per_sync ? b->sweeps_per_sync : (b->last_max > 0 ? b->last_max : 4);
     if (b->use_graph) {   // work goes to the batch's own stream, after what the caller queued on s
         ZT_CU(cudaEventRecord(b->ev_in, s));
         ZT_CU(cudaStreamWaitEvent(b->own, b->ev_in, 0));
         s = b->own;
-        if (b->g_tol_maxit_set && (b->g_tol != tol || b->g_maxit != maxit || b->g_stream != s)) drop_graphs(b);
+        if (b->g_tol_maxit_set && (b->g_tol != tol || b->g_maxit != maxit || b->g_stream != s || b->g_spc != spc))
+            drop_graphs(b);
         if (!b->g_first) {
             if ((rc = capture(b, s, &b->g_first, true, tol, maxit, spc))) return rc;
             if ((rc = capture(b, s, &b->g_more, false, tol, maxit, spc))) return rc;
             b->g_tol = tol;
             b->g_maxit = maxit;
             b->g_stream = s;
+            b->g_spc = spc;
             b->g_tol_maxit_set = 1;
         }
     }
@@ -463,9 +470,10 @@ static int batch_step_impl(zt_batch* b, double tol, int maxit, zt_step_stats* st
         if (all) break;
         if (enq >= maxit) return zt_fail(ZT_ECUDA, "isomp_step_batched: states not done after maxit sweeps");
     }
-    int worst = ZT_OK;
+    int worst = ZT_OK, most = 0;
     for (int i = 0; i < b->n; ++i) {
         const zt_dev_state& hs = b->hstates[i];
+        if (hs.iters > most && !hs.timeout && !hs.nonfinite) most = hs.iters;
         if (stats) {
             stats[i].iters = hs.iters;
             stats[i].converged = hs.converged;
@@ -475,6 +483,7 @@ static int batch_step_impl(zt_batch* b, double tol, int maxit, zt_step_stats* st
         else if (hs.nonfinite && worst != ZT_ETIMEOUT) worst = ZT_ENONFINITE;
         else if (!hs.converged && worst == ZT_OK) worst = ZT_NOT_CONVERGED;
     }
+    if (most > 0) b->last_max = most;
     if (worst == ZT_ETIMEOUT) return zt_fail(worst, "isomp_step_batched: a bounded device wait ran out");
     if (worst == ZT_ENONFINITE) return zt_fail(worst, "isomp_step_batched: a residual is not finite");
     if (worst == ZT_NOT_CONVERGED) return zt_fail(worst, "isomp_step_batched: some instances did not converge");

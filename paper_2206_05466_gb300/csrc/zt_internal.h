@@ -112,6 +112,7 @@ struct zt_plan {
     unsigned int* upd_done = nullptr;  // finished CTAs of the running update launch
     zt_split_ws* split = nullptr;
     long launches = 0;
+    int last_iters = 0;   // sweeps of the previous step (adaptive sweeps_per_sync)
     // Device memory of the plan comes from the stream-ordered allocator on a
     // private stream: creating or freeing a plan never synchronises the
     // device (other threads may keep long-running work on it).  Frees are
@@ -263,7 +264,7 @@ inline cudaError_t zt_setup_stream(cudaStream_t* s) {
 // Kernel attributes (dynamic shared-memory limits) are set once per device
 // and process: setting them again while other threads run the kernels is
 // unnecessary and can stall.  `bit` names the kernel family.
-enum zt_attr_bit : unsigned { ZT_ATTR_SOLVE = 1u, ZT_ATTR_SPLIT = 2u };
+enum zt_attr_bit : unsigned { ZT_ATTR_SOLVE = 1u, ZT_ATTR_SPLIT = 2u, ZT_ATTR_POOL = 4u };
 bool zt_attr_needed(unsigned bit);   // true once per (device, bit); marks it set
 
 // Stream-ordered device allocation on the plan's private stream.

@@ -534,7 +534,6 @@ static void fill_tuning_defaults(zt_tuning& t) {
     if (t.slices == 0) t.slices = 7;
     if (t.digit_bits == 0) t.digit_bits = 7;
     if (t.exact_groups == 0) t.exact_groups = 4;
-    if (t.sweeps_per_sync == 0) t.sweeps_per_sync = 4;
     if (t.wait_us == 0) t.wait_us = 2000000;
 }
 
@@ -567,9 +566,9 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         delete p;
         return zt_fail(ZT_EINVAL, "zt_plan_create: bad final_mode %d", opt->final_mode);
     }
-    if (p->tun.sweeps_per_sync < 1 || p->tun.sweeps_per_sync > 64) {
+    if (p->tun.sweeps_per_sync < 0 || p->tun.sweeps_per_sync > 64) {
         delete p;
-        return zt_fail(ZT_EINVAL, "zt_plan_create: sweeps_per_sync outside [1, 64]");
+        return zt_fail(ZT_EINVAL, "zt_plan_create: sweeps_per_sync outside [0, 64]");
     }
     if (precision == ZT_PRECISION_SPLIT) {   // checked before any device work
         const zt_tuning& t = p->tun;
@@ -599,6 +598,18 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     } while (0)
     ZtTrace tr("zt_plan_create");
     ZT_TRY(cudaGetDevice(&p->device));
+    if (zt_attr_needed(ZT_ATTR_POOL)) {
+        // Plans allocate from the device's stream-ordered pool.  With the default
+        // release threshold (0) memory freed by a destroyed plan is handed back to
+        // the system at later synchronisations, which can stall unrelated steps;
+        // keeping it in the pool makes the next plan's allocation a reuse.
+        cudaMemPool_t pool = nullptr;
+        if (cudaDeviceGetDefaultMemPool(&pool, p->device) == cudaSuccess) {
+            cuuint64_t keep = ~(cuuint64_t)0;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     ZT_TRY(zt_setup_stream(&p->mstream));
     tr.mark("stream");
     ZT_TRY(cudaEventCreateWithFlags(&p->last_use, cudaEventDisableTiming));
@@ -839,8 +850,10 @@ static int step_impl_(zt_plan* p, double2* W, double h, double tol, int maxit, z
     int rc = launch_check(p, "state_init_kernel");
     if (rc) return rc;
     int enq = 0, round = 0;
+    // sweeps per host check: fixed, or as many as the previous step took (the
+    // device gates sweeps past convergence, so a larger chunk only costs launches)
+    const int chunk = p->tun.sweeps_per_sync ? p->tun.sweeps_per_sync : (p->last_iters > 0 ? p->last_iters : 4);
     for (;; ++round) {
-        const int chunk = p->tun.sweeps_per_sync;
         for (int c = 0; c < chunk && enq < maxit; ++c, ++enq)
             if ((rc = enqueue_sweep(p, enq, h, s))) return rc;
         if ((rc = enqueue_final(p, ZT_SWEEP_FINAL + round, W, h, s))) return rc;
@@ -850,6 +863,7 @@ static int step_impl_(zt_plan* p, double2* W, double h, double tol, int maxit, z
         if (enq >= maxit) return zt_fail(ZT_ECUDA, "isomp_step: state not done after maxit sweeps");
     }
     const zt_dev_state& hs = *p->h_state;
+    if (hs.iters > 0 && !hs.timeout && !hs.nonfinite) p->last_iters = hs.iters;
     if (p->timing && (rc = timer_collect(p, hs.iters, ZT_SWEEP_FINAL + round))) return rc;
     if (stats) {
         stats->iters = hs.iters;

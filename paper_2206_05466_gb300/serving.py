@@ -5,9 +5,11 @@ of like N and precision form a class; each class has its own first-come,
 first-served queue.  Before serving, each class's solo step time (a batched
 step of one and of two instances alone on the device) is calibrated.  The head
 of a class's queue is admitted when its plan's device footprint fits the memory
-budget and the admission policy (next_admission) allows it: at most two classes
-are resident at once (so each shares the device with at most one other), only
-classes whose solo step times are within a factor 8 share the device, and a
+budget and the admission policy (next_admission) allows it: by default one
+class is resident at a time (measured: two classes sharing the device, even of
+comparable step time, put the lighter one's p99 step latency at 5-8 times its
+solo step time; a setting allows more, and then only classes whose solo step
+times are within a factor 8 share the device), and a
 resident class takes another job only after it completed a step with its
 current set, while its measured step time stays within twice its solo step time
 and its solo step time with one more job stays below an absolute target; after
@@ -17,7 +19,7 @@ the resident classes rotate.  Under overload the queues absorb the excess
 device until its last step.  Each class is advanced by its own worker thread on
 its own CUDA stream, one batched step (grouped kernels over all the class's
 jobs) per iteration; jobs admitted while others run join their class's batch
-at its next step, and the two resident classes run concurrently on the device.
+at its next step (when several classes are allowed, they run concurrently).
 A class's batch is rebuilt only when its resident set changes.  All arithmetic
 runs in the library's kernels; this module only schedules.
 
@@ -127,7 +129,7 @@ def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate,
 
 class Server:
     def __init__(self, budget_bytes: int, tol: float = 1e-12, maxit: int = 50, graph: bool = False,
-                 target_step_ms: float | None = 100.0, latency_factor: float = 2.0, max_active: int = 2,
+                 target_step_ms: float | None = 100.0, latency_factor: float = 2.0, max_active: int = 1,
                  session_s: float | None = 20.0, compat: float | None = 8.0, burst: int = 4):
         """target_step_ms: a class admits another job only while its solo step time with
         that job stays below this (None: no absolute bound); latency_factor: ... and
