@@ -58,6 +58,7 @@ class _Resident:
     bytes: int
     remaining: int
     last_done: float
+    done: bool = False      # all steps taken; stepped along (results ignored) until the next rebuild
 
 
 def _pct(xs, q):
@@ -222,6 +223,7 @@ class Server:
             torch.cuda.set_device(dev)
             stream = torch.cuda.Stream(priority=class_priority(cls[0]))
             batch, order = None, []
+            since = 0   # batched steps since the last rebuild
             try:
                 while True:
                     with lock:
@@ -243,6 +245,26 @@ class Server:
                                     return
                         time.sleep(0.001)
                         continue
+                    # Finished jobs leave the batch at the next rebuild: at once if nothing
+                    # else is left, otherwise together with the next admission, once a
+                    # quarter of the batch has finished, or after 32 steps (one rebuild
+                    # for several changes keeps rebuild pauses out of most steps).
+                    zombies = [r for r in res.values() if r.done]
+                    live = {j: r for j, r in res.items() if not r.done}
+                    if zombies and (changed or not live or len(zombies) * 4 >= len(res) or since >= 32):
+                        if batch is not None:
+                            batch.close()
+                            batch = None
+                        for r in zombies:
+                            r.plan.close()
+                        with lock:
+                            for r in zombies:
+                                del classes[cls][r.job.jid]
+                                st["used"] -= r.bytes
+                        res = live
+                        changed = True
+                        if not res:
+                            continue
                     if changed or batch is None:
                         if batch is not None:
                             batch.close()
@@ -251,10 +273,12 @@ class Server:
                                         [res[j].job.h for j in order])
                         if self.graph:
                             batch.set_graph(True)
+                        since = 0
                     t_start = clock() - t0
                     with torch.cuda.stream(stream):
                         batch.step(self.tol, self.maxit, stream=stream, allow_not_converged=True)
                     t_done = clock() - t0
+                    since += 1
                     finished = []
                     with lock:
                         st["batched"] += 1
@@ -265,25 +289,19 @@ class Server:
                         res_hist[cls].append(len(order))
                         for j in order:
                             r = classes[cls][j]
+                            if r.done:
+                                continue
                             lat[cls].append(t_done - r.last_done)
                             r.last_done = t_done
                             r.remaining -= 1
                             st["steps"] += 1
                             if r.remaining == 0:
+                                r.done = True
                                 finished.append(r)
-                    if finished:
-                        batch.close()
-                        batch = None
-                        for r in finished:
-                            if keep_results:
-                                results[r.job.jid] = r.W.cpu().numpy()
-                            r.plan.close()
-                        with lock:
-                            for r in finished:
-                                del classes[cls][r.job.jid]
-                                st["used"] -= r.bytes
                                 st["completed"] += 1
-                            dirty[cls] = True
+                    for r in finished:   # the state after the job's last step (the step has synchronised)
+                        if keep_results:
+                            results[r.job.jid] = r.W.cpu().numpy()
             except Exception as e:   # surfaced to the caller after the run
                 errors.append(repr(e))
                 with lock:
