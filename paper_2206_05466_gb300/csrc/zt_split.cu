@@ -538,12 +538,11 @@ __device__ __forceinline__ void fill_slot_warp(const SplitArgs& a, TileSlot& ts,
 // stage j, so group s-2 needs no operand loads of its own.  Each accumulator
 // still receives its units in the same order (K blocks ascending, p ascending):
 // the result is bitwise the same as sweeping the groups one after the other.
-// Only on heavy tiles (on average a unit of group s-2 per K block): on light
-// tiles the saved loads are worth less than overlapping group s-2's drain with
-// group s-1's products (measured: 7.05 -> 7.66 ms per N = 4096 step with every
-// tile swept this way).
+// The two accumulators are then drained together, summed in registers: one
+// drain pass for both groups, and no trip through the int64 accumulator in
+// global memory when they are the tile's only groups.
 __device__ __forceinline__ bool dual_tile(const SplitArgs& a, const TileSlot& ts) {
-    return a.s >= 3 && a.exact_groups <= a.s - 2 && ts.gunits[a.s - 2] >= a.ldk / BK;
+    return a.s >= 3 && a.exact_groups <= a.s - 2 && ts.gunits[a.s - 2] > 0;
 }
 
 // ---- TMA producer (one thread): digit tiles of every active unit of the tile ----
@@ -721,11 +720,15 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
     uint8_t* stg = m.stg + (size_t)(threadIdx.x - 64) * STG_STRIDE;
     int nstg = 0;   // bulk operations issued by this thread in this tile
     int tseg = 0;   // segments of this tile drained so far
+    const bool dual = dual_tile(a, ts);
+    const int tot = dual ? total - 1 : total;   // the last two groups drain as one segment
     for (int g = 0; g < a.s; ++g) {
+        const bool pair = dual && g == a.s - 2;   // groups s-2 and s-1, buffers b and b2
         const int ulim = seg_units(g, a.beta, a.exact_groups);
         const int units = ts.gunits[g];
-        const int nsegs = units == 0 ? 0 : (units - 1) / ulim + 1;
+        const int nsegs = pair ? 1 : (units == 0 ? 0 : (units - 1) / ulim + 1);
         const int sh = (a.s - 1 - g) * a.beta - a.u;
+        const int sh2 = -a.u;   // weight of group s-1
         for (int q = 0; q < nsegs; ++q) {
             const int b = seg % NBUF, use = seg / NBUF;
             ++seg;
@@ -733,8 +736,18 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
                 if (nstg) bulk_wait_all();
                 return false;
             }
+            int b2 = 0;
+            if (pair) {
+                b2 = seg % NBUF;
+                const int use2 = seg / NBUF;
+                ++seg;
+                if (!mbar_wait(&m.accf[b2], use2 & 1, m.abort_flag, a.wait_ns)) {
+                    if (nstg) bulk_wait_all();
+                    return false;
+                }
+            }
             tc_fence_after();
-            const bool first = tseg == 0, last = tseg == total - 1;
+            const bool first = tseg == 0, last = tseg == tot - 1;
             ++tseg;
             if (last && nstg) {   // every reduce-add of this tile has landed and is visible
                 bulk_wait_all();
@@ -743,8 +756,9 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
 #pragma unroll 1
             for (int ch = 0; ch < BN / 32; ++ch) {   // 16 columns at a time
                 const int col0 = half * (BN / 2) + ch * 16;
-                uint32_t r[16];
+                uint32_t r[16], r2[16];
                 tmem_ld16(tmem + lane_base + (uint32_t)(b * BN + col0), r);
+                if (pair) tmem_ld16(tmem + lane_base + (uint32_t)(b2 * BN + col0), r2);
                 const int cb = c0 + col0;
                 if (!row_ok || cb >= ncols) continue;
                 const int lim = min(16, ncols - cb);   // even; a multiple of 4 when v32
@@ -764,6 +778,23 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
                 } else {
 #pragma unroll
                     for (int t = 0; t < 16; ++t) v[t] = (v[t] + (1LL << (-sh - 1))) >> (-sh);
+                }
+                if (pair) {   // group s-1 from the second buffer, at its own weight
+                    long long v2[16];
+                    if (fits32) {
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) v2[t] = (long long)__float2int_rn(__uint_as_float(r2[t]));
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) v2[t] = __float2ll_rn(__uint_as_float(r2[t]));
+                    }
+                    if (sh2 >= 0) {
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) v[t] += v2[t] << sh2;
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) v[t] += (v2[t] + (1LL << (-sh2 - 1))) >> (-sh2);
+                    }
                 }
                 long long* dst = Crow + cb;
                 if (!first && !last) {   // intermediate segment: reduce-add through L2, asynchronously
@@ -842,10 +873,12 @@ __device__ __forceinline__ bool drain_tile(const SplitArgs& a, const TileSlot& t
                         if (t < lim) *reinterpret_cast<longlong2*>(dst + t) = make_longlong2(v[t], v[t + 1]);
                 }
             }
-            if (first && total > 2) fence_proxy_async_global();   // plain stores before later reduce-adds
+            if (first && tot > 2) fence_proxy_async_global();   // plain stores before later reduce-adds
             tc_fence_before();
             mbar_arrive(&m.acce[b]);
+            if (pair) mbar_arrive(&m.acce[b2]);
         }
+        if (pair) break;   // group s-1 went with it
     }
     if (nstg) bulk_wait_all();   // staging reads done before the slots are reused or the CTA leaves
     if (total == 0 && row_ok) {   // every digit product of the tile is zero
