@@ -32,11 +32,13 @@ TOL = 1e-12
 MAXIT = 50
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal rate; no measured FP64 peak is available
 
-# DRAM traffic of the split product kernel per launch (mean over one IsoMP step), from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
-# source it was taken on (sha256 of csrc/zt_split.cu), null otherwise.
-TRAFFIC = {"sha256": "81df2b00899a389e362725178fdf87e3cfa9b100da1357f2aaf88af6b7a42bb9",
-           "bytes_per_launch": 5852482848}
+# DRAM traffic of the split product kernel per launch (mean over one IsoMP step's
+# full and lower-triangle products), from an ncu capture of dram__bytes_read.sum +
+# dram__bytes_write.sum at N = 2048 scaled to N = 4096 by the tile count (x4 for the
+# full product, x528/136 for the lower one); valid only for the kernel source it was
+# taken on (sha256 of csrc/zt_split.cu), null otherwise.
+TRAFFIC = {"sha256": "52b721f6c711e021e4028dac85783c699803bf40b640444dbe394cefcf9b59a6",
+           "bytes_per_launch": 1813769743, "captured_n": 2048}
 
 
 def _peaks():
@@ -664,8 +666,10 @@ def run_gpu(args):
         "gpu_launches": gpu_launches,
         "e2e": e2e,
         "fp64_form": fp64,
-        "roofline": {"bound": "tensor", "kernel": "zgemm_split_persistent", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "tensor", "kernel": "zgemm_split_kernel", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": (f"ncu DRAM bytes at N={TRAFFIC['captured_n']}, scaled by tile count"
+                                        if traffic else "source changed since the capture"),
                      "peak_source": f"{peaks['source']} bf16 sustained",
                      "work": "BF16 digit-pair MMA units issued (2 x 128 x 256 x 64 flops each, counted on the "
                              "device; exactly-zero digit tiles are skipped)",
