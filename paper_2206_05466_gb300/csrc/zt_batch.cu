@@ -152,7 +152,8 @@ int enqueue_products(zt_batch* b, cudaStream_t s, int gate) {
         return rc;
     b->launches += ZT_SOLVE_LAUNCHES;
     if (b->gemm1.n) {
-        // Pt into the X' planes and B'^T slot 1, Wt into slot 0: one launch
+        // Pt into the X' planes, Wt into B'^T slot 0: one launch; then A into slot 1 and
+        // B = Pt A^H (the same form as the single-plan path)
         if ((rc = zt_split_rows_grouped((const SplitRowsArgs*)b->split_PW.tab, b->split_PW.offs, b->split_PW.n,
                                         b->split_PW.total, s, gate)))
             return rc;
@@ -331,19 +332,19 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
         c_sv.push_back(zt_solve_ctas(N));
         if (p->precision == ZT_PRECISION_SPLIT) {
             SplitRowsArgs ra;
-            if ((rc = zt_split_rows_args(p, p->P, 1, 1, &ra))) return fail(rc);
+            if ((rc = zt_split_rows_args(p, p->P, 1, -1, &ra))) return fail(rc);
             sP.push_back(ra);
             if ((rc = zt_split_rows_args(p, p->Wt, 0, 0, &ra))) return fail(rc);
             sW.push_back(ra);
-            if ((rc = zt_split_rows_args(p, p->A, 1, -1, &ra))) return fail(rc);
+            if ((rc = zt_split_rows_args(p, p->A, 0, 1, &ra))) return fail(rc);
             sA.push_back(ra);
             c_sP.push_back(N);
             GemmEntry e;
             int ctas;
-            if ((rc = zt_split_gemm_entry(p, 0, p->A, -1.0, 0, &e, &ctas))) return fail(rc);
+            if ((rc = zt_split_gemm_entry(p, 0, p->A, -1.0, 0, 1, &e, &ctas))) return fail(rc);   // A = Pt Wt
             g1.push_back(e);
             c_g1.push_back(ctas);
-            if ((rc = zt_split_gemm_entry(p, 1, p->B, -1.0, 1, &e, &ctas))) return fail(rc);
+            if ((rc = zt_split_gemm_entry(p, 1, p->B, +1.0, 1, 0, &e, &ctas))) return fail(rc);   // B = Pt A^H
             g2.push_back(e);
             c_g2.push_back(ctas);
         } else {

@@ -53,6 +53,12 @@ __device__ __forceinline__ int zt_group_find(const int* offs, int n, int b) {
     return lo;
 }
 
+// -x by flipping the sign bit: an integer operation, where a stand-alone FP64
+// negation would take an issue slot of the narrow FP64 pipe.
+__device__ __forceinline__ double neg(double x) {
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+
 // Packed lower-triangular index of (r, c), c <= r.
 __host__ __device__ inline size_t zt_tri(int r, int c) {
     return (size_t)r * (size_t)(r + 1) / 2 + (size_t)c;
@@ -90,7 +96,7 @@ struct zt_plan {
     int npartials = 0;
     // Stream solve by bands of 32 diagonals and segments of 32 rows (zt_solve.cu).
     // Per element, packed lower-triangular row-major (entry (r, c) at zt_tri(r, c)):
-    double* fac_l = nullptr;   // LDL^T multiplier l_i (l_0 = 0)
+    double* fac_l = nullptr;   // LDL^T multiplier, negated: -l_i (l_0 = 0)
     double* fac_nd = nullptr;  // -1 / d_i (0 for the dropped m = 0 row)
     double* fac_f = nullptr;   // F_i: the segment's response to its forward inflow
     double* fac_h = nullptr;   // H_i: the segment's response to its backward inflow
@@ -142,7 +148,7 @@ int zt_timer_collect(zt_plan* p, int iters);
 struct SolveArgs {     // stream solve (zt_solve.cu)
     const double2* W;
     double2* P;
-    const double* fl;      // packed lower-triangular l, nd, F, H (constant)
+    const double* fnl;     // packed lower-triangular -l, nd, F, H (constant)
     const double* fnd;
     const double* ff;
     const double* fh;
@@ -307,7 +313,7 @@ int zt_solve_ctas(int N);
 int zt_solve_grouped(const SolveArgs* tab, const int* offs, int n, int total, int maxN, cudaStream_t s, int gate);
 int zt_split_rows_args(zt_plan* p, const double2* X, int to_a, int b_slot, SplitRowsArgs* out);
 int zt_split_rows_grouped(const SplitRowsArgs* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
-int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, GemmEntry* out,
+int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, int keep_a, GemmEntry* out,
                         int* ctas);
 int zt_split_gemm_grouped(const GemmEntry* tab, const int* offs, int n, int total, cudaStream_t s, int gate);
 int zt_fp64_gemm_args(zt_plan* p, const double2* X, const double2* Y, double2* C, double alpha, int lower_only,
@@ -327,4 +333,5 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
 int zt_split_operand(zt_plan* p, const double2* X, int to_a, int b_slot, cudaStream_t s, int gate);
 // Two operands split in one launch: X1 into the X' planes and B'^T slot 1, X2 into slot 0.
 int zt_split_operands2(zt_plan* p, const double2* X1, const double2* X2, cudaStream_t s, int gate);
-int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, cudaStream_t s, int gate);
+int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, int keep_a, cudaStream_t s,
+                     int gate);

@@ -796,17 +796,20 @@ extern "C" int zeitlin_casimirs(zt_plan* p, const double* W, double* C, void* st
 
 // One fixed-point sweep (Eq. 9): Pt = solve(Wt), A = Pt Wt,
 // B = A Pt, Wt <- W_n + h/2 (A - A^H) + h^2/4 B, residual, stop decision.
-// Pt = solve(Wt), A = Pt Wt, B = A Pt (lower half).  In split form Pt is
-// split once into both operand forms.
+// Pt = solve(Wt), A = Pt Wt, B = A Pt (lower half).
 static int enqueue_products(zt_plan* p, cudaStream_t s, int gate) {
     int rc;
     if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, gate))) return rc;
     if (p->precision == ZT_PRECISION_SPLIT) {
-        // Pt into the X' planes and B'^T slot 1, Wt into slot 0, in one launch
+        // The product kernel forms X conj(Y)^T from the X' planes (rows of X) and a
+        // B'^T slot (rows of Y).  A = Pt Wt = -Pt conj(Wt)^T (Wt skew-Hermitian), and
+        // B = A Pt = Pt Wt Pt is skew-Hermitian, so B = -B^H = -Pt^H A^H = Pt A^H = Pt conj(A)^T:
+        // both products take Pt's X' planes, split once.  Pt into the X' planes and Wt
+        // into slot 0 in one launch, then A into slot 1.
         if ((rc = zt_split_operands2(p, p->P, p->Wt, s, gate))) return rc;
-        if ((rc = zt_split_product(p, 0, p->A, -1.0, 0, s, gate))) return rc;   // A = Pt Wt
-        if ((rc = zt_split_operand(p, p->A, 1, -1, s, gate))) return rc;   // A: X' planes
-        return zt_split_product(p, 1, p->B, -1.0, 1, s, gate);                // B = A Pt
+        if ((rc = zt_split_product(p, 0, p->A, -1.0, 0, 1, s, gate))) return rc;   // A = Pt Wt
+        if ((rc = zt_split_operand(p, p->A, 0, 1, s, gate))) return rc;            // A: B'^T slot 1
+        return zt_split_product(p, 1, p->B, +1.0, 1, 0, s, gate);                   // B = Pt A^H
     }
     if ((rc = zgemm(p, p->P, p->Wt, p->A, -1.0, 0, s, gate))) return rc;
     return zgemm(p, p->A, p->P, p->B, -1.0, 1, s, gate);

@@ -3,8 +3,10 @@
 // Diagonal m (0 <= m < N) of the lower triangle holds the n = N-m unknowns of
 // the tridiagonal system T_m x = -w (T_m = -Delta^m, Eq. 13), solved with the
 // plan's LDL^T factors:
-//     forward   z_i = w_i - l_i z_{i-1}                  (l_0 = 0)
-//     backward  x_i = nd_i z_i - l_{i+1} x_{i+1}          (nd_i = -1/d_i)
+//     forward   z_i = w_i + nl_i z_{i-1}                 (nl_i = -l_i, l_0 = 0)
+//     backward  x_i = nd_i z_i + nl_{i+1} x_{i+1}         (nd_i = -1/d_i)
+// The device holds nl, not l: on GB300 a stand-alone FP64 negation is an
+// instruction of the narrow FP64 pipe, and the sweeps are bound by that pipe.
 //
 // Layout of the work.  A band is 32 consecutive diagonals m0 .. m0+31, one per
 // lane of a warp.  In row r the band's elements (r, r-m), m in the band, are
@@ -26,9 +28,10 @@
 //   FB  per (band, segment) warp: forward sweep z0 (kept in shared memory),
 //       then backward sweep x0, parked in the lower triangle of P; the
 //       segment's last z0 and first x0 go to small [K][N] arrays;
-//   S   one thread per (diagonal, re/im): the forward inflows c_k by the
-//       recurrence over the segments' end values, then the backward inflows
-//       d_k; for m = 0 also the mean of the solution;
+//   S   one warp per diagonal: the forward inflows c_k from the segments'
+//       end values, then the backward inflows d_k, each a first-order linear
+//       recurrence over k scanned in parallel across the lanes; for m = 0 also
+//       the mean of the solution;
 //   C   per (band, segment) warp: x = x0 + F c + H d, written to the lower
 //       triangle row by row and, as -conj, to the upper triangle (the mirror
 //       of a band segment is a set of partial row runs, written from shared
@@ -46,50 +49,69 @@
 
 namespace {
 constexpr int BW = 32;            // diagonals per band (lanes of a warp)
-constexpr int SL = 32;            // rows per segment
+constexpr int SL = 16;            // rows per segment: 8 KB of shared memory per warp, 24 warps per SM
+constexpr int SPB = BW / SL;      // segments per 32 rows of a band
+static_assert(BW % SL == 0, "a band's 32-row blocks split into whole segments");
 constexpr int WPC = 4;            // warps per CTA
-constexpr int CH = 8;             // rows per load chunk
+constexpr int CH = 8;             // rows per load chunk of the sweeps
+constexpr int CHC = 4;            // rows per load chunk of the corrections (no dependency between rows)
 constexpr size_t WARP_SMEM = (size_t)SL * BW * sizeof(double2);
 constexpr size_t CTA_SMEM = WPC * WARP_SMEM;
-constexpr int SCAN_TH = 64;    // threads of a scan CTA: 2 N threads spread over many SMs
+constexpr int SCAN_TH = 128;   // threads of a scan CTA: one warp per diagonal
 
 __host__ __device__ inline int nbands(int N) { return (N + BW - 1) / BW; }
-__host__ __device__ inline int items(int N) {   // (band, segment) pairs: band b has nbands - b segments
+// Segments of band b: SPB (nbands - b), the rows m0 = 32 b .. 32 nbands - 1 in
+// blocks of SL (trailing ones may lie past row N - 1; for lane t >= SL the
+// first segment holds no position of its diagonal).  Band 0 has nseg(N).
+__host__ __device__ inline int nseg(int N) { return SPB * nbands(N); }
+__host__ __device__ inline int band_segs(int N, int b) { return SPB * (nbands(N) - b); }
+__host__ __device__ inline int items(int N) {   // (band, segment) pairs
     const int nb = nbands(N);
-    return nb * (nb + 1) / 2;
+    return SPB * (nb * (nb + 1) / 2);
 }
 
 // Work item q -> (band b, segment k).  Items are enumerated band by band from
-// the last band (1 segment) to band 0 (nb segments).
+// the last band (SPB segments) to band 0 (nseg segments): band nb - 1 - r
+// starts at item SPB r (r + 1) / 2.
 __device__ __forceinline__ void item_of(int q, int N, int& b, int& k) {
-    int r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-    while (r * (r + 1) / 2 > q) --r;
-    while ((r + 1) * (r + 2) / 2 <= q) ++r;
-    k = q - r * (r + 1) / 2;
+    int r = (int)((sqrtf(8.0f * (float)(q / SPB) + 1.0f) - 1.0f) * 0.5f);
+    while (r > 0 && SPB * (r * (r + 1) / 2) > q) --r;
+    while (SPB * ((r + 1) * (r + 2) / 2) <= q) ++r;
+    k = q - SPB * (r * (r + 1) / 2);
     b = nbands(N) - 1 - r;
 }
 }  // namespace
 
 // ---- FB: local forward and backward sweeps of one band segment ----
-__device__ __forceinline__ void solve_fb_body(const SolveArgs& a, int q, double2* zs) {
-    if (zt_gate_skip(a.st, a.gate)) return;
+// B0: band 0, which holds the singular m = 0 block.  The two cases are separate
+// instantiations: with a runtime test the compiler executes the band-0 adds
+// (of zeros) in every band, and on GB300 each is an issue slot of the FP64 pipe.
+template <bool B0>
+__device__ __forceinline__ void solve_fb_band(const SolveArgs& a, int b, int k, double2* zs) {
     const int N = a.N, lane = threadIdx.x & 31;
-    int b, k;
-    item_of(q, N, b, k);
     const int m0 = b * BW, R0 = m0 + k * SL, R1 = min(R0 + SL, N);
     const int m = m0 + lane;
     const bool valid = m < N;
     const double2* __restrict__ W = a.W;
-    const double* __restrict__ fl = a.fl;
+    const double* __restrict__ fnl = a.fnl;
     const double* __restrict__ fnd = a.fnd;
 
     // m = 0: mean of the right-hand side (diagonal 0 of W), reduced by the warp
     double mur = 0.0, mui = 0.0;
-    if (b == 0) {
-        for (int i = lane; i < N; i += 32) {
-            const double2 v = W[(size_t)i * N + i];
-            mur += v.x;
-            mui += v.y;
+    if (B0) {   // eight strided loads in flight per lane
+        constexpr int UR = 8;
+        for (int i0 = lane; i0 < N; i0 += 32 * UR) {
+            double2 v[UR];
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                const int i = i0 + 32 * u;
+                v[u] = i < N ? W[(size_t)i * N + i] : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < UR; ++u) {
+                mur += v[u].x;
+                mui += v[u].y;
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             mur += __shfl_xor_sync(0xffffffffu, mur, o);
@@ -110,7 +132,7 @@ __device__ __forceinline__ void solve_fb_body(const SolveArgs& a, int q, double2
             if (valid && r < R1 && r >= m) {
                 const size_t e = (size_t)r * N + (r - m);
                 w[u] = W[e];
-                l[u] = __ldg(fl + zt_tri(r, r - m));
+                l[u] = __ldg(fnl + zt_tri(r, r - m));
             } else {
                 w[u] = make_double2(0.0, 0.0);
                 l[u] = 0.0;
@@ -120,12 +142,12 @@ __device__ __forceinline__ void solve_fb_body(const SolveArgs& a, int q, double2
         for (int u = 0; u < CH; ++u) {
             const int r = R0 + c0 + u;
             if (valid && r < R1 && r >= m) {
-                if (b == 0) {   // warp-uniform: only band 0 holds m = 0
+                if (B0) {
                     w[u].x -= mur;
                     w[u].y -= mui;
                 }
-                zr = fma(-l[u], zr, w[u].x);
-                zi = fma(-l[u], zi, w[u].y);
+                zr = fma(l[u], zr, w[u].x);
+                zi = fma(l[u], zi, w[u].y);
                 zs[(c0 + u) * BW + lane] = make_double2(zr, zi);
             }
         }
@@ -143,7 +165,7 @@ __device__ __forceinline__ void solve_fb_body(const SolveArgs& a, int q, double2
             if (valid && r < R1 && r >= m) {
                 const size_t t = zt_tri(r, r - m);
                 nd[u] = __ldg(fnd + t);
-                l[u] = __ldg(fl + t);
+                l[u] = __ldg(fnl + t);
             } else {
                 nd[u] = l[u] = 0.0;
             }
@@ -153,10 +175,10 @@ __device__ __forceinline__ void solve_fb_body(const SolveArgs& a, int q, double2
             const int r = R0 + c0 + u;
             if (valid && r < R1 && r >= m) {
                 const double2 z = zs[(c0 + u) * BW + lane];
-                xr = fma(-lnext, xr, nd[u] * z.x);
-                xi = fma(-lnext, xi, nd[u] * z.y);
+                xr = fma(lnext, xr, nd[u] * z.x);
+                xi = fma(lnext, xi, nd[u] * z.y);
                 a.P[(size_t)r * N + (r - m)] = make_double2(xr, xi);
-                if (b == 0) {   // warp-uniform: segment sums for the m = 0 mean
+                if (B0) {   // segment sums for the m = 0 mean
                     sxr += xr;
                     sxi += xi;
                 }
@@ -165,81 +187,234 @@ __device__ __forceinline__ void solve_fb_body(const SolveArgs& a, int q, double2
         }
     }
     if (valid) a.seg_x[(size_t)k * N + m] = make_double2(xr, xi);   // x0 at the segment's first position
-    if (m == 0) a.sum_x[k] = make_double2(sxr, sxi);
+    if (B0 && m == 0) a.sum_x[k] = make_double2(sxr, sxi);
 }
 
-// ---- S: inflows of every segment of one diagonal, one part (re/im) per thread ----
+// FB takes the items in reverse order, band 0 first: its warps also reduce
+// diagonal 0 for the m = 0 mean, so they must not be the last to start.
+__device__ __forceinline__ void solve_fb_body(const SolveArgs& a, int q, double2* zs) {
+    if (zt_gate_skip(a.st, a.gate)) return;
+    int b, k;
+    item_of(items(a.N) - 1 - q, a.N, b, k);
+    if (b == 0)
+        solve_fb_band<true>(a, b, k, zs);
+    else
+        solve_fb_band<false>(a, b, k, zs);
+}
+
+// ---- S: inflows of every segment of one diagonal, one warp per diagonal ----
 //   forward:  c_0 = 0,  c_{k+1} = G_end(k) c_k + z0_end(k)
 //   backward: d_{K-1} = 0,  d_{k-1} = x0_start(k) + F_start(k) c_k + H_start(k) d_k
-// For m = 0 also the mean of the solution, sum_k (sum x0 + c_k sum F + d_k sum H) / N.
-__device__ __forceinline__ void solve_scan_body(const SolveArgs& a, int gid) {
+// Both are first-order linear recurrences, so the warp scans them in parallel:
+// lane j owns a run of at most PM consecutive segments and composes their
+// affine maps (v -> A v + B), a shuffle scan composes the runs (forward from
+// lane 0, backward from lane 31), and each lane replays its run from the
+// inflow it receives.  All of a run's inputs are loaded at once into
+// registers, so the whole scan costs one round trip to memory.  For m = 0 also
+// the mean of the solution, sum_k (sum x0 + c_k sum F + d_k sum H) / N,
+// reduced over the lanes in a fixed order.
+template <int PM>
+__device__ __forceinline__ void solve_scan_run(const SolveArgs& a, int m, int k0, int k1) {
+    const int N = a.N, lane = threadIdx.x & 31;
+    constexpr unsigned FULL = 0xffffffffu;
+    double g[PM], h[PM], f[PM];
+    double2 z[PM], x0[PM], c[PM];
+#pragma unroll
+    for (int u = 0; u < PM; ++u) {
+        const int k = k0 + u;
+        if (k < k1) {
+            const size_t e = (size_t)k * N + m;
+            g[u] = __ldg(a.seg_g + e);
+            h[u] = __ldg(a.seg_h + e);
+            f[u] = __ldg(a.seg_f + e);
+            z[u] = __ldg(a.seg_z + e);
+            x0[u] = __ldg(a.seg_x + e);
+        } else {   // identity maps past the run
+            g[u] = h[u] = 1.0;
+            f[u] = 0.0;
+            z[u] = x0[u] = make_double2(0.0, 0.0);
+        }
+    }
+    // forward: this run's map, then the maps of all runs before it
+    double A = 1.0, Br = 0.0, Bi = 0.0;
+#pragma unroll
+    for (int u = 0; u < PM; ++u) {
+        Br = fma(g[u], Br, z[u].x);
+        Bi = fma(g[u], Bi, z[u].y);
+        A *= g[u];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double Ap = __shfl_up_sync(FULL, A, o);
+        const double Brp = __shfl_up_sync(FULL, Br, o);
+        const double Bip = __shfl_up_sync(FULL, Bi, o);
+        if (lane >= o) {
+            Br = fma(A, Brp, Br);
+            Bi = fma(A, Bip, Bi);
+            A *= Ap;
+        }
+    }
+    double cr = __shfl_up_sync(FULL, Br, 1), ci = __shfl_up_sync(FULL, Bi, 1);
+    if (lane == 0) cr = ci = 0.0;
+#pragma unroll
+    for (int u = 0; u < PM; ++u) {
+        c[u] = make_double2(cr, ci);
+        if (k0 + u < k1) a.cf[(size_t)(k0 + u) * N + m] = c[u];
+        cr = fma(g[u], cr, z[u].x);
+        ci = fma(g[u], ci, z[u].y);
+    }
+    // backward: d_{k-1} = H_k d_k + E_k with E_k = x0_k + F_k c_k, runs composed from lane 31 down
+    double2 E[PM];
+    A = 1.0;
+    Br = Bi = 0.0;
+#pragma unroll
+    for (int u = PM - 1; u >= 0; --u) {
+        E[u] = make_double2(fma(f[u], c[u].x, x0[u].x), fma(f[u], c[u].y, x0[u].y));
+        Br = fma(h[u], Br, E[u].x);
+        Bi = fma(h[u], Bi, E[u].y);
+        A *= h[u];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double Ap = __shfl_down_sync(FULL, A, o);
+        const double Brp = __shfl_down_sync(FULL, Br, o);
+        const double Bip = __shfl_down_sync(FULL, Bi, o);
+        if (lane + o < 32) {
+            Br = fma(A, Brp, Br);
+            Bi = fma(A, Bip, Bi);
+            A *= Ap;
+        }
+    }
+    double dr = __shfl_down_sync(FULL, Br, 1), di = __shfl_down_sync(FULL, Bi, 1);
+    if (lane == 31) dr = di = 0.0;
+    double tr = 0.0, ti = 0.0;
+#pragma unroll
+    for (int u = PM - 1; u >= 0; --u) {
+        const int k = k0 + u;
+        if (k < k1) {
+            a.cb[(size_t)k * N + m] = make_double2(dr, di);
+            if (m == 0) {
+                const double2 sx0 = a.sum_x[k];
+                tr += sx0.x + c[u].x * a.sum_f[k] + dr * a.sum_h[k];
+                ti += sx0.y + c[u].y * a.sum_f[k] + di * a.sum_h[k];
+            }
+        }
+        dr = fma(h[u], dr, E[u].x);
+        di = fma(h[u], di, E[u].y);
+    }
+    if (m == 0) {   // warp-uniform
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tr += __shfl_xor_sync(FULL, tr, o);
+            ti += __shfl_xor_sync(FULL, ti, o);
+        }
+        if (lane == 0) *a.mu = make_double2(tr / N, ti / N);
+    }
+}
+
+// The same scan for runs longer than a few segments (N > 4096): the run's
+// values are loaded again where they are needed instead of held in registers.
+__device__ __noinline__ void solve_scan_long(const SolveArgs& a, int m, int k0, int k1) {
+    const int N = a.N, lane = threadIdx.x & 31;
+    constexpr unsigned FULL = 0xffffffffu;
+    double A = 1.0, Br = 0.0, Bi = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const size_t e = (size_t)k * N + m;
+        const double g = __ldg(a.seg_g + e);
+        const double2 z = __ldg(a.seg_z + e);
+        Br = fma(g, Br, z.x);
+        Bi = fma(g, Bi, z.y);
+        A *= g;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double Ap = __shfl_up_sync(FULL, A, o);
+        const double Brp = __shfl_up_sync(FULL, Br, o);
+        const double Bip = __shfl_up_sync(FULL, Bi, o);
+        if (lane >= o) {
+            Br = fma(A, Brp, Br);
+            Bi = fma(A, Bip, Bi);
+            A *= Ap;
+        }
+    }
+    double cr = __shfl_up_sync(FULL, Br, 1), ci = __shfl_up_sync(FULL, Bi, 1);
+    if (lane == 0) cr = ci = 0.0;
+    for (int k = k0; k < k1; ++k) {
+        const size_t e = (size_t)k * N + m;
+        a.cf[e] = make_double2(cr, ci);
+        const double g = __ldg(a.seg_g + e);
+        const double2 z = __ldg(a.seg_z + e);
+        cr = fma(g, cr, z.x);
+        ci = fma(g, ci, z.y);
+    }
+    A = 1.0;
+    Br = Bi = 0.0;
+    for (int k = k1 - 1; k >= k0; --k) {
+        const size_t e = (size_t)k * N + m;
+        const double hk = __ldg(a.seg_h + e), fk = __ldg(a.seg_f + e);
+        const double2 x0 = __ldg(a.seg_x + e), c = a.cf[e];   // cf: written above by this lane
+        Br = fma(hk, Br, fma(fk, c.x, x0.x));
+        Bi = fma(hk, Bi, fma(fk, c.y, x0.y));
+        A *= hk;
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double Ap = __shfl_down_sync(FULL, A, o);
+        const double Brp = __shfl_down_sync(FULL, Br, o);
+        const double Bip = __shfl_down_sync(FULL, Bi, o);
+        if (lane + o < 32) {
+            Br = fma(A, Brp, Br);
+            Bi = fma(A, Bip, Bi);
+            A *= Ap;
+        }
+    }
+    double dr = __shfl_down_sync(FULL, Br, 1), di = __shfl_down_sync(FULL, Bi, 1);
+    if (lane == 31) dr = di = 0.0;
+    double tr = 0.0, ti = 0.0;
+    for (int k = k1 - 1; k >= k0; --k) {
+        const size_t e = (size_t)k * N + m;
+        a.cb[e] = make_double2(dr, di);
+        const double hk = __ldg(a.seg_h + e), fk = __ldg(a.seg_f + e);
+        const double2 x0 = __ldg(a.seg_x + e), c = a.cf[e];
+        if (m == 0) {
+            const double2 sx0 = a.sum_x[k];
+            tr += sx0.x + c.x * a.sum_f[k] + dr * a.sum_h[k];
+            ti += sx0.y + c.y * a.sum_f[k] + di * a.sum_h[k];
+        }
+        dr = fma(hk, dr, fma(fk, c.x, x0.x));
+        di = fma(hk, di, fma(fk, c.y, x0.y));
+    }
+    if (m == 0) {   // warp-uniform
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tr += __shfl_xor_sync(FULL, tr, o);
+            ti += __shfl_xor_sync(FULL, ti, o);
+        }
+        if (lane == 0) *a.mu = make_double2(tr / N, ti / N);
+    }
+}
+
+__device__ __forceinline__ void solve_scan_body(const SolveArgs& a, int m) {
     if (zt_gate_skip(a.st, a.gate)) return;
-    const int N = a.N, m = gid >> 1, part = gid & 1;
-    if (m >= N) return;
-    const int Kb = nbands(N) - m / BW;
-    // values of this diagonal's segments, 16 at a time: the loads of a chunk are
-    // independent of the recurrence, so they are all in flight together
-    const double* __restrict__ sg = a.seg_g;
-    const double* __restrict__ sf = a.seg_f;
-    const double* __restrict__ sh = a.seg_h;
-    const double* __restrict__ sz = reinterpret_cast<const double*>(a.seg_z) + part;
-    const double* __restrict__ sx = reinterpret_cast<const double*>(a.seg_x) + part;
-    double* __restrict__ cf = reinterpret_cast<double*>(a.cf) + part;
-    double* __restrict__ cb = reinterpret_cast<double*>(a.cb) + part;
-    constexpr int U = 16;
-    double c = 0.0;
-    for (int k0 = 0; k0 < Kb; k0 += U) {
-        double gg[U], zz[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const size_t e = (size_t)(k0 + u) * N + m;
-            const bool in = k0 + u < Kb;
-            gg[u] = in ? __ldg(sg + e) : 0.0;
-            zz[u] = in ? __ldg(sz + 2 * e) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (k0 + u < Kb) {
-                const size_t e = (size_t)(k0 + u) * N + m;
-                cf[2 * e] = c;
-                c = fma(gg[u], c, zz[u]);
-            }
-        }
-    }
-    double d = 0.0, tot = 0.0;
-    for (int k1 = Kb - 1; k1 >= 0; k1 -= U) {
-        double xx[U], ff[U], hh[U], cc[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k1 - u;
-            const size_t e = (size_t)(k < 0 ? 0 : k) * N + m;
-            const bool in = k >= 0;
-            xx[u] = in ? __ldg(sx + 2 * e) : 0.0;
-            ff[u] = in ? __ldg(sf + e) : 0.0;
-            hh[u] = in ? __ldg(sh + e) : 0.0;
-            cc[u] = in ? cf[2 * e] : 0.0;   // written above by this thread
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int k = k1 - u;
-            if (k >= 0) {
-                const size_t e = (size_t)k * N + m;
-                cb[2 * e] = d;
-                if (m == 0)
-                    tot += reinterpret_cast<const double*>(a.sum_x + k)[part] + cc[u] * a.sum_f[k] + d * a.sum_h[k];
-                d = fma(hh[u], d, fma(ff[u], cc[u], xx[u]));
-            }
-        }
-    }
-    if (m == 0) reinterpret_cast<double*>(a.mu)[part] = tot / N;
+    const int N = a.N, lane = threadIdx.x & 31;
+    if (m >= N) return;   // warp-uniform
+    const int Kb = band_segs(N, m / BW);
+    const int per = (Kb + 31) / 32;   // warp-uniform
+    const int k0 = min(lane * per, Kb), k1 = min(k0 + per, Kb);
+    if (per <= 2)
+        solve_scan_run<2>(a, m, k0, k1);
+    else if (per <= 4)
+        solve_scan_run<4>(a, m, k0, k1);
+    else if (per <= 8)
+        solve_scan_run<8>(a, m, k0, k1);
+    else
+        solve_scan_long(a, m, k0, k1);   // N > 4096
 }
 
 // ---- C: x = x0 + F c + H d; both triangles ----
-__device__ __forceinline__ void solve_c_body(const SolveArgs& a, int q, double2* xs) {
-    if (zt_gate_skip(a.st, a.gate)) return;
+template <bool B0>
+__device__ __forceinline__ void solve_c_band(const SolveArgs& a, int b, int k, double2* xs) {
     const int N = a.N, lane = threadIdx.x & 31;
-    int b, k;
-    item_of(q, N, b, k);
     const int m0 = b * BW, R0 = m0 + k * SL, R1 = min(R0 + SL, N);
     const int m = m0 + lane;
     const bool valid = m < N;
@@ -247,15 +422,15 @@ __device__ __forceinline__ void solve_c_body(const SolveArgs& a, int q, double2*
     if (valid) {
         c = a.cf[(size_t)k * N + m];
         d = a.cb[(size_t)k * N + m];
-        if (m == 0) mm = *a.mu;
+        if (B0 && m == 0) mm = *a.mu;
     }
     const double* __restrict__ ff = a.ff;
     const double* __restrict__ fh = a.fh;
-    for (int c0 = 0; c0 < SL; c0 += CH) {
-        double2 x0[CH];
-        double f[CH], h[CH];
+    for (int c0 = 0; c0 < SL; c0 += CHC) {
+        double2 x0[CHC];
+        double f[CHC], h[CHC];
 #pragma unroll
-        for (int u = 0; u < CH; ++u) {
+        for (int u = 0; u < CHC; ++u) {
             const int r = R0 + c0 + u;
             if (valid && r < R1 && r >= m) {
                 const size_t t = zt_tri(r, r - m);
@@ -268,12 +443,12 @@ __device__ __forceinline__ void solve_c_body(const SolveArgs& a, int q, double2*
             }
         }
 #pragma unroll
-        for (int u = 0; u < CH; ++u) {
+        for (int u = 0; u < CHC; ++u) {
             const int r = R0 + c0 + u;
             if (valid && r < R1 && r >= m) {
                 double2 x = make_double2(fma(h[u], d.x, fma(f[u], c.x, x0[u].x)),
                                          fma(h[u], d.y, fma(f[u], c.y, x0[u].y)));
-                if (b == 0) {   // warp-uniform: the m = 0 mean (zero on the other lanes)
+                if (B0) {   // the m = 0 mean (zero on the other lanes)
                     x.x -= mm.x;
                     x.y -= mm.y;
                 }
@@ -283,34 +458,55 @@ __device__ __forceinline__ void solve_c_body(const SolveArgs& a, int q, double2*
         }
     }
     __syncwarp();
-    // upper triangle: P[i, i+m] = -conj(P[i+m, i]).  Upper row i = 32k + j holds, for the
-    // lanes t with -t <= j <= 31 - t (and i >= 0, row i + m < R1), adjacent columns i + m.
-    for (int j = -(SL - 1); j <= SL - 1; ++j) {
+    // upper triangle: P[i, i+m] = -conj(P[i+m, i]).  Upper row i = SL k + j holds, for the
+    // lanes t with -t <= j <= SL - 1 - t (and i >= 0, row i + m < R1), adjacent columns i + m.
+    for (int j = -(BW - 1); j <= SL - 1; ++j) {
         const int i = k * SL + j;       // position along the diagonals (k * SL = R0 - m0)
         const int rr = j + lane;        // row of the segment holding (i + m, i)
         if (valid && m > 0 && i >= 0 && rr >= 0 && rr < SL && R0 + rr < R1) {
             const double2 x = xs[rr * BW + lane];
-            a.P[(size_t)i * N + (i + m)] = make_double2(-x.x, x.y);
+            a.P[(size_t)i * N + (i + m)] = make_double2(neg(x.x), x.y);
         }
     }
 }
 
-__global__ void __launch_bounds__(WPC * 32) solve_fb_kernel(const SolveArgs a) {
+__device__ __forceinline__ void solve_c_body(const SolveArgs& a, int q, double2* xs) {
+    if (zt_gate_skip(a.st, a.gate)) return;
+    int b, k;
+    item_of(q, a.N, b, k);
+    if (b == 0)
+        solve_c_band<true>(a, b, k, xs);
+    else
+        solve_c_band<false>(a, b, k, xs);
+}
+
+// Single-plan launches are sized to the resident CTAs and stride over the
+// items, so that no partial last wave of CTAs leaves most SMs idle.  Item
+// q goes to warp q / gridDim.x of CTA q % gridDim.x: consecutive items (the
+// band-0 items, which also reduce diagonal 0, come first in FB) land on
+// different SMs.
+__global__ void __launch_bounds__(WPC * 32, 6) solve_fb_kernel(const SolveArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int w = threadIdx.x >> 5;
-    const int q = blockIdx.x * WPC + w;
-    if (q < items(a.N)) solve_fb_body(a, q, reinterpret_cast<double2*>(smem) + (size_t)w * SL * BW);
+    const int w = threadIdx.x >> 5, nq = items(a.N);
+    double2* zs = reinterpret_cast<double2*>(smem) + (size_t)w * SL * BW;
+    for (int q = w * gridDim.x + blockIdx.x; q < nq; q += gridDim.x * WPC) {
+        solve_fb_body(a, q, zs);
+        __syncwarp();
+    }
 }
 
 __global__ void __launch_bounds__(SCAN_TH) solve_scan_kernel(const SolveArgs a) {
-    solve_scan_body(a, blockIdx.x * SCAN_TH + threadIdx.x);
+    solve_scan_body(a, (blockIdx.x * SCAN_TH + threadIdx.x) >> 5);
 }
 
-__global__ void __launch_bounds__(WPC * 32) solve_c_kernel(const SolveArgs a) {
+__global__ void __launch_bounds__(WPC * 32, 6) solve_c_kernel(const SolveArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int w = threadIdx.x >> 5;
-    const int q = blockIdx.x * WPC + w;
-    if (q < items(a.N)) solve_c_body(a, q, reinterpret_cast<double2*>(smem) + (size_t)w * SL * BW);
+    const int w = threadIdx.x >> 5, nq = items(a.N);
+    double2* xs = reinterpret_cast<double2*>(smem) + (size_t)w * SL * BW;
+    for (int q = w * gridDim.x + blockIdx.x; q < nq; q += gridDim.x * WPC) {
+        solve_c_body(a, q, xs);
+        __syncwarp();
+    }
 }
 
 // Grouped: one grid over several instances (CTA counts prefix-summed in offs).
@@ -338,18 +534,18 @@ __global__ void __launch_bounds__(WPC * 32) solve_c_grouped(const SolveArgs* tab
 __global__ void __launch_bounds__(SCAN_TH) solve_scan_grouped(const SolveArgs* tab, int gate) {
     SolveArgs a = tab[blockIdx.y];
     a.gate = gate;
-    solve_scan_body(a, blockIdx.x * SCAN_TH + threadIdx.x);
+    solve_scan_body(a, (blockIdx.x * SCAN_TH + threadIdx.x) >> 5);
 }
 
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
 static int solve_ctas(int N) { return (items(N) + WPC - 1) / WPC; }
-static int scan_ctas(int N) { return (2 * N + SCAN_TH - 1) / SCAN_TH; }
+static int scan_ctas(int N) { return (N * 32 + SCAN_TH - 1) / SCAN_TH; }
 
 int zt_solve_create(zt_plan* p) {
     const int N = p->N;
-    p->nseg = nbands(N);
+    p->nseg = nseg(N);
     const size_t ns = (size_t)N * p->nseg, ntri = (size_t)N * (N + 1) / 2;
     cudaStream_t ms = p->mstream;
     ZT_CU(ZT_DMALLOC(p->fac_l, ntri * sizeof(double), ms));
@@ -375,6 +571,31 @@ int zt_solve_create(zt_plan* p) {
     return ZT_OK;
 }
 
+// CTAs of a single-plan sweep launch: all resident at once (the smaller of the
+// two kernels' residencies), at most one per warp pair of items.
+static int solve_grid(int N) {
+    static int resident_of[64] = {};   // per device ordinal, filled on first use (benign race)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return solve_ctas(N);
+    }
+    int& resident = resident_of[dev];
+    if (resident == 0) {
+        int nsm = 0, b1 = 0, b2 = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, solve_fb_kernel, WPC * 32, CTA_SMEM) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, solve_c_kernel, WPC * 32, CTA_SMEM) != cudaSuccess ||
+            nsm <= 0 || b1 <= 0 || b2 <= 0) {
+            cudaGetLastError();
+            return solve_ctas(N);
+        }
+        resident = nsm * (b1 < b2 ? b1 : b2);
+    }
+    const int c = solve_ctas(N);
+    return c < resident ? c : resident;
+}
+
 void zt_solve_destroy(zt_plan* p) {
     cudaStream_t ms = p->mstream;
     zt_dfree(p->fac_l, ms);
@@ -395,7 +616,7 @@ void zt_solve_destroy(zt_plan* p) {
 }
 
 size_t zt_solve_bytes(int N) {
-    const size_t K = (size_t)nbands(N), ns = (size_t)N * K, ntri = (size_t)N * (N + 1) / 2;
+    const size_t K = (size_t)nseg(N), ns = (size_t)N * K, ntri = (size_t)N * (N + 1) / 2;
     return 4 * ntri * 8 + ns * (16 + 16 + 8 + 8 + 8 + 16 + 16) + K * (16 + 8 + 8) + 16;
 }
 
@@ -407,7 +628,7 @@ size_t zt_solve_bytes(int N) {
 static void diagonal_responses(int N, int m, const double* l_tri, const double* nd_tri, double* F, double* H,
                                double* sg, double* sf, double* sh, double* sumf, double* sumh,
                                std::vector<double>& G) {
-    const int n = N - m, t = m % BW, Kb = nbands(N) - m / BW;
+    const int n = N - m, t = m % BW, Kb = band_segs(N, m / BW);
     auto at = [&](int i) { return zt_tri(i + m, i); };
     G.resize((size_t)SL);
     for (int k = 0; k < Kb; ++k) {
@@ -437,7 +658,7 @@ static void diagonal_responses(int N, int m, const double* l_tri, const double* 
             hs += h;
         }
         sf[e] = f;
-        sh[e] = h;
+        sh[e] = s1 > s0 ? h : 1.0;   // an empty segment passes its inflows on unchanged
         if (m == 0) {
             sumf[k] = fs;
             sumh[k] = hs;
@@ -448,9 +669,10 @@ static void diagonal_responses(int N, int m, const double* l_tri, const double* 
 int zt_solve_upload_factors(zt_plan* p, const double* host_l, const double* host_nd) {
     const int N = p->N, K = p->nseg;
     const size_t ns = (size_t)N * K, ntri = (size_t)N * (N + 1) / 2;
-    std::vector<double> F, H, sg, sf, sh, sumf, sumh;
+    std::vector<double> F, H, NL, sg, sf, sh, sumf, sumh;
     try {
         F.assign(ntri, 0.0);
+        NL.assign(ntri, 0.0);
         H.assign(ntri, 0.0);
         sg.assign(ns, 0.0);
         sf.assign(ns, 0.0);
@@ -473,7 +695,8 @@ int zt_solve_upload_factors(zt_plan* p, const double* host_l, const double* host
         });
     for (auto& x : th) x.join();
     cudaStream_t cs = p->mstream;
-    cudaMemcpyAsync(p->fac_l, host_l, ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
+    for (size_t i = 0; i < ntri; ++i) NL[i] = -host_l[i];
+    cudaMemcpyAsync(p->fac_l, NL.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
     cudaMemcpyAsync(p->fac_nd, host_nd, ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
     cudaMemcpyAsync(p->fac_f, F.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
     cudaMemcpyAsync(p->fac_h, H.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
@@ -494,7 +717,7 @@ int zt_solve_args(zt_plan* p, const double2* W, double2* P, SolveArgs* out) {
     SolveArgs& a = *out;
     a.W = W;
     a.P = P;
-    a.fl = p->fac_l;
+    a.fnl = p->fac_l;
     a.fnd = p->fac_nd;
     a.ff = p->fac_f;
     a.fh = p->fac_h;
@@ -531,7 +754,7 @@ int zt_launch_stream_solve(zt_plan* p, const double2* W, double2* P, cudaStream_
     SolveArgs a;
     zt_solve_args(p, W, P, &a);
     a.gate = gate;
-    const int ctas = solve_ctas(N);
+    const int ctas = solve_grid(N);
     const double bytes = 8.0 * N * (N + 1.0) + 16.0 * N * N;
     const int t = zt_timer_begin(p, ZT_KERNEL_SOLVE, bytes, bytes, s);
     solve_fb_kernel<<<ctas, WPC * 32, CTA_SMEM, s>>>(a);

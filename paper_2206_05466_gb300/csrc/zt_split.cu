@@ -1332,9 +1332,9 @@ int zt_split_operands2(zt_plan* p, const double2* X1, const double2* X2, cudaStr
     const int N = p->N;
     SplitRowsArgs r1, r2;
     int rc;
-    if ((rc = zt_split_rows_args(p, X1, 1, 1, &r1)) || (rc = zt_split_rows_args(p, X2, 0, 0, &r2))) return rc;
+    if ((rc = zt_split_rows_args(p, X1, 1, -1, &r1)) || (rc = zt_split_rows_args(p, X2, 0, 0, &r2))) return rc;
     r1.gate = r2.gate = gate;
-    const double bytes = 2 * 16.0 * N * N + 2.0 * w->s * (double)N * w->ldk + 2 * 4.0 * w->s * (double)N * w->ldk;
+    const double bytes = 2 * 16.0 * N * N + 2.0 * w->s * (double)N * w->ldk + 4.0 * w->s * (double)N * w->ldk;
     const int t = zt_timer_begin(p, ZT_KERNEL_SPLIT, bytes, bytes, s);
     split_rows2_kernel<<<2 * N, 256, 0, s>>>(r1, r2, N);
     zt_timer_end(p, t, s);
@@ -1344,8 +1344,8 @@ int zt_split_operands2(zt_plan* p, const double2* X1, const double2* X2, cudaStr
     return ZT_OK;
 }
 
-static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, SplitArgs& a,
-                         int* ngroups_out) {
+static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, int keep_a,
+                         SplitArgs& a, int* ngroups_out) {
     zt_split_ws* w = p->split;
     const int N = p->N;
     a.N = N;
@@ -1375,8 +1375,8 @@ static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int l
     a.ngroups = ngroups;
     a.tickets = nullptr;
     if (w->skip_zero) {   // the occupancy this product reads is cleared by its last CTA
-        a.clr_a = w->occA;
-        a.clr_a_n = w->ngA * w->nkb;
+        a.clr_a = keep_a ? nullptr : w->occA;   // keep_a: the X' planes serve a later product too
+        a.clr_a_n = keep_a ? 0 : w->ngA * w->nkb;
         a.clr_b = w->occB[b_slot];
         a.clr_b_n = w->ngB * w->nkb;
         a.done = w->tickets + 1;
@@ -1389,12 +1389,12 @@ static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int l
     *ngroups_out = ngroups;
 }
 
-int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, GemmEntry* out,
-                        int* ctas) {
+int zt_split_gemm_entry(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, int keep_a,
+                        GemmEntry* out, int* ctas) {
     zt_split_ws* w = p->split;
     if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
     int ngroups;
-    product_args(p, b_slot, C, alpha, lower_only, out->a, &ngroups);
+    product_args(p, b_slot, C, alpha, lower_only, keep_a, out->a, &ngroups);
     out->tmA = w->tmA;
     out->tmB = w->tmB[b_slot];
     *ctas = ngroups;
@@ -1408,13 +1408,14 @@ int zt_split_gemm_grouped(const GemmEntry* tab, const int* offs, int n, int tota
     return ZT_OK;
 }
 
-int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, cudaStream_t s, int gate) {
+int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower_only, int keep_a, cudaStream_t s,
+                     int gate) {
     zt_split_ws* w = p->split;
     if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
     const int N = p->N;
     SplitArgs a;
     int ngroups;
-    product_args(p, b_slot, C, alpha, lower_only, a, &ngroups);
+    product_args(p, b_slot, C, alpha, lower_only, keep_a, a, &ngroups);
     a.gate = gate;
     a.units = p->timing ? p->d_units : nullptr;   // issued work is counted on the device
     const double alg = lower_only ? 4.0 * N * (double)N * (N + 1.0) : 8.0 * (double)N * N * N;
@@ -1445,7 +1446,7 @@ int zt_launch_zgemm_split(zt_plan* p, const double2* X, const double2* Y, double
     int rc;
     if ((rc = zt_split_operand(p, X, 1, -1, s, gate))) return rc;
     if ((rc = zt_split_operand(p, Y, 0, 0, s, gate))) return rc;
-    return zt_split_product(p, 0, C, alpha, lower_only, s, gate);
+    return zt_split_product(p, 0, C, alpha, lower_only, 0, s, gate);
 }
 
 // ---------------------------------------------------------------------------
