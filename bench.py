@@ -208,11 +208,12 @@ def _tuning(args, N):
         timed = sorted((t for t in res["trials"] if "ms" in t), key=lambda t: t["ms"])
         return dict(res["tuning"]), {"mode": "auto", "target_rel_err": args.tune_target,
                                      "probe_rel_err": res["rel_err"], "probe_ms": res["ms"],
+                                     "second_product": res.get("gemm2"),
                                      "candidates": len(res["trials"]),
                                      "fastest": [{**t["tuning"], "ms": round(t["ms"], 3),
                                                   "rel_err": t["rel_err"]} for t in timed[:6]]}
     tun = dict(slices=args.slices, digit_bits=args.digit_bits, exact_groups=args.exact_groups,
-               tile_order=args.tile_order, no_persistent=args.no_persistent)
+               tile_order=args.tile_order, no_persistent=args.no_persistent, slices2=args.slices2)
     return tun, {"mode": "fixed"}
 
 
@@ -643,9 +644,13 @@ def run_gpu(args):
     _log("done")
     if rank != 0:
         return 0
-    pairs = tun["slices"] * (tun["slices"] + 1) / 2
-    # dense equivalent: every digit pair on every computed tile of the timed launches
-    dense_work = pairs * prod["work_alg"] if prod["work_alg"] else None
+    s1 = tun["slices"]
+    s2 = tun.get("slices2") or s1
+    pairs = {"first": s1 * (s1 + 1) / 2, "second": s2 * (s2 + 1) / 2}
+    # dense equivalent: every digit pair on every computed tile of the timed launches (the
+    # full products are 8 N^3 of the 8 N^3 + 4 N^2 (N + 1) algorithmic flops of a sweep)
+    f1 = 8.0 * N ** 3 / (8.0 * N ** 3 + 4.0 * N * N * (N + 1.0))
+    dense_work = (pairs["first"] * f1 + pairs["second"] * (1 - f1)) * prod["work_alg"] if prod["work_alg"] else None
     achieved = prod["work"] / (prod["total_ms"] / 1e3) / 1e12 if prod["total_ms"] else None
     peak = peaks["bf16_tflops_sustained"]
     src = open(os.path.join(ROOT, "paper_2206_05466_gb300", "csrc", "zt_split.cu"), "rb").read()
@@ -656,7 +661,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 (products: bf16 digit slices, fp32/int64 accumulate)",
         "data": "synthetic",
         "config": {"workload": f"IsoMP N={N} h={H} seeded W0 (decay 2, spectral norm 1), tol {TOL} Frobenius, "
-                               f"maxit {MAXIT}, split-precision products s={tun['slices']} beta={tun['digit_bits']}",
+                               f"maxit {MAXIT}, split-precision products s={tun['slices']} beta={tun['digit_bits']}"
+                               f" (second product s={tun.get('slices2') or tun['slices']})",
                    "N": N, "h": H, "precision": "split", "tuning": tun, "tuning_source": tune_info,
                    "parallelism": f"replicas x{ws}",
                    "l2": "working set > L2 (digit planes ~1.4 GB + 6 matrices of 268 MB)"},
@@ -718,6 +724,7 @@ def main():
     ap.add_argument("--tune-target", type=float, default=1e-11)
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--digit-bits", type=int, default=8)
+    ap.add_argument("--slices2", type=int, default=0, help="fixed tuning: digits of the second product (0: slices)")
     ap.add_argument("--exact-groups", type=int, default=2)
     ap.add_argument("--tile-order", type=int, default=0)
     ap.add_argument("--no-persistent", type=int, default=0, help="fixed tuning: 1 = one tile per CTA")

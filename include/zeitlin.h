@@ -69,6 +69,12 @@ typedef struct zt_tuning {
     int debug_stall_loads; /* SPLIT, testing only: k > 0 stops the product kernel's operand
                             loads after k - 1 of them, so that its bounded waits run out and
                             the call returns ZT_ETIMEOUT (default 0: off) */
+    int slices2;         /* SPLIT: digit slices of the second product of a sweep, B = Pt A^H
+                            (Sec. 3.1), 2..slices; 0 (default) = slices.  B enters the update
+                            (Eq. 9) and the final assembly (Eq. 8) scaled by h^2/4, so it needs
+                            fewer digits than A = Pt Wt for the same error in W: Pt's digit
+                            planes are truncated to their leading slices2 digits and A is split
+                            into slices2 digits */
 } zt_tuning;
 
 typedef struct zt_step_stats {

@@ -5,9 +5,18 @@ For a matrix size N it times each candidate tuning on seeded probe operands
 seeded su(N) recipe) through the C ABI, measures
 the candidate's error against a reference product with more digits (8 slices
 of 7 bits, ~2^-55 relative), times whole IsoMP steps of the workload for the
-candidates within `target` (relative Frobenius error), and keeps the fastest.  Choices are cached as JSON keyed by
-(N, GPU name) in $ZEITLIN_TUNE_CACHE (default ~/.cache/zeitlin_gb300/tune.json).
-All arithmetic runs in the library's kernels; this module only orchestrates.
+candidates within `target` (relative Frobenius error), and keeps the fastest.
+
+The second product of a sweep, B = Pt A^H, enters W (Eqs. 8-9) scaled by h^2/4
+where A enters scaled by h/2, so it is given the error that makes its share of
+the error in W no larger than A's: (h^2/4) e_B |B| <= (h/2) target |A|, i.e.
+e_B <= target (2/h) |A|/|B| (Frobenius norms of the probe's A and B).  Its digit
+count (slices2) is the smallest whose measured error on the probe's second
+product meets that bound.
+
+Choices are cached as JSON keyed by (N, GPU name) in $ZEITLIN_TUNE_CACHE
+(default ~/.cache/zeitlin_gb300/tune.json).  All arithmetic runs in the
+library's kernels; this module only orchestrates.
 """
 from __future__ import annotations
 
@@ -39,6 +48,42 @@ def load_cached(N):
         return json.load(open(_cache_path())).get(_key(N))
     except Exception:
         return None
+
+
+def _second_product_digits(N, tuning, X, Y, target, h):
+    """Smallest digit count of the second product B = Pt A^H within its error share (module doc)."""
+    import numpy as np
+    import torch
+
+    from . import zeitlin as z
+
+    ref_plan = z.Plan(N, z.PRECISION_SPLIT, **REFERENCE)
+    A = torch.empty_like(X)
+    z.zt_zgemm_skew(ref_plan, X, Y, A)   # A = Pt W
+    Bm = torch.empty_like(X)
+    z.zt_zgemm_skew(ref_plan, X, A, Bm)   # -X conj(A)^T = -Pt A^H = -B (A is not skew-Hermitian)
+    torch.cuda.synchronize()
+    ref_plan.close()
+    ref_h = Bm.cpu().numpy()
+    nB = float(np.linalg.norm(ref_h))
+    nA = float(np.linalg.norm(A.cpu().numpy()))
+    bound = target * (2.0 / h) * nA / nB if nB > 0 else float("inf")
+    s, beta, eg = tuning["slices"], tuning["digit_bits"], tuning["exact_groups"]
+    errs, choice = {}, s
+    C = torch.empty_like(X)
+    for s2 in range(s, 2, -1):
+        # measured as a product of s2-digit splits of Pt and A: a fresh split rounds where
+        # the truncated planes of Pt cut off, an error of the same size
+        plan = z.Plan(N, z.PRECISION_SPLIT, slices=s2, digit_bits=beta, exact_groups=min(eg, s2))
+        z.zt_zgemm_skew(plan, X, A, C)
+        torch.cuda.synchronize()
+        plan.close()
+        errs[s2] = float(np.linalg.norm(C.cpu().numpy() - ref_h)) / nB
+        if errs[s2] > bound:
+            break
+        choice = s2
+    return {"slices2": choice, "bound": bound, "rel_err": errs.get(choice), "errors": errs,
+            "norm_ratio_A_over_B": nA / nB if nB > 0 else None, "h": h}
 
 
 def autotune(N: int, target: float = 1e-11, candidates=None, reps: int = 3, use_cache: bool = True,
@@ -107,7 +152,10 @@ def autotune(N: int, target: float = 1e-11, candidates=None, reps: int = 3, use_
     if not ok:
         raise RuntimeError(f"no candidate meets relative error {target}: {trials}")
     best = min(ok, key=lambda t: t["ms"])
-    out = {"tuning": best["tuning"], "rel_err": best["rel_err"], "ms": best["ms"], "target": target,
+    tuning = dict(best["tuning"])
+    gemm2 = _second_product_digits(N, tuning, X, Y, target, step_h)
+    tuning["slices2"] = gemm2["slices2"]
+    out = {"tuning": tuning, "rel_err": best["rel_err"], "ms": best["ms"], "target": target, "gemm2": gemm2,
            "trials": trials}
     if use_cache:
         path = _cache_path()

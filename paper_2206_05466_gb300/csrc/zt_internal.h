@@ -94,14 +94,14 @@ struct zt_plan {
     double* partials = nullptr;
     double* cas_part = nullptr;   // Casimir partial sums [CTAs + 1][8]
     int npartials = 0;
-    // Stream solve by bands of 32 diagonals and segments of 32 rows (zt_solve.cu).
+    // Stream solve by bands of 32 diagonals and segments of 16 rows (zt_solve.cu).
     // Per element, packed lower-triangular row-major (entry (r, c) at zt_tri(r, c)):
     double* fac_l = nullptr;   // LDL^T multiplier, negated: -l_i (l_0 = 0)
     double* fac_nd = nullptr;  // -1 / d_i (0 for the dropped m = 0 row)
     double* fac_f = nullptr;   // F_i: the segment's response to its forward inflow
     double* fac_h = nullptr;   // H_i: the segment's response to its backward inflow
     // Per (segment k, diagonal m), [K][N] (coalesced over m):
-    int nseg = 0;              // K = ceil(N / 32)
+    int nseg = 0;              // K = 2 ceil(N / 32) segments of 16 rows
     double2* seg_z = nullptr;  // local forward sweep at the segment's last position
     double2* seg_x = nullptr;  // local backward sweep at the segment's first position
     double* seg_g = nullptr;   // G at the last position (constant)
@@ -187,6 +187,7 @@ struct SplitRowsArgs { // digit splitting of one operand (zt_split.cu)
 
 struct SplitArgs {     // tcgen05 split product (zt_split.cu)
     int N, s, beta, ldk, Mpad, Npad, u, exact_groups, ntn, lower_only;
+    int s_occA;   // digits X' was split into (the occupancy's reference; s <= s_occA)
     // digit occupancy per (row group, K block): s - (first nonzero digit), 0 = all zero;
     // NULL disables zero-unit skipping
     const int* occA;

@@ -581,6 +581,7 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         else if (t.no_persistent != 0 && t.no_persistent != 1) bad = "no_persistent must be 0 or 1";
         else if (t.wait_us < 1 || t.wait_us > 60000000) bad = "wait_us outside [1, 60000000]";
         else if (t.debug_stall_loads < 0) bad = "debug_stall_loads must be >= 0";
+        else if (t.slices2 != 0 && (t.slices2 < 2 || t.slices2 > t.slices)) bad = "slices2 outside [2, slices]";
         if (bad) {
             delete p;
             return zt_fail(ZT_EINVAL, "zt_plan_create: %s", bad);

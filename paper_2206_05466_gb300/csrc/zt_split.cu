@@ -80,6 +80,8 @@ constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) |
 
 struct zt_split_ws {
     int s = 7, beta = 7, exact_groups = 4;
+    int s2 = 7, u2 = 0;                           // digits of B'^T slot 1 and of the products that
+                                                  // read it; accumulator shift for s2 digits
     unsigned long long wait_ns = 2000000000ull;   // limit of one mbarrier wait
     int stall_loads = 0;                          // testing only (zt_tuning.debug_stall_loads)
     int ldk = 0, Mpad = 0, Npad = 0, u = 0;
@@ -497,7 +499,7 @@ __device__ __forceinline__ void fill_slot_warp(const SplitArgs& a, TileSlot& ts,
         const int kb = kb0 + lane;
         int c = 2 * MAX_S;   // no unit
         if (kb < nkb) {
-            const int fa = a.occA ? a.s - a.occA[(size_t)tig * nkb + kb] : 0;
+            const int fa = a.occA ? a.s_occA - a.occA[(size_t)tig * nkb + kb] : 0;   // may exceed a.s
             const int fb = a.occB ? a.s - a.occB[(size_t)tjg * nkb + kb] : 0;
             ts.fa[kb] = (uint8_t)fa;
             ts.fb[kb] = (uint8_t)fb;
@@ -1140,6 +1142,8 @@ int zt_split_create(zt_plan* p) {
     if (beta < 6 || beta > 8) return zt_fail(ZT_EINVAL, "digit_bits=%d outside [6, 8]", beta);
     if (eg < 1 || eg > s) return zt_fail(ZT_EINVAL, "exact_groups=%d outside [1, slices]", eg);
     if (s * beta > 62) return zt_fail(ZT_EINVAL, "slices*digit_bits must be <= 62");
+    if (p->tun.slices2 != 0 && (p->tun.slices2 < 2 || p->tun.slices2 > s))
+        return zt_fail(ZT_EINVAL, "slices2=%d outside [2, slices]", p->tun.slices2);
     zt_split_ws* w = new (std::nothrow) zt_split_ws();
     if (!w) return zt_fail(ZT_ENOMEM, "host allocation failed");
     p->split = w;
@@ -1152,16 +1156,19 @@ int zt_split_create(zt_plan* p) {
     w->ldk = round_up(2 * N, BK);
     w->Mpad = round_up(N, BM);
     w->Npad = round_up(2 * N, BN);
-    // smallest u >= 0 with the worst-case int64 accumulator below 2^62
-    {
+    // smallest u >= 0 with the worst-case int64 accumulator below 2^62 (for s and s2 digits)
+    auto shift_for = [&](int sd) {
         const double R = std::ldexp(1.0, beta);
         double bound = 0.0;
-        for (int g = 0; g < s; ++g) bound += (g + 1) * std::pow(R, s - 1 - g);
+        for (int g = 0; g < sd; ++g) bound += (g + 1) * std::pow(R, sd - 1 - g);
         bound *= (double)w->ldk * std::ldexp(1.0, 2 * beta - 2);
         int u = 0;
         while (bound >= std::ldexp(1.0, 62 + u)) ++u;
-        w->u = u;
-    }
+        return u;
+    };
+    w->u = shift_for(s);
+    w->s2 = p->tun.slices2 ? p->tun.slices2 : s;
+    w->u2 = shift_for(w->s2);
     cudaStream_t cs = p->mstream;   // the plan's private stream (synchronised at the end of plan creation)
     const size_t szA = (size_t)s * w->Mpad * w->ldk * sizeof(__nv_bfloat16);
     const size_t szB = (size_t)s * w->Npad * w->ldk * sizeof(__nv_bfloat16);
@@ -1268,9 +1275,12 @@ int zt_split_rows_args(zt_plan* p, const double2* X, int to_a, int b_slot, Split
     zt_split_ws* w = p->split;
     if (!w) return zt_fail(ZT_EINVAL, "plan has no split-precision workspace");
     SplitRowsArgs& a = *out;
+    // B'^T slot 1 holds s2 digits; a split into X' and slot 1 at once needs s2 == s
+    if (b_slot == 1 && to_a && w->s2 != w->s)
+        return zt_fail(ZT_EINVAL, "split into X' and slot 1 at once needs slices2 == slices");
     a.X = X;
     a.N = p->N;
-    a.s = w->s;
+    a.s = b_slot == 1 ? w->s2 : w->s;
     a.beta = w->beta;
     a.ldk = w->ldk;
     a.dA = to_a ? w->dA : nullptr;
@@ -1349,12 +1359,15 @@ static void product_args(zt_plan* p, int b_slot, double2* C, double alpha, int l
     zt_split_ws* w = p->split;
     const int N = p->N;
     a.N = N;
-    a.s = w->s;
+    // a product with slot 1 takes s2 digit groups: the leading s2 planes of X' (a
+    // plane's weight does not depend on how many planes follow it) and slot 1's s2
+    a.s = b_slot == 1 ? w->s2 : w->s;
+    a.s_occA = w->s;
     a.beta = w->beta;
     a.ldk = w->ldk;
     a.Mpad = w->Mpad;
     a.Npad = w->Npad;
-    a.u = w->u;
+    a.u = b_slot == 1 ? w->u2 : w->u;
     a.exact_groups = w->exact_groups;
     a.ntn = w->Npad / BN;
     a.lower_only = lower_only;
@@ -1563,6 +1576,7 @@ extern "C" int zt_zgemm_skew_split_noalloc(int N, const double* X, const double*
     SplitArgs a;
     a.N = N;
     a.s = NA_S;
+    a.s_occA = NA_S;
     a.beta = NA_BETA;
     a.ldk = NA_LDK;
     a.Mpad = NA_MPAD;

@@ -20,8 +20,10 @@ device until its last step.  Each class is advanced by its own worker thread on
 its own CUDA stream, one batched step (grouped kernels over all the class's
 jobs) per iteration; jobs admitted while others run join their class's batch
 at its next step (when several classes are allowed, they run concurrently).
-A class's batch is rebuilt only when its resident set changes.  All arithmetic
-runs in the library's kernels; this module only schedules.
+A class's batch is rebuilt only when its resident set changes, and the new
+batch is built on a helper thread while the current one keeps stepping: the
+worker swaps it in between two steps, so a rebuild does not pause the class.
+All arithmetic runs in the library's kernels; this module only schedules.
 
 Reported: per-step latency of resident jobs (time between a job's consecutive
 completed steps; p50/p99, overall and per class), aggregate job-steps/s,
@@ -30,6 +32,7 @@ queueing delay (arrival to admission) and the peak of admitted footprint.
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
 import threading
 import time
@@ -63,6 +66,19 @@ class _Resident:
 
 def _pct(xs, q):
     return float(np.percentile(np.asarray(xs) * 1e3, q)) if len(xs) else None
+
+
+def _step_breakdown(step_log):
+    """Batched-step times per class and tag: count, p50 and p99 (ms)."""
+    out = {}
+    for cls in sorted({c for c, _, _ in step_log}):
+        name = f"N={cls[0]},{'split' if cls[1] == z.PRECISION_SPLIT else 'fp64'}"
+        rows = [(dt, tags) for c, dt, tags in step_log if c == cls]
+        groups = {"all": [dt for dt, _ in rows], "untagged": [dt for dt, t in rows if not t]}
+        for tag in ("swap", "admission", "more_sweeps"):
+            groups[tag] = [dt for dt, t in rows if tag in t]
+        out[name] = {k: {"n": len(v), "p50": _pct(v, 50), "p99": _pct(v, 99)} for k, v in groups.items() if v}
+    return out
 
 
 def solo_step_s(solo, cls, n):
@@ -203,6 +219,7 @@ class Server:
             return low
         lock = threading.Lock()
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
+        pending_arrivals = pending   # (the workers' name for it)
         queues: dict[tuple, collections.deque] = collections.defaultdict(collections.deque)
         ema: dict[tuple, float] = {}            # moving average of the class's step time (s)
         active_since: dict[tuple, float] = {}   # start of the class's current session (s)
@@ -215,6 +232,11 @@ class Server:
         lat: dict[tuple, list] = collections.defaultdict(list)
         max_res: dict[tuple, int] = collections.defaultdict(int)   # peak resident jobs per class
         qdelay, results, errors, admit_times = [], {}, [], []
+        # per batched step: (class, seconds, tags) -- tags: the first step after a batch swap,
+        # an admission (plan creation and upload) overlapping the step, more sweeps than the
+        # class's previous step (a second convergence check inside the step)
+        step_log = []
+        admitting = [0]
         pinned = {}
         st = {"used": 0, "peak": 0, "steps": 0, "completed": 0, "batched": 0, "stop": False}
         t0 = clock()
@@ -222,62 +244,95 @@ class Server:
         def worker(cls):
             torch.cuda.set_device(dev)
             stream = torch.cuda.Stream(priority=class_priority(cls[0]))
+            builder = concurrent.futures.ThreadPoolExecutor(max_workers=1)
             batch, order = None, []
+            pending = None       # (order, future of the batch being built for that order)
+            prev_max = 0         # most sweeps any job took in the previous step
+            want = False         # the resident set changed since the last build was started
             since = 0   # batched steps since the last rebuild
+
+            def build(ord_, res_):
+                torch.cuda.set_device(dev)
+                b = z.Batch([res_[j].plan for j in ord_], [res_[j].W for j in ord_], [res_[j].job.h for j in ord_])
+                if self.graph:
+                    b.set_graph(True)
+                return b
+
+            def swap_in(new_order, new_batch):
+                # the old batch is idle (its last step synchronised); its finished jobs
+                # that the new batch leaves out are released now
+                nonlocal batch, order, since
+                if batch is not None:
+                    batch.close()
+                keep = set(new_order)
+                with lock:
+                    gone = [r for j, r in classes[cls].items() if j not in keep and r.done]
+                    for r in gone:
+                        del classes[cls][r.job.jid]
+                        st["used"] -= r.bytes
+                for r in gone:
+                    r.plan.close()
+                batch, order, since = new_batch, new_order, 0
+
             try:
                 while True:
                     with lock:
                         res = dict(classes[cls])
-                        changed = dirty[cls]
+                        if dirty[cls]:
+                            want = True
                         dirty[cls] = False
                         stop = st["stop"]
                     if stop:   # time limit: leave; resident jobs are released by the caller
+                        if pending is not None:
+                            pb = pending[1].result()
+                            pb.close()
                         if batch is not None:
                             batch.close()
+                        builder.shutdown()
                         return
-                    if not res:
-                        if batch is not None:
-                            batch.close()
-                            batch = None
-                        if not pending and not queues[cls]:
+                    live = {j: r for j, r in res.items() if not r.done}
+                    if pending is not None and pending[1].done():
+                        new_order, fut = pending
+                        pending = None
+                        swap_in(new_order, fut.result())
+                        continue
+                    if not live:
+                        # nothing left to step: release everything at once
+                        if pending is not None:
+                            pending[1].result().close()
+                            pending = None
+                        if batch is not None or res:
+                            swap_in([], None)
+                        want = False
+                        if not pending_jobs(cls):
                             with lock:
-                                if not classes[cls] and not pending and not queues[cls]:
+                                if not classes[cls] and not pending_jobs(cls):
+                                    builder.shutdown()
                                     return
                         time.sleep(0.001)
                         continue
-                    # Finished jobs leave the batch at the next rebuild: at once if nothing
-                    # else is left, otherwise together with the next admission, once a
-                    # quarter of the batch has finished, or after 32 steps (one rebuild
-                    # for several changes keeps rebuild pauses out of most steps).
-                    zombies = [r for r in res.values() if r.done]
-                    live = {j: r for j, r in res.items() if not r.done}
-                    if zombies and (changed or not live or len(zombies) * 4 >= len(res) or since >= 32):
-                        if batch is not None:
-                            batch.close()
-                            batch = None
-                        for r in zombies:
-                            r.plan.close()
-                        with lock:
-                            for r in zombies:
-                                del classes[cls][r.job.jid]
-                                st["used"] -= r.bytes
-                        res = live
-                        changed = True
-                        if not res:
-                            continue
-                    if changed or batch is None:
-                        if batch is not None:
-                            batch.close()
-                        order = sorted(res)
-                        batch = z.Batch([res[j].plan for j in order], [res[j].W for j in order],
-                                        [res[j].job.h for j in order])
-                        if self.graph:
-                            batch.set_graph(True)
-                        since = 0
+                    # Finished jobs leave the batch at the next rebuild: together with the next
+                    # admission, once a quarter of the batch has finished, or after 32 steps.
+                    nz = sum(1 for j in order if res.get(j) is not None and res[j].done)
+                    if nz and (nz * 4 >= len(order) or since >= 32):
+                        want = True
+                    if want and pending is None:
+                        new_order = sorted(live)
+                        want = False
+                        if batch is None:   # nothing to step meanwhile: build here
+                            swap_in(new_order, build(new_order, res))
+                        else:
+                            pending = (new_order, builder.submit(build, new_order, res))
                     t_start = clock() - t0
+                    adm0 = admitting[0]
                     with torch.cuda.stream(stream):
-                        batch.step(self.tol, self.maxit, stream=stream, allow_not_converged=True)
+                        _, sts = batch.step(self.tol, self.maxit, stream=stream, allow_not_converged=True)
                     t_done = clock() - t0
+                    mx = max(x["iters"] for x in sts)
+                    tags = (("swap",) if since == 0 else ()) + (("admission",) if adm0 or admitting[0] else ()) + \
+                        (("more_sweeps",) if prev_max and mx > prev_max else ())
+                    prev_max = mx
+                    step_log.append((cls, t_done - t_start, tags))
                     since += 1
                     finished = []
                     with lock:
@@ -306,6 +361,9 @@ class Server:
                 errors.append(repr(e))
                 with lock:
                     st["stop"] = True
+
+        def pending_jobs(cls):
+            return bool(pending_arrivals) or bool(queues[cls])
 
         while True:
             now = clock() - t0
@@ -340,6 +398,7 @@ class Server:
                     break
                 need = z.plan_estimate_bytes(job.N, job.precision)
                 ta = clock()
+                admitting[0] += 1
                 plan = z.Plan(job.N, job.precision)
                 tb = clock()
                 src = pinned.get(id(job.W0))   # initial states shared by jobs are pinned once
@@ -349,6 +408,7 @@ class Server:
                 with torch.cuda.stream(upload):
                     W = src.to("cuda", non_blocking=True)
                 upload.synchronize()
+                admitting[0] -= 1
                 admit_times.append((tb - ta, clock() - tb))
                 t_adm = clock() - t0
                 cls = (job.N, job.precision)
@@ -408,5 +468,6 @@ class Server:
             "peak_admitted_bytes": st["peak"],
             "admit_plan_ms_mean": float(np.mean([a for a, _ in admit_times]) * 1e3) if admit_times else None,
             "admit_upload_ms_mean": float(np.mean([b for _, b in admit_times]) * 1e3) if admit_times else None,
+            "step_time_ms_by_tag": _step_breakdown(step_log),
             "results": results,
         }

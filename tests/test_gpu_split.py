@@ -207,3 +207,63 @@ def test_launch_orders_give_identical_products(order):
         want, _ = oracle.isomp_step(W, 0.01)
         assert _rel(Wd.cpu().numpy(), want) <= 1e-10
         plan.close()
+
+
+@pytest.mark.parametrize("s2", [3, 4, 5])
+def test_second_product_digits_step_matches_oracle(s2):
+    # B = Pt A^H with fewer digits (slices2): every step still within the split
+    # tolerance of the FP64 oracle (B enters W scaled by h^2/4)
+    N, h = 160, 0.01
+    W0 = vorticity_w0(N, seed=7)
+    plan = z.Plan(N, z.PRECISION_SPLIT, slices=6, digit_bits=8, exact_groups=2, slices2=s2)
+    Wd = _cuda(W0)
+    Wo = W0.copy()
+    for n in range(5):
+        info = z.isomp_step(plan, Wd, h)
+        Wo, st = oracle.isomp_step(Wo, h)
+        assert info["converged"] and abs(info["iters"] - st.iters) <= 1
+        err = _rel(Wd.cpu().numpy(), Wo)
+        assert err <= 1e-10, (s2, n, err)
+    plan.close()
+
+
+def test_second_product_digits_batched_equals_single():
+    N, h = 96, 0.01
+    tun = dict(slices=6, digit_bits=8, exact_groups=2, slices2=4)
+    W0s = [vorticity_w0(N, seed=30 + k) for k in range(3)]
+    single = []
+    for W0 in W0s:
+        p = z.Plan(N, z.PRECISION_SPLIT, **tun)
+        W = _cuda(W0)
+        for _ in range(2):
+            z.isomp_step(p, W, h)
+        single.append(W.cpu().numpy())
+        p.close()
+    plans = [z.Plan(N, z.PRECISION_SPLIT, **tun) for _ in W0s]
+    Ws = [_cuda(W0) for W0 in W0s]
+    b = z.Batch(plans, Ws, [h] * len(W0s))
+    for _ in range(2):
+        rc, _ = b.step()
+        assert rc == z.ZT_OK
+    for W, want in zip(Ws, single):
+        assert np.array_equal(W.cpu().numpy(), want)
+    b.close()
+    for p in plans:
+        p.close()
+
+
+def test_second_product_digits_error_bound():
+    # the leading s2 digits of each operand: a product error near 2^-(beta s2) of the row scales
+    N = 256
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+    Y = vorticity_w0(N, seed=5)
+    want = X @ Y
+    prev = None
+    for s in (3, 4, 5, 6):
+        got = _gemm(z.Plan(N, z.PRECISION_SPLIT, slices=s, digit_bits=8, exact_groups=2), X, Y)
+        e = _rel(got, want)
+        assert e < 2.0 ** (-8 * s + 12), (s, e)
+        if prev is not None:
+            assert e < prev / 16, (s, e, prev)
+        prev = e
