@@ -11,8 +11,10 @@ comparable step time, put the lighter one's p99 step latency at 5-8 times its
 solo step time; a setting allows more, and then only classes whose solo step
 times are within a factor 8 share the device), and a
 resident class takes another job only after it completed a step with its
-current set, while its measured step time stays within twice its solo step time
-and its solo step time with one more job stays below an absolute target; after
+current set, while its measured step time stays below 0.8 x 2 times its solo
+step time with one job (a batch's step time grows with its size; past a few
+dozen small jobs the device is full and larger batches only add latency) and
+its solo step time with one more job stays below an absolute target; after
 a session of 20 s a class stops taking jobs while other classes wait, so that
 the resident classes rotate.  Under overload the queues absorb the excess
 (reported as queueing delay).  An admitted job's state stays resident on the
@@ -34,6 +36,7 @@ from __future__ import annotations
 import collections
 import concurrent.futures
 import dataclasses
+import gc
 import threading
 import time
 
@@ -75,7 +78,7 @@ def _step_breakdown(step_log):
         name = f"N={cls[0]},{'split' if cls[1] == z.PRECISION_SPLIT else 'fp64'}"
         rows = [(dt, tags) for c, dt, tags in step_log if c == cls]
         groups = {"all": [dt for dt, _ in rows], "untagged": [dt for dt, t in rows if not t]}
-        for tag in ("swap", "admission", "more_sweeps"):
+        for tag in ("swap", "admission", "more_sweeps", "gc", "building"):
             groups[tag] = [dt for dt, t in rows if tag in t]
         out[name] = {k: {"n": len(v), "p50": _pct(v, 50), "p99": _pct(v, 99)} for k, v in groups.items() if v}
     return out
@@ -88,7 +91,7 @@ def solo_step_s(solo, cls, n):
     return t1 + per * max(0, n - 1)
 
 
-def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate, factor=2.0,
+def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate, factor=2.0, headroom=0.8,
                    max_active=2, target=None, active_since=None, now=0.0, session_s=None, compat=None):
     """The class whose head job is admitted next, or None (the admission policy).
 
@@ -101,11 +104,15 @@ def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate,
       * Memory: the head job's plan footprint estimate(N, precision) must fit the
         remaining budget, unless nothing at all is resident.
       * Latency: an active class admits another job only after it completed a step
-        with its current set (stepped), while its measured step time ema[cls] is
-        within `factor` times its calibrated solo step time with that set
-        (solo_step_s), and while the solo step time with one more job stays within
-        the absolute `target` (seconds).  With neither (both None) admission is by
-        footprint and the number of active classes alone.
+        with its current set (stepped), while its measured step time ema[cls] stays
+        below `headroom` x `factor` times its solo step time with one job (the
+        headroom leaves room for the jobs of the next admission burst, so that the
+        class's steps stay within `factor` times that solo time), and while the
+        calibrated solo step time with one more job stays within the absolute
+        `target` (seconds).  (Measured: a batch's step time grows with its size, and
+        past a few dozen small jobs the device is full, so larger batches only add
+        latency.)  With neither (both None) admission is by footprint and the number
+        of active classes alone.
       * Sessions: an active class that has been active for more than session_s
         seconds (active_since[cls]) admits no further job while a class that is not
         active has jobs waiting, so that the active classes drain and free their
@@ -133,7 +140,7 @@ def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate,
         if factor is not None or target is not None:
             if not stepped.get(cls):
                 continue
-            if factor is not None and (cls not in ema or ema[cls] > factor * solo_step_s(solo, cls, n)):
+            if factor is not None and (cls not in ema or ema[cls] > headroom * factor * solo_step_s(solo, cls, 1)):
                 continue
             if target is not None and solo_step_s(solo, cls, n + 1) > target:
                 continue
@@ -166,6 +173,8 @@ class Server:
         self.session_s = session_s
         self.compat = compat
         self.burst = max(1, int(burst))
+        self.headroom = 0.8
+        self.step_series = None   # a list here receives (class, start s, seconds, jobs, sweeps, tags) per step
 
     def calibrate(self, classes, W0s, h=0.01, reps=2):
         """Solo step time of each class (N, precision), alone on the device: batched steps
@@ -237,6 +246,12 @@ class Server:
         # class's previous step (a second convergence check inside the step)
         step_log = []
         admitting = [0]
+        gc_runs = [0]   # garbage collections started so far (any thread)
+
+        def _gc_cb(phase, info):
+            if phase == "start":
+                gc_runs[0] += 1
+        gc.callbacks.append(_gc_cb)
         pinned = {}
         st = {"used": 0, "peak": 0, "steps": 0, "completed": 0, "batched": 0, "stop": False}
         t0 = clock()
@@ -324,15 +339,18 @@ class Server:
                         else:
                             pending = (new_order, builder.submit(build, new_order, res))
                     t_start = clock() - t0
-                    adm0 = admitting[0]
+                    adm0, gc0, bld0 = admitting[0], gc_runs[0], pending is not None
                     with torch.cuda.stream(stream):
                         _, sts = batch.step(self.tol, self.maxit, stream=stream, allow_not_converged=True)
                     t_done = clock() - t0
                     mx = max(x["iters"] for x in sts)
                     tags = (("swap",) if since == 0 else ()) + (("admission",) if adm0 or admitting[0] else ()) + \
-                        (("more_sweeps",) if prev_max and mx > prev_max else ())
+                        (("more_sweeps",) if prev_max and mx > prev_max else ()) + \
+                        (("gc",) if gc_runs[0] != gc0 else ()) + (("building",) if bld0 else ())
                     prev_max = mx
                     step_log.append((cls, t_done - t_start, tags))
+                    if self.step_series is not None:
+                        self.step_series.append((cls, t_start, t_done - t_start, len(order), mx, tags))
                     since += 1
                     finished = []
                     with lock:
@@ -383,6 +401,7 @@ class Server:
                 with lock:
                     cls = next_admission(queues, {c: len(v) for c, v in classes.items()}, st["used"], self.budget,
                                          stepped, ema, solo, z.plan_estimate_bytes, factor=self.factor,
+                                         headroom=self.headroom,
                                          max_active=self.max_active, target=self.target,
                                          active_since=active_since, now=clock() - t0, session_s=self.session_s,
                                          compat=self.compat)
@@ -432,6 +451,7 @@ class Server:
                 time.sleep(0.001)
         for th in list(workers.values()):
             th.join()
+        gc.callbacks.remove(_gc_cb)
         wall = clock() - t0
         for c in classes.values():
             for r in c.values():
@@ -453,15 +473,15 @@ class Server:
             "per_class": {f"N={k[0]},{'split' if k[1] == z.PRECISION_SPLIT else 'fp64'}":
                           {"job_steps": len(v), "p50_ms": _pct(v, 50), "p99_ms": _pct(v, 99),
                            "max_resident": max_res[k],
-                           "solo_ms_at_mean_resident": 1e3 * solo_step_s(solo, k, round(np.mean(res_hist[k])))
-                           if res_hist[k] else None,
-                           "p99_over_solo": (_pct(v, 99) / (1e3 * solo_step_s(solo, k, round(np.mean(res_hist[k])))))
-                           if res_hist[k] else None}
+                           "mean_resident": float(np.mean(res_hist[k])) if res_hist[k] else None,
+                           "solo_ms": 1e3 * solo_step_s(solo, k, 1),   # one job of the class alone on the device
+                           "p99_over_solo": _pct(v, 99) / (1e3 * solo_step_s(solo, k, 1))}
                           for k, v in lat.items()},
             "solo_calibration_ms": {f"N={k[0]},{'split' if k[1] == z.PRECISION_SPLIT else 'fp64'}":
                                     [1e3 * solo[k][0], 1e3 * solo[k][1]] for k in solo},
             "calibration_s": calib_s,
             "policy": {"max_active_classes": self.max_active, "latency_factor": self.factor,
+                       "headroom": self.headroom,
                        "target_step_ms": None if self.target is None else self.target * 1e3,
                        "session_s": self.session_s, "compat": self.compat, "burst": self.burst},
             "queue_delay_s_p50": float(np.percentile(qdelay, 50)) if qdelay else None,

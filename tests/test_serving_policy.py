@@ -61,16 +61,18 @@ def test_at_most_two_classes_resident():
 def test_latency_gates_a_resident_class():
     c = (256, 1)
     q = _q(J(256, 1, 0.0))
-    res = {c: 3}   # solo with 3 jobs: 14 ms
+    res = {c: 3}   # solo with one job: 10 ms; the gate: 0.8 x 2 x 10 ms = 16 ms
     # no completed step since the last admission: wait
-    assert pick(q, res, stepped={c: False}, ema={c: 0.014}) is None
-    # stepped, but slower than twice solo (28 ms): wait
-    assert pick(q, res, stepped={c: True}, ema={c: 0.030}) is None
-    # stepped, within twice solo: admit
-    assert pick(q, res, stepped={c: True}, ema={c: 0.020}) == c
+    assert pick(q, res, stepped={c: False}, ema={c: 0.012}) is None
+    # stepped, but the batch already takes more than the gate: wait
+    assert pick(q, res, stepped={c: True}, ema={c: 0.017}) is None
+    # stepped, below the gate: admit
+    assert pick(q, res, stepped={c: True}, ema={c: 0.013}) == c
+    # the headroom is a parameter
+    assert pick(q, res, stepped={c: True}, ema={c: 0.017}, headroom=0.9) == c
     # the absolute target bounds the solo step time with one more job (16 ms)
-    assert pick(q, res, stepped={c: True}, ema={c: 0.020}, target=0.015) is None
-    assert pick(q, res, stepped={c: True}, ema={c: 0.020}, target=0.017) == c
+    assert pick(q, res, stepped={c: True}, ema={c: 0.013}, target=0.015) is None
+    assert pick(q, res, stepped={c: True}, ema={c: 0.013}, target=0.017) == c
     # an empty class always takes its head job, whatever the target
     assert pick(_q(J(1024, 0, 0.0)), {}, target=0.001) == (1024, 0)
 
@@ -79,7 +81,7 @@ def test_sessions_rotate_classes():
     c, other = (256, 1), (512, 0)
     q = _q(J(256, 1, 5.0), J(512, 0, 1.0))
     res = {c: 2, (1024, 0): 1}   # two active classes; `other` waits for a place
-    kw = dict(stepped={c: True}, ema={c: 0.012}, session_s=20.0)
+    kw = dict(stepped={c: True}, ema={c: 0.011}, session_s=20.0)
     # within its session the active class keeps admitting
     assert pick(q, res, active_since={c: 0.0}, now=10.0, **kw) == c
     # past its session, with another class waiting, it admits no more
