@@ -413,12 +413,14 @@ __device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
     __shared__ int last;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();   // this CTA's partial and stores, before it counts as finished
-        last = atomicAdd(ua.done, 1u) == (unsigned int)ua.nctas - 1u;
+        // acq_rel at GPU scope: releases this CTA's partial and stores (ordered before
+        // it by the barrier), and the last CTA acquires every other CTA's
+        unsigned int prev;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(prev) : "l"(ua.done) : "memory");
+        last = prev == (unsigned int)ua.nctas - 1u;
     }
     __syncthreads();
     if (!last) return;
-    __threadfence();
     if (partials) converge_body(partials, ua.nctas, ua.st);
     else if (threadIdx.x == 0 && ua.st->done) ua.st->finalized = 1;   // W_{n+1} written by every CTA
     if (threadIdx.x == 0) *ua.done = 0u;

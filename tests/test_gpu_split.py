@@ -129,6 +129,10 @@ def test_autotuner_picks_an_accurate_tuning(tmp_path, monkeypatch):
     res = autotune.autotune(256, target=1e-11)
     assert res["rel_err"] <= 1e-11
     assert all("rel_err" in t for t in res["trials"])
+    # the second product's digits: within its error share, and no more than the first's
+    g2 = res["gemm2"]
+    assert 3 <= res["tuning"]["slices2"] <= res["tuning"]["slices"]
+    assert g2["errors"][res["tuning"]["slices2"]] <= g2["bound"]
     again = autotune.autotune(256, target=1e-11)   # served from the cache
     assert again["tuning"] == res["tuning"]
 
