@@ -799,31 +799,35 @@ extern "C" int zeitlin_casimirs(zt_plan* p, const double* W, double* C, void* st
 
 // One fixed-point sweep (Eq. 9): Pt = solve(Wt), A = Pt Wt,
 // B = A Pt, Wt <- W_n + h/2 (A - A^H) + h^2/4 B, residual, stop decision.
-// Pt = solve(Wt), A = Pt Wt, B = A Pt (lower half).
-static int enqueue_products(zt_plan* p, cudaStream_t s, int gate) {
+// Pt = solve(Wk), A = Pt Wk, B = A Pt (lower half), Wk the current iterate.
+static int enqueue_products(zt_plan* p, const double2* Wk, cudaStream_t s, int gate) {
     int rc;
-    if ((rc = zt_launch_stream_solve(p, p->Wt, p->P, s, gate))) return rc;
+    if ((rc = zt_launch_stream_solve(p, Wk, p->P, s, gate))) return rc;
     if (p->precision == ZT_PRECISION_SPLIT) {
         // The product kernel forms X conj(Y)^T from the X' planes (rows of X) and a
         // B'^T slot (rows of Y).  A = Pt Wt = -Pt conj(Wt)^T (Wt skew-Hermitian), and
         // B = A Pt = Pt Wt Pt is skew-Hermitian, so B = -B^H = -Pt^H A^H = Pt A^H = Pt conj(A)^T:
         // both products take Pt's X' planes, split once.  Pt into the X' planes and Wt
         // into slot 0 in one launch, then A into slot 1.
-        if ((rc = zt_split_operands2(p, p->P, p->Wt, s, gate))) return rc;
+        if ((rc = zt_split_operands2(p, p->P, Wk, s, gate))) return rc;
         if ((rc = zt_split_product(p, 0, p->A, -1.0, 0, 1, s, gate))) return rc;   // A = Pt Wt
         if ((rc = zt_split_operand(p, p->A, 0, 1, s, gate))) return rc;            // A: B'^T slot 1
         return zt_split_product(p, 1, p->B, +1.0, 1, 0, s, gate);                   // B = Pt A^H
     }
-    if ((rc = zgemm(p, p->P, p->Wt, p->A, -1.0, 0, s, gate))) return rc;
+    if ((rc = zgemm(p, p->P, Wk, p->A, -1.0, 0, s, gate))) return rc;
     return zgemm(p, p->A, p->P, p->B, -1.0, 1, s, gate);
 }
 
-static int enqueue_sweep(zt_plan* p, int k, double h, cudaStream_t s) {
+// Sweep k of the step from W = W_n.  W stays W_n until the final assembly
+// writes W_{n+1} into it, so it serves as W_n and as the first iterate Wt^0:
+// sweep 0 reads W, later sweeps the workspace Wt that every sweep writes.
+static int enqueue_sweep(zt_plan* p, int k, const double2* W, double h, cudaStream_t s) {
     int rc;
     p->cur_sweep = k;
-    if ((rc = enqueue_products(p, s, ZT_GATE_SWEEP))) return rc;
+    const double2* Wk = k == 0 ? W : p->Wt;
+    if ((rc = enqueue_products(p, Wk, s, ZT_GATE_SWEEP))) return rc;
     // the update's last CTA reduces the residual and takes the stop decision
-    rc = launch_update(p, p->Wn, p->Wt, p->Wt, h, +1.0, true, s, ZT_GATE_SWEEP);
+    rc = launch_update(p, W, Wk, p->Wt, h, +1.0, true, s, ZT_GATE_SWEEP);
     p->cur_sweep = -1;
     return rc;
 }
@@ -832,7 +836,7 @@ static int enqueue_sweep(zt_plan* p, int k, double h, cudaStream_t s) {
 static int enqueue_final(zt_plan* p, int tag, double2* W, double h, cudaStream_t s) {
     int rc;
     p->cur_sweep = tag;
-    if (p->tun.final_mode == ZT_FINAL_FRESH && (rc = enqueue_products(p, s, ZT_GATE_FINAL))) return rc;
+    if (p->tun.final_mode == ZT_FINAL_FRESH && (rc = enqueue_products(p, p->Wt, s, ZT_GATE_FINAL))) return rc;
     // the assembly's last CTA marks the state finalised (W_{n+1} written by every CTA)
     rc = launch_update(p, p->Wt, nullptr, W, h, -1.0, false, s, ZT_GATE_FINAL);
     p->cur_sweep = -1;
@@ -849,9 +853,6 @@ static int step_impl(zt_plan* p, double2* W, double h, double tol, int maxit, zt
 }
 static int step_impl_(zt_plan* p, double2* W, double h, double tol, int maxit, zt_step_stats* stats,
                       cudaStream_t s) {
-    const size_t mat = (size_t)p->N * p->N * sizeof(double2);
-    ZT_CU(cudaMemcpyAsync(p->Wn, W, mat, cudaMemcpyDeviceToDevice, s));
-    ZT_CU(cudaMemcpyAsync(p->Wt, W, mat, cudaMemcpyDeviceToDevice, s));
     state_init_kernel<<<1, 1, 0, s>>>(p->state, tol, maxit);
     int rc = launch_check(p, "state_init_kernel");
     if (rc) return rc;
@@ -861,7 +862,7 @@ static int step_impl_(zt_plan* p, double2* W, double h, double tol, int maxit, z
     const int chunk = p->tun.sweeps_per_sync ? p->tun.sweeps_per_sync : (p->last_iters > 0 ? p->last_iters : 4);
     for (;; ++round) {
         for (int c = 0; c < chunk && enq < maxit; ++c, ++enq)
-            if ((rc = enqueue_sweep(p, enq, h, s))) return rc;
+            if ((rc = enqueue_sweep(p, enq, W, h, s))) return rc;
         if ((rc = enqueue_final(p, ZT_SWEEP_FINAL + round, W, h, s))) return rc;
         ZT_CU(cudaMemcpyAsync(p->h_state, p->state, sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
         ZT_CU(cudaStreamSynchronize(s));
