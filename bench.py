@@ -734,7 +734,7 @@ def main():
     ap.add_argument("--digit-bits", type=int, default=8)
     ap.add_argument("--slices2", type=int, default=0, help="fixed tuning: digits of the second product (0: slices)")
     ap.add_argument("--exact-groups", type=int, default=2)
-    ap.add_argument("--tile-order", type=int, default=0)
+    ap.add_argument("--tile-order", type=int, default=6)
     ap.add_argument("--no-persistent", type=int, default=0, help="fixed tuning: 1 = one tile per CTA")
     ap.add_argument("--fp64", action="store_true", help="profile mode: the FP64 form")
     ap.add_argument("--fp64-steps", type=int, default=2)

@@ -60,7 +60,8 @@ typedef struct zt_tuning {
                             tiles that are exactly zero (identical results)                  */
     int tile_order;      /* SPLIT launch order of output tiles: 0 (default) / 3 / 4 / 5 = column
                             blocks of 8 / 16 / 4 / 2 tiles, rows walked inside a block;
-                            1 = row-major; 2 = tiles near the diagonal first */
+                            1 = row-major; 2 = tiles near the diagonal first; 6 = column
+                            blocks of 8 from the last block to the first */
     int no_persistent;   /* SPLIT: 0 (default) = persistent product kernel (one CTA per SM working
                             through the tiles); 1 = one tile per CTA */
     int wait_us;         /* SPLIT: limit of each bounded wait inside the product kernel, in

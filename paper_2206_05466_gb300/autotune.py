@@ -24,10 +24,11 @@ import json
 import os
 
 # digit splits with about 49 and 48 bits (7 x 7 and 6 x 8); leading exact groups;
-# launch orders (column blocks of 8, 16, 4, 2 tiles); persistent or one tile per CTA
+# launch orders (column blocks of 8 first to last or last to first, of 16, of 2
+# tiles); persistent or one tile per CTA
 DEFAULT_CANDIDATES = [
     dict(slices=s, digit_bits=b, exact_groups=eg, tile_order=to, no_persistent=np_)
-    for (s, b) in ((7, 7), (6, 8)) for eg in (3, 2) for to in (0, 3, 4, 5) for np_ in (0, 1)
+    for (s, b) in ((7, 7), (6, 8)) for eg in (3, 2) for to in (0, 6, 3, 5) for np_ in (0, 1)
 ]
 REFERENCE = dict(slices=8, digit_bits=7, exact_groups=8)
 

@@ -579,7 +579,7 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         else if (t.digit_bits < 6 || t.digit_bits > 8) bad = "digit_bits outside [6, 8]";
         else if (t.exact_groups < 1 || t.exact_groups > t.slices) bad = "exact_groups outside [1, slices]";
         else if (t.slices * t.digit_bits > 62) bad = "slices*digit_bits above 62";
-        else if (t.tile_order < 0 || t.tile_order > 5) bad = "tile_order outside [0, 5]";
+        else if (t.tile_order < 0 || t.tile_order > 6) bad = "tile_order outside [0, 6]";
         else if (t.no_persistent != 0 && t.no_persistent != 1) bad = "no_persistent must be 0 or 1";
         else if (t.wait_us < 1 || t.wait_us > 60000000) bad = "wait_us outside [1, 60000000]";
         else if (t.debug_stall_loads < 0) bad = "debug_stall_loads must be >= 0";

@@ -1201,13 +1201,19 @@ int zt_split_create(zt_plan* p) {
     // 1: row-major.  2: with all-zero digit tiles skipped, tiles near the
     // diagonal (where the leading digits of both operands are nonzero) carry
     // most of the work, so they are dispatched first and the light far tiles
-    // fill the tail (longest-first ordering).
+    // fill the tail (longest-first ordering).  6: column blocks of 8 taken from
+    // the last to the first: the first block ends with the tiles farthest from
+    // the diagonal, so the light tiles fill the tail and the panels still share
+    // L2 as in order 0.
     {
         const int ntmg = w->Mpad / BM, ntng = w->Npad / BN;
         const int order = p->tun.tile_order;
-        const int cblk = order == 0 ? 8 : order == 3 ? 16 : order == 4 ? 4 : order == 5 ? 2 : ntng;
+        const int cblk = (order == 0 || order == 6) ? 8 : order == 3 ? 16 : order == 4 ? 4 : order == 5 ? 2 : ntng;
         std::vector<std::pair<double, int>> full, lower;
-        for (int cb0 = 0; cb0 < ntng; cb0 += cblk)
+        std::vector<int> blocks;
+        for (int cb0 = 0; cb0 < ntng; cb0 += cblk) blocks.push_back(cb0);
+        if (order == 6) std::reverse(blocks.begin(), blocks.end());
+        for (int cb0 : blocks)
             for (int tg = 0; tg < ntmg; ++tg)
                 for (int ug = cb0; ug < cb0 + cblk && ug < ntng; ++ug) {
                     const double dist = std::fabs((double)tg - (double)ug);

@@ -57,7 +57,7 @@ def test_argument_validation_on_host():
 
 @pytest.mark.parametrize("bad", [dict(slices=2), dict(slices=9), dict(digit_bits=5), dict(digit_bits=9),
                                  dict(slices=4, exact_groups=5), dict(slices=8, digit_bits=8),
-                                 dict(tile_order=6), dict(tile_order=-1), dict(sweeps_per_sync=65), dict(sweeps_per_sync=-1),
+                                 dict(tile_order=7), dict(tile_order=-1), dict(sweeps_per_sync=65), dict(sweeps_per_sync=-1),
                                  dict(final_mode=7), dict(no_persistent=2), dict(wait_us=-1),
                                  dict(wait_us=60000001), dict(debug_stall_loads=-1), dict(slices2=1),
                                  dict(slices=6, slices2=7), dict(slices2=-1)])

@@ -195,7 +195,7 @@ def test_persistent_kernel_equals_one_tile_per_cta(N):
     assert np.array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("order", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("order", [0, 1, 2, 3, 4, 5, 6])
 def test_launch_orders_give_identical_products(order):
     # the launch order permutes the tiles, never their arithmetic
     N = 700
