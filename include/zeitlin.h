@@ -46,6 +46,10 @@ extern "C" {
 #define ZT_FINAL_FRESH  0      /* W_{n+1} from products recomputed at the last iterate */
 #define ZT_FINAL_REUSE  1      /* W_{n+1} from the products of the last sweep           */
 
+#define ZT_FIRST_EXTRAPOLATED 0   /* first iterate W_n + (W_n - W_{n-1})/2 when the plan's previous
+                                     step advanced the same W with the same h and converged; else W_n */
+#define ZT_FIRST_WN           1   /* first iterate W_n                                             */
+
 typedef struct zt_plan zt_plan;
 
 /* Tuning knobs; zero fields take the library default. */
@@ -76,6 +80,9 @@ typedef struct zt_tuning {
                             fewer digits than A = Pt Wt for the same error in W: Pt's digit
                             planes are truncated to their leading slices2 digits and A is split
                             into slices2 digits */
+    int first_iterate;   /* ZT_FIRST_EXTRAPOLATED (default) or ZT_FIRST_WN: the fixed-point
+                            iteration's starting point (Eq. 9 converges to the same Wt from either,
+                            within tol; the extrapolated one is an O(h^2) guess and saves sweeps) */
 } zt_tuning;
 
 typedef struct zt_step_stats {

@@ -142,7 +142,7 @@ class StepInfo:
 
 
 def isomp_step(Wn: np.ndarray, h: float, tol: float = 1e-12, maxit: int = 50,
-               final: str = "fresh"):
+               final: str = "fresh", Wt0=None):
     """One isospectral-midpoint step W_n -> W_{n+1} (Sec. 2, Eqs. 8, 9).
 
     Fixed point (Eq. 9), with the two products of Sec. 3.1:
@@ -150,12 +150,13 @@ def isomp_step(Wn: np.ndarray, h: float, tol: float = 1e-12, maxit: int = 50,
         Wt^{k+1} = W_n + h/2 (A - A^H) + h^2/4 B
     (Wt^k Pt = A^H because Pt and Wt are skew-Hermitian).  Then the second
     line of Eq. 8, W_{n+1} = Wt + h/2 (A - A^H) - h^2/4 B.
+    Wt0 is the first iterate Wt^0 (the paper does not fix it; default W_n).
     Returns (W_{n+1}, StepInfo).
     """
     if final not in ("fresh", "reuse"):
         raise ValueError("final must be 'fresh' or 'reuse'")
     Wn = np.asarray(Wn, dtype=np.complex128)
-    Wt = Wn.copy()
+    Wt = Wn.copy() if Wt0 is None else np.asarray(Wt0, dtype=np.complex128).copy()
     hist = []
     converged = False
     A = B = None

@@ -18,12 +18,13 @@
 
 namespace {
 
-struct CopyArgs {   // W -> W_n and W -> Wt, and the instance's step state reset
+struct CopyArgs {   // W -> W_n and the first iterate -> Wt, and the instance's step state reset
     const double2* src;
     double2* d1;
     double2* d2;
     long long count;
     zt_dev_state* st;
+    int extrap;         // the plan starts from the extrapolated midpoint when its history allows
 };
 constexpr int COPY_PER_CTA = 256 * 4;
 
@@ -40,6 +41,8 @@ __global__ void __launch_bounds__(256) copy_grouped(const CopyArgs* tab, const i
                                                     int maxit) {
     const int inst = zt_group_find(offs, n, blockIdx.x);
     const CopyArgs a = tab[inst];
+    // the history flag is read by every CTA and changed only at the end of a step
+    const int hist = a.extrap && a.st->hist;
     if (blockIdx.x == offs[inst] && threadIdx.x == 0) {   // the instance's first CTA resets its state
         zt_dev_state* st = a.st;
         st->done = 0;
@@ -55,10 +58,10 @@ __global__ void __launch_bounds__(256) copy_grouped(const CopyArgs* tab, const i
     const long long base = (long long)(blockIdx.x - offs[inst]) * COPY_PER_CTA;
     for (int q = 0; q < 4; ++q) {
         const long long i = base + threadIdx.x + 256 * q;
-        if (i < a.count) {
+        if (i < a.count) {   // the same arithmetic as step_start_kernel of a single plan
             const double2 v = a.src[i];
+            a.d2[i] = hist ? zt_extrapolate(v, a.d1[i]) : v;
             a.d1[i] = v;
-            a.d2[i] = v;
         }
     }
 }
@@ -324,7 +327,7 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
         zt_plan* p = plans[i];
         const int N = p->N;
         const long long nn = (long long)N * N;
-        cp.push_back({b->W[i], p->Wn, p->Wt, nn, p->state});
+        cp.push_back({b->W[i], p->Wn, p->Wt, nn, p->state, p->tun.first_iterate == ZT_FIRST_EXTRAPOLATED ? 1 : 0});
         c_cp.push_back((int)((nn + COPY_PER_CTA - 1) / COPY_PER_CTA));
         SolveArgs sa;
         zt_solve_args(p, p->Wt, p->P, &sa);
@@ -405,6 +408,11 @@ extern "C" int zt_batch_create(int count, zt_plan* const* plans, double* const* 
     std::vector<zt_dev_state*> sts(count);
     for (int i = 0; i < count; ++i) sts[i] = plans[i]->state;
     cudaError_t e;
+    // a plan whose previous step advanced another W or h has no usable history here
+    for (int i = 0; i < count; ++i)
+        if (plans[i]->last_W != (const void*)b->W[i] || plans[i]->last_h != b->h[i])
+            if ((e = cudaMemsetAsync(&plans[i]->state->hist, 0, sizeof(int), b->mstream)) != cudaSuccess)
+                return fail(zt_cuda_check(e, "cudaMemsetAsync(hist)"));
     if ((e = ZT_DMALLOC(b->dstates, count * sizeof(zt_dev_state*), b->mstream)) != cudaSuccess)
         return fail(zt_cuda_check(e, "cudaMallocAsync"));
     if ((e = cudaMemcpyAsync(b->dstates, sts.data(), count * sizeof(zt_dev_state*), cudaMemcpyHostToDevice,
@@ -473,6 +481,8 @@ static int batch_step_impl(zt_batch* b, double tol, int maxit, zt_step_stats* st
     }
     int worst = ZT_OK, most = 0;
     for (int i = 0; i < b->n; ++i) {
+        b->plans[i]->last_W = b->W[i];   // the history the next step (batched or not) may use
+        b->plans[i]->last_h = b->h[i];
         const zt_dev_state& hs = b->hstates[i];
         if (hs.iters > most && !hs.timeout && !hs.nonfinite) most = hs.iters;
         if (stats) {

@@ -19,7 +19,8 @@ struct zt_dev_state {
     int    timeout;     // a bounded device wait ran out (tcgen05 kernels)
     int    maxit;
     int    finalized;   // W_{n+1} has been written (set after the final assembly completed)
-    int    pad1;
+    int    hist;        // the plan's W_n buffer holds the previous step's W_n and that step
+                        // converged: the next step may start from the extrapolated midpoint
     double residual;    // last Frobenius residual
     double tol;
 };
@@ -57,6 +58,14 @@ __device__ __forceinline__ int zt_group_find(const int* offs, int n, int b) {
 // negation would take an issue slot of the narrow FP64 pipe.
 __device__ __forceinline__ double neg(double x) {
     return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+
+// First iterate of the fixed point (Eq. 9) from the last two states: the
+// midpoint extrapolated along the trajectory, W_n + (W_n - W_{n-1}) / 2, an
+// O(h^2) guess of the fixed point where W_n is an O(h) one.  Element-wise and
+// odd in (w, wp), so a skew-Hermitian pair gives a skew-Hermitian result.
+__device__ __forceinline__ double2 zt_extrapolate(double2 w, double2 wp) {
+    return make_double2(fma(0.5, w.x - wp.x, w.x), fma(0.5, w.y - wp.y, w.y));
 }
 
 // Packed lower-triangular index of (r, c), c <= r.
@@ -119,6 +128,8 @@ struct zt_plan {
     zt_split_ws* split = nullptr;
     long launches = 0;
     int last_iters = 0;   // sweeps of the previous step (adaptive sweeps_per_sync)
+    const void* last_W = nullptr;   // W and h of the plan's previous step (the history of the
+    double last_h = 0.0;            // extrapolated first iterate is used only for the same W and h)
     // Device memory of the plan comes from the stream-ordered allocator on a
     // private stream: creating or freeing a plan never synchronises the
     // device (other threads may keep long-running work on it).  Frees are

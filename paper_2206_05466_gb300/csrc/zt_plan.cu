@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "zt_internal.h"
@@ -422,7 +423,10 @@ __device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
     __syncthreads();
     if (!last) return;
     if (partials) converge_body(partials, ua.nctas, ua.st);
-    else if (threadIdx.x == 0 && ua.st->done) ua.st->finalized = 1;   // W_{n+1} written by every CTA
+    else if (threadIdx.x == 0 && ua.st->done) {   // W_{n+1} written by every CTA
+        ua.st->finalized = 1;
+        ua.st->hist = ua.st->converged;   // the next step may extrapolate from this one
+    }
     if (threadIdx.x == 0) *ua.done = 0u;
 }
 
@@ -447,7 +451,9 @@ int zt_update_grouped(const UpdateArgs* tab, const int* offs, int n, int total, 
     return ZT_OK;
 }
 
-__global__ void state_init_kernel(zt_dev_state* st, double tol, int maxit) {
+// keep_hist = 0 drops the history (another W or h than the plan's previous step).
+__global__ void state_init_kernel(zt_dev_state* st, double tol, int maxit, int keep_hist) {
+    if (!keep_hist) st->hist = 0;
     st->done = 0;
     st->iters = 0;
     st->converged = 0;
@@ -457,6 +463,21 @@ __global__ void state_init_kernel(zt_dev_state* st, double tol, int maxit) {
     st->residual = 0.0;
     st->tol = tol;
     st->finalized = 0;
+}
+
+// Start of a step: the first iterate Wt^0 (the extrapolated midpoint when the
+// plan's history allows it, else W_n) and the copy of W_n kept for the next
+// step's extrapolation.  Runs after state_init_kernel on the same stream.
+__global__ void __launch_bounds__(256) step_start_kernel(const double2* __restrict__ W, double2* __restrict__ Wn,
+                                                         double2* __restrict__ Wt, long long count,
+                                                         const zt_dev_state* __restrict__ st) {
+    const int hist = st->hist;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double2 w = W[i];
+        Wt[i] = hist ? zt_extrapolate(w, Wn[i]) : w;
+        Wn[i] = w;
+    }
 }
 
 static int launch_update(zt_plan* p, const double2* base, const double2* old, double2* out,
@@ -571,6 +592,10 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
     if (p->tun.sweeps_per_sync < 0 || p->tun.sweeps_per_sync > 64) {
         delete p;
         return zt_fail(ZT_EINVAL, "zt_plan_create: sweeps_per_sync outside [0, 64]");
+    }
+    if (p->tun.first_iterate != ZT_FIRST_EXTRAPOLATED && p->tun.first_iterate != ZT_FIRST_WN) {
+        delete p;
+        return zt_fail(ZT_EINVAL, "zt_plan_create: bad first_iterate %d", p->tun.first_iterate);
     }
     if (precision == ZT_PRECISION_SPLIT) {   // checked before any device work
         const zt_tuning& t = p->tun;
@@ -819,12 +844,13 @@ static int enqueue_products(zt_plan* p, const double2* Wk, cudaStream_t s, int g
 }
 
 // Sweep k of the step from W = W_n.  W stays W_n until the final assembly
-// writes W_{n+1} into it, so it serves as W_n and as the first iterate Wt^0:
-// sweep 0 reads W, later sweeps the workspace Wt that every sweep writes.
-static int enqueue_sweep(zt_plan* p, int k, const double2* W, double h, cudaStream_t s) {
+// writes W_{n+1} into it, so it serves as W_n throughout.  The first iterate is
+// Wt (written by step_start_kernel) or, without extrapolation, W itself; later
+// sweeps read the workspace Wt that every sweep writes.
+static int enqueue_sweep(zt_plan* p, int k, const double2* W, bool from_wt, double h, cudaStream_t s) {
     int rc;
     p->cur_sweep = k;
-    const double2* Wk = k == 0 ? W : p->Wt;
+    const double2* Wk = (k == 0 && !from_wt) ? W : p->Wt;
     if ((rc = enqueue_products(p, Wk, s, ZT_GATE_SWEEP))) return rc;
     // the update's last CTA reduces the residual and takes the stop decision
     rc = launch_update(p, W, Wk, p->Wt, h, +1.0, true, s, ZT_GATE_SWEEP);
@@ -853,16 +879,28 @@ static int step_impl(zt_plan* p, double2* W, double h, double tol, int maxit, zt
 }
 static int step_impl_(zt_plan* p, double2* W, double h, double tol, int maxit, zt_step_stats* stats,
                       cudaStream_t s) {
-    state_init_kernel<<<1, 1, 0, s>>>(p->state, tol, maxit);
+    // first iterate: extrapolated from this plan's previous step when that step
+    // advanced the same W with the same h (decided on the device from its history)
+    const bool extrap = p->tun.first_iterate == ZT_FIRST_EXTRAPOLATED;
+    const int keep = extrap && p->last_W == (const void*)W && p->last_h == h;
+    p->last_W = W;
+    p->last_h = h;
+    state_init_kernel<<<1, 1, 0, s>>>(p->state, tol, maxit, keep);
     int rc = launch_check(p, "state_init_kernel");
     if (rc) return rc;
+    if (extrap) {
+        const long long nn = (long long)p->N * p->N;
+        const int grid = (int)std::min<long long>((nn + 255) / 256, 4096);
+        step_start_kernel<<<grid, 256, 0, s>>>(W, p->Wn, p->Wt, nn, p->state);
+        if ((rc = launch_check(p, "step_start_kernel"))) return rc;
+    }
     int enq = 0, round = 0;
     // sweeps per host check: fixed, or as many as the previous step took (the
     // device gates sweeps past convergence, so a larger chunk only costs launches)
     const int chunk = p->tun.sweeps_per_sync ? p->tun.sweeps_per_sync : (p->last_iters > 0 ? p->last_iters : 4);
     for (;; ++round) {
         for (int c = 0; c < chunk && enq < maxit; ++c, ++enq)
-            if ((rc = enqueue_sweep(p, enq, W, h, s))) return rc;
+            if ((rc = enqueue_sweep(p, enq, W, extrap, h, s))) return rc;
         if ((rc = enqueue_final(p, ZT_SWEEP_FINAL + round, W, h, s))) return rc;
         ZT_CU(cudaMemcpyAsync(p->h_state, p->state, sizeof(zt_dev_state), cudaMemcpyDeviceToHost, s));
         ZT_CU(cudaStreamSynchronize(s));

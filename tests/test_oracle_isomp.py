@@ -164,3 +164,20 @@ def test_residual_history_contracts():
     assert info.converged and 2 <= len(hist) <= 6
     for a, b in zip(hist, hist[1:]):
         assert b < 1e-2 * a
+
+
+def test_fixed_point_does_not_depend_on_the_first_iterate():
+    # Eq. 9 is a contraction for small h: from W_n or from the midpoint extrapolated
+    # along the trajectory, W_n + (W_n - W_{n-1})/2, the same W_{n+1} (within tol),
+    # the extrapolated start (an O(h^2) guess) in no more sweeps
+    N, h = 48, 0.005
+    W0 = vorticity_w0(N, seed=3)
+    W1, _ = oracle.isomp_step(W0, h)
+    plain, ip = oracle.isomp_step(W1, h)
+    extra, ie = oracle.isomp_step(W1, h, Wt0=W1 + 0.5 * (W1 - W0))
+    assert np.linalg.norm(extra - plain) / np.linalg.norm(plain) < 1e-14
+    assert ie.converged and ie.iters <= ip.iters
+    assert ie.history[0] < 1e-2 * ip.history[0]
+    # a poor first iterate converges to the same point too
+    far, iff = oracle.isomp_step(W1, h, Wt0=np.zeros_like(W1))
+    assert iff.converged and np.linalg.norm(far - plain) / np.linalg.norm(plain) < 1e-14
