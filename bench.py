@@ -569,12 +569,19 @@ def run_gpu(args):
     t_max = _barrier_max(t_ms, ws)
     value = _job_rate(args.steps, t_max / 1e3, ws)
 
-    # ---- end to end through the C ABI with host buffers (pinned), copies timed ----
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed: a
+    # trajectory whose state lives on the host (each step's input is the previous
+    # step's output, copied in; its result copied out) ----
     _log('e2e')
-    Wh = torch.from_numpy(W0).pin_memory()
+    Wh = torch.from_numpy(W0.copy()).pin_memory()
     Wout = torch.empty_like(Wh).pin_memory()
     Wd2 = torch.empty_like(Wd)
     e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(2):   # untimed: the plan's history for this buffer
+        Wd2.copy_(Wh, non_blocking=True)
+        z.isomp_step(plan, Wd2, H, TOL, MAXIT)
+        Wh.copy_(Wd2, non_blocking=True)
+        torch.cuda.synchronize()
     _barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -583,6 +590,7 @@ def run_gpu(args):
         z.isomp_step(plan, Wd2, H, TOL, MAXIT)
         Wout.copy_(Wd2, non_blocking=True)
         torch.cuda.synchronize()
+        Wh, Wout = Wout, Wh
     t_e2e = _barrier_max(time.perf_counter() - t0, ws)
     e2e = {"value": _job_rate(e2e_steps, t_e2e, ws), "unit": "steps/s", "h2d_bytes_per_step": int(Wh.numel() * 16),
            "d2h_bytes_per_step": int(Wout.numel() * 16), "steps": e2e_steps}
