@@ -361,6 +361,7 @@ __device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
     const int N = ua.N;
     __shared__ double2 sAT[UT][UT + 1];
     __shared__ double2 sOut[UT][UT + 1];
+    __shared__ double2 sDiag[UT];   // old values on the tile's diagonal
     __shared__ double sred[256];
     int bi = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
     while (bi * (bi + 1) / 2 > t) --bi;
@@ -374,6 +375,9 @@ __device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
         sAT[jj][tx] = (j < N && i < N) ? A[(size_t)j * N + i] : make_double2(0.0, 0.0);
     }
     __syncthreads();
+    // ||out - old||_F^2 over the whole matrix = 2 (sum over the lower triangle) - (sum over
+    // the diagonal): the per-element weight costs no FP64 instruction (the FP64 pipe is
+    // narrow on GB300), the diagonal's share is taken once per diagonal tile below
     double acc = 0.0;
     for (int q = 0; q < UT / 8; ++q) {
         const int ii = ty + 8 * q, jj = tx, i = i0 + ii, j = j0 + jj;
@@ -385,20 +389,29 @@ __device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
             v.y = w.y + h2 * (a.y + at.y) + c2 * bb.y;
             if (i == j) v.x = 0.0;
             if (partials) {
-                const double2 o = old[e];
+                const double2 o = old[e];   // read before out[e] is written (old may be out)
                 const double dx = v.x - o.x, dy = v.y - o.y;
-                acc += (i == j ? 1.0 : 2.0) * (dx * dx + dy * dy);
+                acc = fma(dx, dx, fma(dy, dy, acc));
+                if (i == j) sDiag[ii] = o;
             }
             out[e] = v;
             sOut[ii][jj] = v;
         }
     }
     __syncthreads();
-    for (int q = 0; q < UT / 8; ++q) {   // mirror: out[j, i] = -conj(out[i, j])
+    if (partials && bi == bj && ty == 0) {   // the tile's diagonal, counted once
+        const int i = i0 + tx;
+        if (i < N) {
+            const double2 v = sOut[tx][tx], o = sDiag[tx];
+            const double dx = v.x - o.x, dy = v.y - o.y;
+            acc = fma(-0.5 * dx, dx, fma(-0.5 * dy, dy, acc));
+        }
+    }
+    for (int q = 0; q < UT / 8; ++q) {   // mirror: out[j, i] = -conj(out[i, j]), the sign by its bit
         const int jj = ty + 8 * q, ii = tx, i = i0 + ii, j = j0 + jj;
         if (i < N && j < N && i > j) {
             const double2 v = sOut[ii][jj];
-            out[(size_t)j * N + i] = make_double2(-v.x, v.y);
+            out[(size_t)j * N + i] = make_double2(neg(v.x), v.y);
         }
     }
     if (partials) {
@@ -408,7 +421,7 @@ __device__ __forceinline__ void update_body(const UpdateArgs& ua, int t) {
             if (threadIdx.x < w) sred[threadIdx.x] += sred[threadIdx.x + w];
             __syncthreads();
         }
-        if (threadIdx.x == 0) partials[t] = sred[0];
+        if (threadIdx.x == 0) partials[t] = 2.0 * sred[0];
     }
     // the launch's last CTA: residual and stop decision (sweeps) or the finalised mark
     __shared__ int last;
