@@ -326,7 +326,17 @@ __device__ __forceinline__ void split_rows_body(const SplitRowsArgs& ra, int j) 
         const int kq = threadIdx.x + 256 * it;
         const bool live = kq < ldk / 8;
         int fz = s;   // first nonzero digit of this thread's entries (s: none)
+        // The fixed-point value v (up to 62 bits) in two 32-bit halves: lo = v mod
+        // 2^(kl beta) and hi = v >> (kl beta).  The balanced chain below takes the low
+        // kl digits from lo; what is left of lo then is the carry, 0 or 1, into hi,
+        // and (hi R^kl + lo + H) >> beta = hi R^(kl-1) + ((lo + H) >> beta), so the
+        // digits are those of the chain on v itself, with 32-bit integer operations.
+        // (Both halves keep a bit of headroom: kl beta <= 30 and (s - kl) beta <= 30; wider
+        // splits, beyond the tuned ones, run the chain on the 64-bit value.)
+        const int kl = min(30 / beta, s - 1);
+        const bool halves = (s - kl) * beta <= 30;
         long long vr[4], vi[4];
+        int lr[4], li[4], hr[4], hi[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int k = 4 * kq + u;
@@ -336,9 +346,16 @@ __device__ __forceinline__ void split_rows_body(const SplitRowsArgs& ra, int j) 
                 vr[u] = to_fixed(v.x, e, sb);
                 vi[u] = to_fixed(v.y, e, sb);
             }
+            const long long m = (1LL << (kl * beta)) - 1;
+            lr[u] = (int)(vr[u] & m);
+            li[u] = (int)(vi[u] & m);
+            hr[u] = (int)(vr[u] >> (kl * beta));
+            hi[u] = (int)(vi[u] >> (kl * beta));
         }
-        for (int p = s - 1; p >= 0; --p) {
-            __align__(16) __nv_bfloat162 wa[4], wb0[4], wb1[4];
+        const int Hh = (int)H, Rm = (int)(R - 1);
+        // digit p of the four entries from the halves x (lo or hi), stored to the planes
+        auto emit = [&](int p, auto* xr, auto* xi) {   // int (a half) or long long (the value)
+            __align__(16) __nv_bfloat162 wa[4], wb1[4];
             bool nz = false;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
@@ -346,31 +363,41 @@ __device__ __forceinline__ void split_rows_body(const SplitRowsArgs& ra, int j) 
                 // digits fit 32 bits, so the conversions stay off the FP64 pipe
                 int dr, di;
                 if (p > 0) {
-                    const long long tr = vr[u] + H, ti = vi[u] + H;
-                    dr = ((int)tr & (int)(R - 1)) - (int)H;
-                    di = ((int)ti & (int)(R - 1)) - (int)H;
-                    vr[u] = tr >> beta;
-                    vi[u] = ti >> beta;
+                    const auto tr = xr[u] + Hh, ti = xi[u] + Hh;
+                    dr = ((int)tr & Rm) - Hh;
+                    di = ((int)ti & Rm) - Hh;
+                    xr[u] = tr >> beta;
+                    xi[u] = ti >> beta;
                 } else {
-                    dr = (int)vr[u];
-                    di = (int)vi[u];
+                    dr = (int)xr[u];
+                    di = (int)xi[u];
                 }
                 nz |= (dr | di) != 0;
                 const float fr = (float)dr, fi = (float)di;
+                // X' row and B'^T row 2j: interleaved(y); B'^T row 2j+1: interleaved(i y) = (-im, re)
                 wa[u] = __floats2bfloat162_rn(fr, fi);
-                // B'^T row 2j: interleaved(y); row 2j+1: interleaved(i y) = (-im, re)
-                wb0[u] = __floats2bfloat162_rn(fr, fi);
                 wb1[u] = __floats2bfloat162_rn(-fi, fr);
             }
             if (nz) fz = p;
-            if (!live) continue;
+            if (!live) return;
             const size_t col = (size_t)8 * kq;
             if (dA) *reinterpret_cast<uint4*>(dA + p * planeA + (size_t)j * ldk + col) = *reinterpret_cast<uint4*>(wa);
             if (dB) {
-                *reinterpret_cast<uint4*>(dB + p * planeB + (size_t)(2 * j) * ldk + col) = *reinterpret_cast<uint4*>(wb0);
+                *reinterpret_cast<uint4*>(dB + p * planeB + (size_t)(2 * j) * ldk + col) = *reinterpret_cast<uint4*>(wa);
                 *reinterpret_cast<uint4*>(dB + p * planeB + (size_t)(2 * j + 1) * ldk + col) =
                     *reinterpret_cast<uint4*>(wb1);
             }
+        };
+        if (halves) {
+            for (int p = s - 1; p >= s - kl; --p) emit(p, lr, li);   // the low kl digits from lo
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {   // lo's carry into hi
+                hr[u] += lr[u];
+                hi[u] += li[u];
+            }
+            for (int p = s - kl - 1; p >= 0; --p) emit(p, hr, hi);
+        } else {
+            for (int p = s - 1; p >= 0; --p) emit(p, vr, vi);
         }
         int occ = s - fz;   // 0: all digits zero, s: leading digit present
         occ = max(occ, __shfl_xor_sync(0xffffffffu, occ, 1));
