@@ -104,10 +104,11 @@ def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate,
       * Memory: the head job's plan footprint estimate(N, precision) must fit the
         remaining budget, unless nothing at all is resident.
       * Latency: an active class admits another job only after it completed a step
-        with its current set (stepped), while its measured step time ema[cls] stays
-        below `headroom` x `factor` times its solo step time with one job (the
-        headroom leaves room for the jobs of the next admission burst, so that the
-        class's steps stay within `factor` times that solo time), and while the
+        with its current set (stepped), while its measured step time ema[cls], and its
+        calibrated solo step time with one more job, stay below `headroom` x `factor`
+        times its solo step time with one job (the headroom leaves room for the jobs
+        of the next admission burst, so that the class's steps stay within `factor`
+        times that solo time), and while the
         calibrated solo step time with one more job stays within the absolute
         `target` (seconds).  (Measured: a batch's step time grows with its size, and
         past a few dozen small jobs the device is full, so larger batches only add
@@ -140,7 +141,10 @@ def next_admission(queues, resident, used, budget, stepped, ema, solo, estimate,
         if factor is not None or target is not None:
             if not stepped.get(cls):
                 continue
-            if factor is not None and (cls not in ema or ema[cls] > headroom * factor * solo_step_s(solo, cls, 1)):
+            gate = None if factor is None else headroom * factor * solo_step_s(solo, cls, 1)
+            if factor is not None and (cls not in ema or ema[cls] > gate):
+                continue
+            if factor is not None and solo_step_s(solo, cls, n + 1) > gate:   # the calibrated cost of one more
                 continue
             if target is not None and solo_step_s(solo, cls, n + 1) > target:
                 continue

@@ -111,3 +111,14 @@ def test_compatibility_keeps_light_and_heavy_classes_apart():
     assert next_admission(_q(J(2048, 0, 0.0)), res, 0, 10**9, {}, {}, solo, est, compat=8.0) is None
     assert next_admission(_q(J(2048, 0, 0.0)), res, 0, 10**9, {}, {}, solo, est, compat=None) == (2048, 0)
     assert next_admission(_q(J(2048, 0, 0.0)), {}, 0, 10**9, {}, {}, solo, est, compat=8.0) == (2048, 0)
+
+
+def test_calibrated_cost_of_one_more_job_is_gated_too():
+    # heavy per-job cost: one job 50 ms, +25 ms per further job; the gate 0.8 x 2 x 50 = 80 ms
+    c = (1024, 0)
+    solo = {c: (0.050, 0.025)}
+    q = _q(J(1024, 0, 0.0))
+    kw = dict(stepped={c: True}, ema={c: 0.050})
+    assert next_admission(q, {c: 1}, 0, 10**9, solo=solo, estimate=est, **kw) == c       # 2 jobs: 75 ms
+    kw = dict(stepped={c: True}, ema={c: 0.075})
+    assert next_admission(q, {c: 2}, 0, 10**9, solo=solo, estimate=est, **kw) is None    # 3 jobs: 100 ms
