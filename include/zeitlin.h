@@ -83,6 +83,8 @@ typedef struct zt_tuning {
     int first_iterate;   /* ZT_FIRST_EXTRAPOLATED (default) or ZT_FIRST_WN: the fixed-point
                             iteration's starting point (Eq. 9 converges to the same Wt from either,
                             within tol; the extrapolated one is an O(h^2) guess and saves sweeps) */
+    int second_form;     /* SPLIT: kernel form of the second product of a sweep: 0 (default) = that
+                            of the first (no_persistent), 1 = one tile per CTA, 2 = persistent */
 } zt_tuning;
 
 typedef struct zt_step_stats {

@@ -178,13 +178,15 @@ def autotune(N: int, target: float = 1e-11, candidates=None, reps: int = 3, use_
     ms_best = best["ms"]
     if gemm2["slices2"] != tuning["slices"]:
         # lighter second products may favour another kernel form or launch order:
-        # the leading candidates of the chosen digit split again, with slices2 set
+        # the leading candidates of the chosen digit split again, with slices2 set and
+        # the second product in either kernel form (one tile per CTA, persistent)
         same = sorted((t for t in ok if all(t["tuning"][k] == tuning[k] for k in ("slices", "digit_bits"))),
-                      key=lambda t: t["ms"])[:6]
+                      key=lambda t: t["ms"])[:4]
         retimed = []
         for t in same:
-            tun2 = dict(t["tuning"], slices2=gemm2["slices2"])
-            retimed.append({"tuning": tun2, "ms": _time_steps(N, tun2, Y, step_h, reps)})
+            for form in (1, 2):
+                tun2 = dict(t["tuning"], slices2=gemm2["slices2"], second_form=form)
+                retimed.append({"tuning": tun2, "ms": _time_steps(N, tun2, Y, step_h, reps)})
         pick = min(retimed, key=lambda t: t["ms"])
         tuning, ms_best = pick["tuning"], pick["ms"]
         gemm2["retimed"] = [{**t["tuning"], "ms": round(t["ms"], 3)} for t in retimed]

@@ -622,6 +622,7 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
         else if (t.wait_us < 1 || t.wait_us > 60000000) bad = "wait_us outside [1, 60000000]";
         else if (t.debug_stall_loads < 0) bad = "debug_stall_loads must be >= 0";
         else if (t.slices2 != 0 && (t.slices2 < 2 || t.slices2 > t.slices)) bad = "slices2 outside [2, slices]";
+        else if (t.second_form < 0 || t.second_form > 2) bad = "second_form outside [0, 2]";
         if (bad) {
             delete p;
             return zt_fail(ZT_EINVAL, "zt_plan_create: %s", bad);

@@ -95,6 +95,7 @@ struct zt_split_ws {
     int n_full = 0, n_lower = 0;
     int skip_zero = 1;                           // skip digit-pair units whose tiles are all zero
     int persistent = 1;                          // persistent product kernel
+    int persistent2 = 1;                         // ... for the products with slot 1 (the second product)
     int nsm = 0;                                 // SMs of the device
     unsigned int* tickets = nullptr;             // tile ticket counter of the persistent kernel,
                                                  // then the count of finished CTAs (occupancy clear)
@@ -1263,6 +1264,7 @@ int zt_split_create(zt_plan* p) {
         ZT_CU(cudaStreamSynchronize(cs));   // host vectors go out of scope
     }
     w->persistent = p->tun.no_persistent ? 0 : 1;
+    w->persistent2 = p->tun.second_form == 0 ? w->persistent : (p->tun.second_form == 2 ? 1 : 0);
     ZT_CU(cudaDeviceGetAttribute(&w->nsm, cudaDevAttrMultiProcessorCount, p->device));
     ZT_CU(ZT_DMALLOC(w->tickets, 16, cs));   // [0] tile tickets, [1] finished CTAs
     ZT_CU(cudaMemsetAsync(w->tickets, 0, 16, cs));
@@ -1467,7 +1469,7 @@ int zt_split_product(zt_plan* p, int b_slot, double2* C, double alpha, int lower
     const double alg = lower_only ? 4.0 * N * (double)N * (N + 1.0) : 8.0 * (double)N * N * N;
     const int t = zt_timer_begin(p, ZT_KERNEL_PRODUCT, 0.0, alg, s);
     cudaError_t e;
-    if (w->persistent) {   // one CTA per SM works through the tile groups
+    if (b_slot == 1 ? w->persistent2 : w->persistent) {   // one CTA per SM works through the tile groups
         e = cudaMemsetAsync(w->tickets, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) {
             zt_timer_end(p, t, s);

@@ -39,7 +39,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("slices", ctypes.c_int), ("digit_bits", ctypes.c_int), ("exact_groups", ctypes.c_int),
                 ("final_mode", ctypes.c_int), ("sweeps_per_sync", ctypes.c_int), ("dense", ctypes.c_int),
                 ("tile_order", ctypes.c_int), ("no_persistent", ctypes.c_int), ("wait_us", ctypes.c_int),
-                ("debug_stall_loads", ctypes.c_int), ("slices2", ctypes.c_int), ("first_iterate", ctypes.c_int)]
+                ("debug_stall_loads", ctypes.c_int), ("slices2", ctypes.c_int), ("first_iterate", ctypes.c_int),
+                ("second_form", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -165,13 +166,13 @@ class Plan:
 
     def __init__(self, N: int, precision: int = PRECISION_FP64, slices=0, digit_bits=0,
                  exact_groups=0, final_mode=FINAL_FRESH, sweeps_per_sync=0, dense=0, tile_order=0,
-                 no_persistent=0, wait_us=0, debug_stall_loads=0, slices2=0, first_iterate=0):
+                 no_persistent=0, wait_us=0, debug_stall_loads=0, slices2=0, first_iterate=0, second_form=0):
         L = load()
         self.N = int(N)
         self.precision = precision
         tun = Tuning(slices, digit_bits, exact_groups, final_mode, sweeps_per_sync, 1 if dense else 0,
                      int(tile_order), int(no_persistent), int(wait_us), int(debug_stall_loads), int(slices2),
-                     int(first_iterate))
+                     int(first_iterate), int(second_form))
         h = ctypes.c_void_p()
         _check(L.zt_plan_create(self.N, precision, ctypes.byref(tun), ctypes.byref(h)))
         self._h = h
@@ -380,7 +381,8 @@ def plan_estimate_bytes(N: int, precision: int = PRECISION_FP64, **tuning) -> in
     t = Tuning(tuning.get("slices", 0), tuning.get("digit_bits", 0), tuning.get("exact_groups", 0),
                tuning.get("final_mode", 0), tuning.get("sweeps_per_sync", 0), 1 if tuning.get("dense", 0) else 0,
                tuning.get("tile_order", 0), tuning.get("no_persistent", 0), tuning.get("wait_us", 0),
-               tuning.get("debug_stall_loads", 0), tuning.get("slices2", 0), tuning.get("first_iterate", 0))
+               tuning.get("debug_stall_loads", 0), tuning.get("slices2", 0), tuning.get("first_iterate", 0),
+               tuning.get("second_form", 0))
     v = load().zt_plan_estimate_bytes(int(N), int(precision), ctypes.byref(t))
     if v < 0:
         raise ValueError(f"invalid N={N}")

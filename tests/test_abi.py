@@ -61,7 +61,8 @@ def test_argument_validation_on_host():
                                  dict(final_mode=7), dict(no_persistent=2), dict(wait_us=-1),
                                  dict(wait_us=60000001), dict(debug_stall_loads=-1), dict(slices2=1),
                                  dict(slices=6, slices2=7), dict(slices2=-1),
-                                 dict(first_iterate=2), dict(first_iterate=-1)])
+                                 dict(first_iterate=2), dict(first_iterate=-1),
+                                 dict(second_form=3), dict(second_form=-1)])
 def test_split_tuning_validation_on_host(bad):
     # rejected before any device work, so this runs without a GPU
     L = z.load()

@@ -271,3 +271,19 @@ def test_second_product_digits_error_bound():
         if prev is not None:
             assert e < prev / 16, (s, e, prev)
         prev = e
+
+
+def test_second_product_kernel_form_is_bitwise_neutral():
+    # the second product in the persistent or the one-tile-per-CTA kernel: the same bits
+    N, h = 300, 0.01
+    W0 = vorticity_w0(N, seed=44)
+    outs = []
+    for form in (1, 2):
+        plan = z.Plan(N, z.PRECISION_SPLIT, slices=6, digit_bits=8, exact_groups=2, no_persistent=1,
+                      slices2=4, second_form=form)
+        Wd = torch.from_numpy(W0.copy()).cuda()
+        for _ in range(2):
+            z.isomp_step(plan, Wd, h)
+        outs.append(Wd.cpu().numpy())
+        plan.close()
+    assert np.array_equal(outs[0], outs[1])
