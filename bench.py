@@ -199,12 +199,12 @@ def run_reference(args):
     return 0
 
 
-def _tuning(args, N):
-    """Split-product tuning: autotuned (cached per N and GPU) or fixed from the flags."""
+def _tuning(args, N, h=H):
+    """Split-product tuning: autotuned (cached per N, step size and GPU) or fixed from the flags."""
     if args.tuning == "auto":
         from paper_2206_05466_gb300 import autotune
 
-        res = autotune.autotune(N, target=args.tune_target)
+        res = autotune.autotune(N, target=args.tune_target, step_h=h)
         timed = sorted((t for t in res["trials"] if "ms" in t), key=lambda t: t["ms"])
         return dict(res["tuning"]), {"mode": "auto", "target_rel_err": args.tune_target,
                                      "probe_rel_err": res["rel_err"], "probe_ms": res["ms"],
@@ -366,9 +366,13 @@ def _ensemble(args, tun, steps, graph=True):
     from paper_2206_05466_gb300.inputs import ensemble_sizes, vorticity_w0
 
     sizes = ensemble_sizes(args.ens_count, seed=0)
-    # the second product's digit count was chosen for the headline workload (N, h);
-    # the ensemble's members keep the full digit count for both products
-    tun = {k: v for k, v in tun.items() if k != "slices2"}
+    # the tuning is the one chosen for the largest member size at the ensemble's step
+    # size (the second product's digits depend on h); with fixed flags the members keep
+    # the full digit count for both products
+    if args.tuning == "auto":
+        tun, _ = _tuning(args, max(sizes), h=0.01)
+    else:
+        tun = {k: v for k, v in tun.items() if k != "slices2"}
     cache = {}
     plans, Ws = [], []
     for k, N in enumerate(sizes):
