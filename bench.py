@@ -37,8 +37,8 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor) nominal rate; no measured
 # dram__bytes_write.sum at N = 2048 scaled to N = 4096 by the tile count (x4 for the
 # full product, x528/136 for the lower one); valid only for the kernel source it was
 # taken on (sha256 of csrc/zt_split.cu), null otherwise.
-TRAFFIC = {"sha256": "d3b46b6731c494608ba52eed5d9df4e4d6205f6a264e40f01e5a14ade92c1722",
-           "bytes_per_launch": 1411528960, "captured_n": 2048}
+TRAFFIC = {"sha256": "25c42489b964d7f5429b585415bd53a10b52306b458e69eb9df6f77a6e5730c9",
+           "bytes_per_launch": 1414305445, "captured_n": 2048}
 
 
 def _peaks():
