@@ -219,6 +219,12 @@ ZT_API long long zt_plan_estimate_bytes(int N, int precision, const zt_tuning* o
  * (every launch of every entry point on this plan). */
 ZT_API long zt_plan_launch_count(const zt_plan* plan);
 
+/* Forget the plan's step history (Eq. 9's first iterate, zt_tuning.first_iterate):
+ * the next step starts from W_n.  For callers that rewrite W in place between
+ * steps; the result is the same either way (within tol), only the sweep count
+ * depends on the first iterate.  A NULL plan is ignored. */
+ZT_API void zt_plan_reset_history(zt_plan* plan);
+
 /* Measurement hook (no counterpart in the paper).  When enabled, the library
  * records a CUDA event pair on the launching stream around every launch of
  * the kernel classes below, and sums, per class, the elapsed time and the

@@ -720,6 +720,10 @@ extern "C" int zt_plan_create(int N, int precision, const zt_tuning* opt, zt_pla
 
 extern "C" long zt_plan_launch_count(const zt_plan* p) { return p ? p->launches : 0; }
 
+extern "C" void zt_plan_reset_history(zt_plan* p) {
+    if (p) p->last_W = nullptr;   // the next step's state_init drops the device history too
+}
+
 static int check_ptr(const void* ptr, const char* name) {
     if (!ptr) return zt_fail(ZT_EINVAL, "%s is NULL", name);
     if (((uintptr_t)ptr & 15u) != 0) return zt_fail(ZT_EINVAL, "%s is not 16-byte aligned", name);

@@ -114,6 +114,8 @@ def load(build_if_missing: bool = True):
     L.zeitlin_energy_spectrum.restype = i
     L.zt_plan_launch_count.argtypes = [vp]
     L.zt_plan_launch_count.restype = l
+    L.zt_plan_reset_history.argtypes = [vp]
+    L.zt_plan_reset_history.restype = None
     L.zt_plan_set_timing.argtypes = [vp, i]
     L.zt_plan_set_timing.restype = i
     dp, lp = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_long)
@@ -194,6 +196,10 @@ class Plan:
 
     def launch_count(self) -> int:
         return load().zt_plan_launch_count(self._h)
+
+    def reset_history(self):
+        """The next step starts from W_n (for callers that rewrite W in place)."""
+        load().zt_plan_reset_history(self._h)
 
     def set_timing(self, enable: bool = True):
         _check(load().zt_plan_set_timing(self._h, 1 if enable else 0))

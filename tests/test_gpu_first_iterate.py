@@ -99,3 +99,20 @@ def test_first_iterate_wn_follows_the_oracle_sweep_for_sweep():
         assert info["iters"] == st.iters
         assert _rel(W.cpu().numpy(), want) <= 1e-11
     p.close()
+
+
+def test_reset_history_gives_the_w_n_start():
+    N, h = 72, 0.01
+    W0 = vorticity_w0(N, seed=9)
+    p = z.Plan(N, z.PRECISION_SPLIT)
+    A = torch.from_numpy(W0.copy()).cuda()
+    for _ in range(2):
+        z.isomp_step(p, A, h)
+    p.reset_history()
+    B = A.clone()
+    z.isomp_step(p, A, h)
+    q = z.Plan(N, z.PRECISION_SPLIT)
+    z.isomp_step(q, B, h)
+    assert np.array_equal(A.cpu().numpy(), B.cpu().numpy())
+    p.close()
+    q.close()
