@@ -648,6 +648,12 @@ def run_gpu(args):
     if rank == 0 and args.casimir_steps > 0:
         _log("casimir drift (split)")
         drift = {"split": _drift_leg(N, z.PRECISION_SPLIT, H, args.casimir_steps, tun)}
+        if args.casimir_n2 > 0 and args.casimir_n2 != N:   # the workload's second precision-form size
+            _log(f"casimir drift (split, N={args.casimir_n2})")
+            tun2, _ = _tuning(args, args.casimir_n2)
+            drift[f"split_n{args.casimir_n2}"] = _drift_leg(args.casimir_n2, z.PRECISION_SPLIT, H,
+                                                            args.casimir_steps, tun2)
+            drift[f"split_n{args.casimir_n2}"]["tuning"] = tun2
         if args.casimir_fp64_steps > 0:
             _log("casimir drift (fp64)")
             drift["fp64"] = _drift_leg(args.casimir_fp64_n, z.PRECISION_FP64, 0.01, args.casimir_fp64_steps)
@@ -734,6 +740,8 @@ def main():
     ap.add_argument("--casimir-steps", type=int, default=1000,
                     help="split steps at --n for the Casimir drift (0: skip)")
     ap.add_argument("--casimir-fp64-n", type=int, default=1024)
+    ap.add_argument("--casimir-n2", type=int, default=2048,
+                    help="split-form drift leg at this second size too (0: skip)")
     ap.add_argument("--casimir-fp64-steps", type=int, default=1000,
                     help="FP64-form steps at --casimir-fp64-n, h = 0.01, for its Casimir drift (0: skip)")
     ap.add_argument("--dense-product", type=int, default=1, help="time the product with dense=1 (0: skip)")
