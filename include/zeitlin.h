@@ -139,8 +139,11 @@ ZT_API int zeitlin_stream_solve(zt_plan* plan, const double* W, double* P, void*
  * Eqs. 8 and 9; products as in Sec. 3.1).  Fixed-point sweeps
  *   Pt = Delta_N^{-1} Wt,  A = Pt Wt,  B = A Pt,
  *   Wt <- W_n + h/2 (A - A^H) + h^2/4 B,   r = ||Wt_new - Wt_old||_F
- * from Wt = W_n until r < tol or maxit sweeps, then
+ * until r < tol or maxit sweeps, then
  *   W_{n+1} = Wt + h/2 (A - A^H) - h^2/4 B.
+ * The first iterate is W_n, or W_n + (W_n - W_{n-1})/2 when the plan's previous
+ * step advanced this W buffer with this h and converged (zt_tuning.first_iterate,
+ * zt_plan_reset_history): the fixed point, and W_{n+1}, are the same within tol.
  * W must be in su(N).  `stats` (host pointer, may be NULL) receives the sweep
  * count and last residual.  Blocks the host thread until the step is done.
  * Returns ZT_OK, ZT_NOT_CONVERGED (W_{n+1} written from the last iterate),
