@@ -147,7 +147,8 @@ int count_launch(zt_batch* b, const char* what) {
     return ZT_OK;
 }
 
-// Pt = solve(Wt), A = Pt Wt, B = A Pt for every instance (grouped launches).
+// Pt = solve(Wt), A = Pt Wt, B = A Pt (in split form as Pt A^H) for every instance
+// (grouped launches).
 int enqueue_products(zt_batch* b, cudaStream_t s, int gate) {
     int rc;
     if ((rc = zt_solve_grouped((const SolveArgs*)b->solve.tab, b->solve.offs, b->solve.n, b->solve.total, b->maxN,

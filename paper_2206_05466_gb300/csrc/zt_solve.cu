@@ -13,8 +13,9 @@
 // 32 adjacent entries of that row: one 512-byte run of W or P, so a warp reads
 // or writes a whole row of its band in one coalesced access, and the
 // per-element factors (packed lower-triangular, row-major) likewise.  A warp
-// works on a segment of 32 rows of its band; for lane t (diagonal m0 + t) that
-// is the positions [32k - t, 32k + 32 - t) of its diagonal.
+// works on a segment of SL = 16 rows of its band; for lane t (diagonal m0 + t)
+// that is the positions [16k - t, 16k + 16 - t) of its diagonal (empty for the
+// first segment of lanes t >= 16).
 //
 // Both recurrences are linear, so each segment is swept from zero inflows and
 // corrected afterwards.  With c the true z just before the segment and d the
