@@ -580,7 +580,7 @@ def run_gpu(args):
     Wh = torch.from_numpy(W0.copy()).pin_memory()
     Wout = torch.empty_like(Wh).pin_memory()
     Wd2 = torch.empty_like(Wd)
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, args.steps)   # as many as the timed region: a host-side stall of one step stays a small share
     for _ in range(2):   # untimed: the plan's history for this buffer
         Wd2.copy_(Wh, non_blocking=True)
         z.isomp_step(plan, Wd2, H, TOL, MAXIT)

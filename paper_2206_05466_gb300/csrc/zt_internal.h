@@ -104,11 +104,11 @@ struct zt_plan {
     double* cas_part = nullptr;   // Casimir partial sums [CTAs + 1][8]
     int npartials = 0;
     // Stream solve by bands of 32 diagonals and segments of 16 rows (zt_solve.cu).
-    // Per element, packed lower-triangular row-major (entry (r, c) at zt_tri(r, c)):
-    double* fac_l = nullptr;   // LDL^T multiplier, negated: -l_i (l_0 = 0)
-    double* fac_nd = nullptr;  // -1 / d_i (0 for the dropped m = 0 row)
-    double* fac_f = nullptr;   // F_i: the segment's response to its forward inflow
-    double* fac_h = nullptr;   // H_i: the segment's response to its backward inflow
+    // Per element, packed lower-triangular row-major (entry (r, c) at zt_tri(r, c)),
+    // as pairs so that one 16-byte load brings both numbers a sweep needs:
+    double2* fac_lnd = nullptr;   // (-l_i, nd_i): LDL^T multiplier negated (l_0 = 0), nd_i = -1 / d_i
+                                  // (0 for the dropped m = 0 row)
+    double2* fac_fh = nullptr;    // (F_i, H_i): the segment's responses to its forward and backward inflows
     // Per (segment k, diagonal m), [K][N] (coalesced over m):
     int nseg = 0;              // K = 2 ceil(N / 32) segments of 16 rows
     double2* seg_z = nullptr;  // local forward sweep at the segment's last position
@@ -159,10 +159,8 @@ int zt_timer_collect(zt_plan* p, int iters);
 struct SolveArgs {     // stream solve (zt_solve.cu)
     const double2* W;
     double2* P;
-    const double* fnl;     // packed lower-triangular -l, nd, F, H (constant)
-    const double* fnd;
-    const double* ff;
-    const double* fh;
+    const double2* fln;    // packed lower-triangular (-l, nd) pairs (constant)
+    const double2* ffh;    // packed lower-triangular (F, H) pairs (constant)
     double2* seg_z;        // [K][N]
     double2* seg_x;        // [K][N]
     const double* seg_g;   // [K][N] (constant)

@@ -12,7 +12,8 @@
 // lane of a warp.  In row r the band's elements (r, r-m), m in the band, are
 // 32 adjacent entries of that row: one 512-byte run of W or P, so a warp reads
 // or writes a whole row of its band in one coalesced access, and the
-// per-element factors (packed lower-triangular, row-major) likewise.  A warp
+// per-element factors (packed lower-triangular, row-major, as the pairs
+// (-l, nd) and (F, H): one 16-byte load each) likewise.  A warp
 // works on a segment of SL = 16 rows of its band; for lane t (diagonal m0 + t)
 // that is the positions [16k - t, 16k + 16 - t) of its diagonal (empty for the
 // first segment of lanes t >= 16).
@@ -37,11 +38,15 @@
 //       triangle row by row and, as -conj, to the upper triangle (the mirror
 //       of a band segment is a set of partial row runs, written from shared
 //       memory).
+// FB and C issue every load of a segment before its first dependent
+// operation: the 16 rows of W (FB) or x0 (C) go to the warp's shared memory
+// by asynchronous copies, the factor pairs to registers (which is what bounds
+// the kernels to 16 warps per SM).
 // FP64 work: 3 + 2 fused operations per real component and element.
 //
 // The singular m = 0 block (the l = 0 mode): the mean of its right-hand side
 // is removed before the forward sweep (band-0 warps reduce diagonal 0 of W
-// first), the leading N-1 equations are solved with x_{N-1} = 0 (the factors
+// while their copies are in flight), the leading N-1 equations are solved with x_{N-1} = 0 (the factors
 // of the dropped row are zero), and the mean of the solution is removed in C.
 #include <thread>
 #include <vector>
@@ -50,15 +55,24 @@
 
 namespace {
 constexpr int BW = 32;            // diagonals per band (lanes of a warp)
-constexpr int SL = 16;            // rows per segment: 8 KB of shared memory per warp, 24 warps per SM
+constexpr int SL = 16;            // rows per segment: 8 KB of shared memory per warp
 constexpr int SPB = BW / SL;      // segments per 32 rows of a band
 static_assert(BW % SL == 0, "a band's 32-row blocks split into whole segments");
-constexpr int WPC = 4;            // warps per CTA
-constexpr int CH = 8;             // rows per load chunk of the sweeps
-constexpr int CHC = 4;            // rows per load chunk of the corrections (no dependency between rows)
+constexpr int WPC = 4;            // warps per CTA; 4 CTAs per SM (the 2 x 16 factors of a lane's segment
+                                  // are held in registers)
 constexpr size_t WARP_SMEM = (size_t)SL * BW * sizeof(double2);
 constexpr size_t CTA_SMEM = WPC * WARP_SMEM;
 constexpr int SCAN_TH = 128;   // threads of a scan CTA: one warp per diagonal
+
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned:
+// W and P are checked on entry, the staging rows are 16-byte slots).
+__device__ __forceinline__ void zt_cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void zt_cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
 
 __host__ __device__ inline int nbands(int N) { return (N + BW - 1) / BW; }
 // Segments of band b: SPB (nbands - b), the rows m0 = 32 b .. 32 nbands - 1 in
@@ -94,10 +108,27 @@ __device__ __forceinline__ void solve_fb_band(const SolveArgs& a, int b, int k, 
     const int m = m0 + lane;
     const bool valid = m < N;
     const double2* __restrict__ W = a.W;
-    const double* __restrict__ fnl = a.fnl;
-    const double* __restrict__ fnd = a.fnd;
+    const double2* __restrict__ fln = a.fln;
+
+    // Every load of the segment is issued before the first dependent operation:
+    // W's rows go to shared memory by asynchronous copies (zs[row][lane], later
+    // overwritten by z0), the factor pairs (-l, nd) to registers.
+    double nl[SL], nd[SL];
+#pragma unroll
+    for (int u = 0; u < SL; ++u) {
+        const int r = R0 + u;
+        if (valid && r < R1 && r >= m) {
+            zt_cp_async16(zs + u * BW + lane, W + (size_t)r * N + (r - m));
+            const double2 q = __ldg(fln + zt_tri(r, r - m));
+            nl[u] = q.x;
+            nd[u] = q.y;
+        } else {
+            nl[u] = nd[u] = 0.0;
+        }
+    }
 
     // m = 0: mean of the right-hand side (diagonal 0 of W), reduced by the warp
+    // while the copies are in flight
     double mur = 0.0, mui = 0.0;
     if (B0) {   // eight strided loads in flight per lane
         constexpr int UR = 8;
@@ -121,70 +152,41 @@ __device__ __forceinline__ void solve_fb_band(const SolveArgs& a, int b, int k, 
         mur = m == 0 ? mur / N : 0.0;
         mui = m == 0 ? mui / N : 0.0;
     }
+    zt_cp_async_wait_all();   // each lane reads back only the rows it copied
 
-    // forward sweep from a zero inflow; z0 kept in shared memory, [row][lane]
+    // forward sweep from a zero inflow, z0 in place of w
     double zr = 0.0, zi = 0.0;
-    for (int c0 = 0; c0 < SL; c0 += CH) {
-        double2 w[CH];
-        double l[CH];
 #pragma unroll
-        for (int u = 0; u < CH; ++u) {   // loads first: the chunk's rows are independent
-            const int r = R0 + c0 + u;
-            if (valid && r < R1 && r >= m) {
-                const size_t e = (size_t)r * N + (r - m);
-                w[u] = W[e];
-                l[u] = __ldg(fnl + zt_tri(r, r - m));
-            } else {
-                w[u] = make_double2(0.0, 0.0);
-                l[u] = 0.0;
+    for (int u = 0; u < SL; ++u) {
+        const int r = R0 + u;
+        if (valid && r < R1 && r >= m) {
+            double2 w = zs[u * BW + lane];
+            if (B0) {
+                w.x -= mur;
+                w.y -= mui;
             }
-        }
-#pragma unroll
-        for (int u = 0; u < CH; ++u) {
-            const int r = R0 + c0 + u;
-            if (valid && r < R1 && r >= m) {
-                if (B0) {
-                    w[u].x -= mur;
-                    w[u].y -= mui;
-                }
-                zr = fma(l[u], zr, w[u].x);
-                zi = fma(l[u], zi, w[u].y);
-                zs[(c0 + u) * BW + lane] = make_double2(zr, zi);
-            }
+            zr = fma(nl[u], zr, w.x);
+            zi = fma(nl[u], zi, w.y);
+            zs[u * BW + lane] = make_double2(zr, zi);
         }
     }
     if (valid) a.seg_z[(size_t)k * N + m] = make_double2(zr, zi);   // the last row of the segment is active
-    __syncwarp();
 
     // backward sweep of nd z0 from a zero right inflow
     double xr = 0.0, xi = 0.0, lnext = 0.0, sxr = 0.0, sxi = 0.0;
-    for (int c0 = SL - CH; c0 >= 0; c0 -= CH) {
-        double nd[CH], l[CH];
 #pragma unroll
-        for (int u = 0; u < CH; ++u) {
-            const int r = R0 + c0 + u;
-            if (valid && r < R1 && r >= m) {
-                const size_t t = zt_tri(r, r - m);
-                nd[u] = __ldg(fnd + t);
-                l[u] = __ldg(fnl + t);
-            } else {
-                nd[u] = l[u] = 0.0;
+    for (int u = SL - 1; u >= 0; --u) {
+        const int r = R0 + u;
+        if (valid && r < R1 && r >= m) {
+            const double2 z = zs[u * BW + lane];
+            xr = fma(lnext, xr, nd[u] * z.x);
+            xi = fma(lnext, xi, nd[u] * z.y);
+            a.P[(size_t)r * N + (r - m)] = make_double2(xr, xi);
+            if (B0) {   // segment sums for the m = 0 mean
+                sxr += xr;
+                sxi += xi;
             }
-        }
-#pragma unroll
-        for (int u = CH - 1; u >= 0; --u) {
-            const int r = R0 + c0 + u;
-            if (valid && r < R1 && r >= m) {
-                const double2 z = zs[(c0 + u) * BW + lane];
-                xr = fma(lnext, xr, nd[u] * z.x);
-                xi = fma(lnext, xi, nd[u] * z.y);
-                a.P[(size_t)r * N + (r - m)] = make_double2(xr, xi);
-                if (B0) {   // segment sums for the m = 0 mean
-                    sxr += xr;
-                    sxi += xi;
-                }
-                lnext = l[u];
-            }
+            lnext = nl[u];
         }
     }
     if (valid) a.seg_x[(size_t)k * N + m] = make_double2(xr, xi);   // x0 at the segment's first position
@@ -425,37 +427,35 @@ __device__ __forceinline__ void solve_c_band(const SolveArgs& a, int b, int k, d
         d = a.cb[(size_t)k * N + m];
         if (B0 && m == 0) mm = *a.mu;
     }
-    const double* __restrict__ ff = a.ff;
-    const double* __restrict__ fh = a.fh;
-    for (int c0 = 0; c0 < SL; c0 += CHC) {
-        double2 x0[CHC];
-        double f[CHC], h[CHC];
+    // x0 (parked in P's lower triangle by FB) to shared memory by asynchronous
+    // copies, the pairs (F, H) to registers, all rows of the segment at once
+    const double2* __restrict__ ffh = a.ffh;
+    double f[SL], h[SL];
 #pragma unroll
-        for (int u = 0; u < CHC; ++u) {
-            const int r = R0 + c0 + u;
-            if (valid && r < R1 && r >= m) {
-                const size_t t = zt_tri(r, r - m);
-                x0[u] = a.P[(size_t)r * N + (r - m)];
-                f[u] = __ldg(ff + t);
-                h[u] = __ldg(fh + t);
-            } else {
-                x0[u] = make_double2(0.0, 0.0);
-                f[u] = h[u] = 0.0;
-            }
+    for (int u = 0; u < SL; ++u) {
+        const int r = R0 + u;
+        if (valid && r < R1 && r >= m) {
+            zt_cp_async16(xs + u * BW + lane, a.P + (size_t)r * N + (r - m));
+            const double2 q = __ldg(ffh + zt_tri(r, r - m));
+            f[u] = q.x;
+            h[u] = q.y;
+        } else {
+            f[u] = h[u] = 0.0;
         }
+    }
+    zt_cp_async_wait_all();   // each lane reads back only the rows it copied
 #pragma unroll
-        for (int u = 0; u < CHC; ++u) {
-            const int r = R0 + c0 + u;
-            if (valid && r < R1 && r >= m) {
-                double2 x = make_double2(fma(h[u], d.x, fma(f[u], c.x, x0[u].x)),
-                                         fma(h[u], d.y, fma(f[u], c.y, x0[u].y)));
-                if (B0) {   // the m = 0 mean (zero on the other lanes)
-                    x.x -= mm.x;
-                    x.y -= mm.y;
-                }
-                a.P[(size_t)r * N + (r - m)] = x;
-                xs[(c0 + u) * BW + lane] = x;
+    for (int u = 0; u < SL; ++u) {
+        const int r = R0 + u;
+        if (valid && r < R1 && r >= m) {
+            const double2 x0 = xs[u * BW + lane];
+            double2 x = make_double2(fma(h[u], d.x, fma(f[u], c.x, x0.x)), fma(h[u], d.y, fma(f[u], c.y, x0.y)));
+            if (B0) {   // the m = 0 mean (zero on the other lanes)
+                x.x -= mm.x;
+                x.y -= mm.y;
             }
+            a.P[(size_t)r * N + (r - m)] = x;
+            xs[u * BW + lane] = x;
         }
     }
     __syncwarp();
@@ -486,7 +486,7 @@ __device__ __forceinline__ void solve_c_body(const SolveArgs& a, int q, double2*
 // q goes to warp q / gridDim.x of CTA q % gridDim.x: consecutive items (the
 // band-0 items, which also reduce diagonal 0, come first in FB) land on
 // different SMs.
-__global__ void __launch_bounds__(WPC * 32, 6) solve_fb_kernel(const SolveArgs a) {
+__global__ void __launch_bounds__(WPC * 32, 4) solve_fb_kernel(const SolveArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5, nq = items(a.N);
     double2* zs = reinterpret_cast<double2*>(smem) + (size_t)w * SL * BW;
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(SCAN_TH) solve_scan_kernel(const SolveArgs a) 
     solve_scan_body(a, (blockIdx.x * SCAN_TH + threadIdx.x) >> 5);
 }
 
-__global__ void __launch_bounds__(WPC * 32, 6) solve_c_kernel(const SolveArgs a) {
+__global__ void __launch_bounds__(WPC * 32, 4) solve_c_kernel(const SolveArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = threadIdx.x >> 5, nq = items(a.N);
     double2* xs = reinterpret_cast<double2*>(smem) + (size_t)w * SL * BW;
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(WPC * 32, 6) solve_c_kernel(const SolveArgs a)
 }
 
 // Grouped: one grid over several instances (CTA counts prefix-summed in offs).
-__global__ void __launch_bounds__(WPC * 32) solve_fb_grouped(const SolveArgs* tab, const int* offs, int n, int gate) {
+__global__ void __launch_bounds__(WPC * 32, 4) solve_fb_grouped(const SolveArgs* tab, const int* offs, int n, int gate) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int inst = zt_group_find(offs, n, blockIdx.x);
     SolveArgs a = tab[inst];
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(WPC * 32) solve_fb_grouped(const SolveArgs* ta
     if (q < items(a.N)) solve_fb_body(a, q, reinterpret_cast<double2*>(smem) + (size_t)w * SL * BW);
 }
 
-__global__ void __launch_bounds__(WPC * 32) solve_c_grouped(const SolveArgs* tab, const int* offs, int n, int gate) {
+__global__ void __launch_bounds__(WPC * 32, 4) solve_c_grouped(const SolveArgs* tab, const int* offs, int n, int gate) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int inst = zt_group_find(offs, n, blockIdx.x);
     SolveArgs a = tab[inst];
@@ -549,10 +549,8 @@ int zt_solve_create(zt_plan* p) {
     p->nseg = nseg(N);
     const size_t ns = (size_t)N * p->nseg, ntri = (size_t)N * (N + 1) / 2;
     cudaStream_t ms = p->mstream;
-    ZT_CU(ZT_DMALLOC(p->fac_l, ntri * sizeof(double), ms));
-    ZT_CU(ZT_DMALLOC(p->fac_nd, ntri * sizeof(double), ms));
-    ZT_CU(ZT_DMALLOC(p->fac_f, ntri * sizeof(double), ms));
-    ZT_CU(ZT_DMALLOC(p->fac_h, ntri * sizeof(double), ms));
+    ZT_CU(ZT_DMALLOC(p->fac_lnd, ntri * sizeof(double2), ms));
+    ZT_CU(ZT_DMALLOC(p->fac_fh, ntri * sizeof(double2), ms));
     ZT_CU(ZT_DMALLOC(p->seg_z, ns * sizeof(double2), ms));
     ZT_CU(ZT_DMALLOC(p->seg_x, ns * sizeof(double2), ms));
     ZT_CU(ZT_DMALLOC(p->seg_g, ns * sizeof(double), ms));
@@ -599,10 +597,8 @@ static int solve_grid(int N) {
 
 void zt_solve_destroy(zt_plan* p) {
     cudaStream_t ms = p->mstream;
-    zt_dfree(p->fac_l, ms);
-    zt_dfree(p->fac_nd, ms);
-    zt_dfree(p->fac_f, ms);
-    zt_dfree(p->fac_h, ms);
+    zt_dfree(p->fac_lnd, ms);
+    zt_dfree(p->fac_fh, ms);
     zt_dfree(p->seg_z, ms);
     zt_dfree(p->seg_x, ms);
     zt_dfree(p->seg_g, ms);
@@ -622,7 +618,7 @@ size_t zt_solve_bytes(int N) {
 }
 
 // Segment responses of diagonal m (lane t = m mod 32 of band m / 32): segment k
-// covers positions [max(0, 32k - t), min(n, 32k + 32 - t)).  G (forward
+// covers positions [max(0, 16k - t), min(n, 16k + 16 - t)).  G (forward
 // product over the segment), F (backward sweep of nd G, zero right inflow) and
 // H (backward sweep of a unit right inflow); per segment G at its last
 // position, F and H at its first, and for m = 0 the sums of F and H.
@@ -670,11 +666,13 @@ static void diagonal_responses(int N, int m, const double* l_tri, const double* 
 int zt_solve_upload_factors(zt_plan* p, const double* host_l, const double* host_nd) {
     const int N = p->N, K = p->nseg;
     const size_t ns = (size_t)N * K, ntri = (size_t)N * (N + 1) / 2;
-    std::vector<double> F, H, NL, sg, sf, sh, sumf, sumh;
+    std::vector<double> F, H, sg, sf, sh, sumf, sumh;
+    std::vector<double2> LND, FH;
     try {
         F.assign(ntri, 0.0);
-        NL.assign(ntri, 0.0);
         H.assign(ntri, 0.0);
+        LND.resize(ntri);
+        FH.resize(ntri);
         sg.assign(ns, 0.0);
         sf.assign(ns, 0.0);
         sh.assign(ns, 0.0);
@@ -696,11 +694,12 @@ int zt_solve_upload_factors(zt_plan* p, const double* host_l, const double* host
         });
     for (auto& x : th) x.join();
     cudaStream_t cs = p->mstream;
-    for (size_t i = 0; i < ntri; ++i) NL[i] = -host_l[i];
-    cudaMemcpyAsync(p->fac_l, NL.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
-    cudaMemcpyAsync(p->fac_nd, host_nd, ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
-    cudaMemcpyAsync(p->fac_f, F.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
-    cudaMemcpyAsync(p->fac_h, H.data(), ntri * sizeof(double), cudaMemcpyHostToDevice, cs);
+    for (size_t i = 0; i < ntri; ++i) {
+        LND[i] = make_double2(-host_l[i], host_nd[i]);
+        FH[i] = make_double2(F[i], H[i]);
+    }
+    cudaMemcpyAsync(p->fac_lnd, LND.data(), ntri * sizeof(double2), cudaMemcpyHostToDevice, cs);
+    cudaMemcpyAsync(p->fac_fh, FH.data(), ntri * sizeof(double2), cudaMemcpyHostToDevice, cs);
     cudaMemcpyAsync(p->seg_g, sg.data(), ns * sizeof(double), cudaMemcpyHostToDevice, cs);
     cudaMemcpyAsync(p->seg_f, sf.data(), ns * sizeof(double), cudaMemcpyHostToDevice, cs);
     cudaMemcpyAsync(p->seg_h, sh.data(), ns * sizeof(double), cudaMemcpyHostToDevice, cs);
@@ -718,10 +717,8 @@ int zt_solve_args(zt_plan* p, const double2* W, double2* P, SolveArgs* out) {
     SolveArgs& a = *out;
     a.W = W;
     a.P = P;
-    a.fnl = p->fac_l;
-    a.fnd = p->fac_nd;
-    a.ff = p->fac_f;
-    a.fh = p->fac_h;
+    a.fln = p->fac_lnd;
+    a.ffh = p->fac_fh;
     a.seg_z = p->seg_z;
     a.seg_x = p->seg_x;
     a.seg_g = p->seg_g;
